@@ -1,0 +1,174 @@
+/*
+ * sfft.h -- C ABI of the GB300 (sm_103a) implementation of the SFFT hot path:
+ * Fourier-space construction of the delta-function-basis least-squares
+ * system, its solution, and the spatially varying convolve-and-subtract
+ * (Hu et al., "Image Subtraction in Fourier Space", arXiv:2109.09334).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images are row-major [x][y] arrays of n0 x n1 pixels: x is axis 0 (rows,
+ * length n0), y is axis 1 (contiguous), as in Eq. 1.  Pixel coordinates in
+ * the polynomials of Eq. 2 and Eq. 6 are normalised to [-1, 1]:
+ *     xt = (2x - (n0-1)) / (n0-1),   yt = (2y - (n1-1)) / (n1-1),
+ * which spans the same polynomial space as the raw indices.  Shifts and
+ * convolutions are circular (Eq. 12), every index taken mod n0, n1.
+ *
+ * Unknowns are in real-space units (the a-ring of Eq. 6; Eq. 13's
+ * a = n0*n1*a-ring is a uniform rescaling that is not applied), ordered:
+ *   kernel block first -- for each kernel term (i,j) with i+j <= dk, ordered
+ *   by total degree then descending i: (0,0),(1,0),(0,1),(2,0),(1,1),(0,2),...
+ *   -- the offsets (alpha,beta) row-major, alpha from -w0 to w0 (outer), beta
+ *   from -w1 to w1; with a constant photometric ratio the offset (0,0) of
+ *   every term other than (0,0) is omitted; then the background terms (p,q)
+ *   with p+q <= db in the same monomial order.  n = nk*L + nb, or
+ *   nk*(L-1) + 1 + nb with a constant photometric ratio, where L =
+ *   (2w0+1)(2w1+1), nk = (dk+1)(dk+2)/2, nb = (db+1)(db+2)/2.
+ *
+ * Memory: every pointer named d_* is device memory owned by the caller; h_*
+ * is host memory owned by the caller (page-locked for asynchronous copies).
+ * A plan owns its workspace; it is not thread-safe and serves one pair at a
+ * time on the stream it is used with.
+ *
+ * Errors: calls are asynchronous on the given stream.  A negative return
+ * value reports an invalid argument, an allocation failure or a launch
+ * failure, synchronously, and nothing was enqueued past the failing launch.
+ * Numerical failures (matrix not positive definite, refinement not
+ * converged) are written to sfft_solve_info.status in device memory.
+ * No exception crosses this interface.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFFT_OK = 0,
+    SFFT_ERR_INVALID = -1,       /* bad argument or configuration */
+    SFFT_ERR_OOM = -2,           /* device or host allocation failed */
+    SFFT_ERR_CUDA = -3,          /* a CUDA call or kernel launch failed */
+    SFFT_ERR_SINGULAR = -4,      /* normal matrix not positive definite (device status) */
+    SFFT_ERR_NOT_CONVERGED = -5, /* iterative refinement did not reach tolerance (device status) */
+    SFFT_ERR_TIMEOUT = -6,       /* a bounded wait ran out */
+    SFFT_ERR_BUSY = -7,          /* no free slot / memory for a request right now */
+    SFFT_ERR_UNSUPPORTED = -8    /* valid but not implemented (e.g. image size) */
+} sfft_status;
+
+typedef enum { SFFT_F32 = 0, SFFT_F64 = 1 } sfft_dtype;
+
+typedef enum {
+    SFFT_PREC_FP64 = 0,  /* plain path: FP64 FFTs, products, sums and Cholesky */
+    SFFT_PREC_MIXED = 1  /* FP32 FFTs and products with compensated (two-sum)
+                            accumulation of the frequency sums, FP32 Cholesky of
+                            the Jacobi-scaled matrix, FP64 residual refinement */
+} sfft_precision;
+
+/* Fit parameters of one image pair (Sec. 3.3 and Table A1). */
+typedef struct {
+    int32_t n0, n1;           /* image size; each a power of two in [16, 8192] */
+    int32_t w0, w1;           /* kernel half-widths: L0 = 2*w0+1, L1 = 2*w1+1 (Eq. 3-4) */
+    int32_t dk;               /* kernel polynomial degree D_K (Eq. 6), 0..3 */
+    int32_t db;               /* background polynomial degree D_B (Eq. 2), 0..3 */
+    int32_t const_phot_ratio; /* 1: kernel sum constant over the field (Sec. 2.2) */
+    int32_t dtype;            /* sfft_dtype of the images R, S and of the output D */
+    int32_t precision;        /* sfft_precision */
+} sfft_config;
+
+/* Written by sfft_solve in device memory. */
+typedef struct {
+    int32_t status;       /* SFFT_OK, SFFT_ERR_SINGULAR or SFFT_ERR_NOT_CONVERGED */
+    int32_t iters;        /* refinement iterations performed */
+    double rel_residual;  /* ||rhs - M x||_2 / ||rhs||_2 of the returned x (FP64) */
+    double min_pivot;     /* smallest Cholesky pivot of the Jacobi-scaled matrix */
+} sfft_solve_info;
+
+typedef struct sfft_plan_s *sfft_plan_t;
+typedef void *sfft_stream_t; /* a cudaStream_t; NULL is the legacy default stream */
+
+/* Human-readable name of a status code.  Never NULL. */
+const char *sfft_status_string(int status);
+
+/* Number of unknowns n of Eq. 18 for this configuration (no GPU use). */
+int sfft_num_unknowns(const sfft_config *cfg, int32_t *n);
+
+/*
+ * Create a plan for one configuration: validates it, allocates the device
+ * workspace, and computes on `stream` the twiddle tables and the 1-D spectra
+ * of the background monomials (T^pq of Eq. 2 is separable, so its DFT is the
+ * outer product of two 1-D DFTs).  *out is NULL on failure.
+ */
+int sfft_plan_create(const sfft_config *cfg, sfft_stream_t stream, sfft_plan_t *out);
+
+/* Synchronises the plan's last stream, then frees its workspace. NULL is a no-op. */
+int sfft_plan_destroy(sfft_plan_t plan);
+
+/* Device bytes the plan holds. */
+int sfft_plan_workspace_bytes(sfft_plan_t plan, uint64_t *bytes);
+
+/*
+ * Build the normal equations M theta = rhs of Eq. 18 (blocks Eq. 19-24) from
+ * the reference R and science S, through the lag tables of App. B
+ * (Eq. B5-B16): forward FFTs of the monomial-weighted images R^ij = xt^i yt^j R
+ * and of S, spectrum products, a pruned inverse DFT evaluated only at the lags
+ * |rho| <= 2w (Omega) and |rho| <= w (Lambda, Theta), and the index maps of
+ * Eq. B5/B7/B9/B13 into M and rhs.  C and E (Eq. B11, B15) are moment sums.
+ *   d_ref, d_sci : n0*n1 images of cfg.dtype.
+ *   d_mask       : n0*n1 bytes or NULL; 0 marks a pixel excluded from the fit
+ *                  (R and S zero-filled there, Sec. 3); NULL uses every pixel.
+ *   d_M          : n*n doubles, row-major, symmetric (both triangles written).
+ *   d_rhs        : n doubles.
+ */
+int sfft_build_system(sfft_plan_t plan, const void *d_ref, const void *d_sci,
+                      const uint8_t *d_mask, double *d_M, double *d_rhs,
+                      sfft_stream_t stream);
+
+/*
+ * Solve M theta = rhs (Eq. 18; the paper names no solver).  FP64 precision:
+ * Cholesky in FP64.  Mixed precision: Jacobi scaling, Cholesky in FP32, then
+ * iterative refinement with FP64 residuals r = rhs - M theta until
+ * ||r|| / ||rhs|| <= 1e-12 or 30 iterations.
+ *   d_M, d_rhs : as written by sfft_build_system (read only).
+ *   d_x        : n doubles, the coefficients theta in the unknown order above.
+ *   d_info     : device sfft_solve_info, or NULL.
+ */
+int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double *d_x,
+               sfft_solve_info *d_info, sfft_stream_t stream);
+
+/*
+ * Difference image of Eq. 12-13 from the UNMASKED pair (two-step process of
+ * Sec. 3): D = S - sum_ij (R^ij o k_ij) - sum_pq b_pq T^pq, evaluated in
+ * Fourier space along y and as an L0-tap circular stencil along x.
+ *   d_x    : n doubles from sfft_solve.
+ *   d_diff : n0*n1 output image of cfg.dtype (may not alias d_ref or d_sci).
+ */
+int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const double *d_x,
+                  void *d_diff, sfft_stream_t stream);
+
+/*
+ * One whole pair on device buffers: build, solve and subtract.  d_M, d_rhs,
+ * d_x and d_info may be NULL, in which case plan-owned buffers are used.
+ */
+int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci,
+                  const uint8_t *d_mask, double *d_M, double *d_rhs, double *d_x,
+                  sfft_solve_info *d_info, void *d_diff, sfft_stream_t stream);
+
+/*
+ * One whole pair from and to host memory: copies h_ref, h_sci (and h_mask if
+ * not NULL) to plan-owned device buffers, runs build, solve and subtract,
+ * copies the coefficients, the solve status and the difference image back,
+ * and synchronises the stream before returning.
+ *   h_x    : n doubles or NULL.  h_info : host sfft_solve_info or NULL.
+ *   h_diff : n0*n1 image of cfg.dtype.
+ */
+int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci,
+                       const uint8_t *h_mask, double *h_x, sfft_solve_info *h_info,
+                       void *h_diff, sfft_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFFT_H */

@@ -1,0 +1,125 @@
+"""GB300 (sm_103a) implementation of the SFFT hot path (arXiv:2109.09334).
+
+Image subtraction in Fourier space: the delta-function-basis least-squares
+system (Eq. 18-24, App. B) is built from FFTs of the monomial-weighted
+images, spectrum products and a pruned inverse DFT; it is solved by a
+Jacobi-scaled Cholesky with FP64 refinement; and the difference image
+(Eq. 12-13) is formed in Fourier space.  All arithmetic runs in the CUDA
+library ``libsfft.so`` behind the C ABI of ``include/sfft.h``; this package is
+its ctypes binding plus a small convenience wrapper over torch tensors (torch
+only provides device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import binding
+from .binding import (  # noqa: F401
+    SfftError,
+    make_config,
+    sfft_build_system,
+    sfft_num_unknowns,
+    sfft_plan_create,
+    sfft_plan_destroy,
+    sfft_plan_workspace_bytes,
+    sfft_run_pair,
+    sfft_run_pair_host,
+    sfft_solve,
+    sfft_solve_info,
+    sfft_subtract,
+    status_string,
+)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def info_from_bytes(buf):
+    """Parse a 24-byte sfft_solve_info copied to the host."""
+    raw = bytes(buf)
+    s = sfft_solve_info.from_buffer_copy(raw[: ctypes.sizeof(sfft_solve_info)])
+    return {"status": s.status, "iters": s.iters, "rel_residual": s.rel_residual, "min_pivot": s.min_pivot}
+
+
+class SfftPlan:
+    """One plan (workspace + tables) for a fixed image size and fit configuration."""
+
+    def __init__(self, n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed",
+                 stream=None):
+        torch = _torch()
+        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        self.n = sfft_num_unknowns(self.cfg)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = sfft_plan_create(self.cfg, self.stream)
+        self.shape = (n0, n1)
+        self.dtype = {"float32": torch.float32, "f32": torch.float32,
+                      "float64": torch.float64, "f64": torch.float64}[str(dtype)]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if self.handle:
+            sfft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self):
+        return sfft_plan_workspace_bytes(self.handle)
+
+    def _check_img(self, t):
+        torch = _torch()
+        assert t.is_cuda and t.dtype == self.dtype and tuple(t.shape) == self.shape and t.is_contiguous(), \
+            f"expected a contiguous {self.dtype} CUDA tensor of shape {self.shape}"
+        return t
+
+    def build_system(self, ref, sci, mask=None):
+        torch = _torch()
+        self._check_img(ref), self._check_img(sci)
+        M = torch.empty((self.n, self.n), dtype=torch.float64, device=self.device)
+        rhs = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        sfft_build_system(self.handle, ref, sci, mask, M, rhs, self.stream)
+        return M, rhs
+
+    def solve(self, M, rhs):
+        torch = _torch()
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        info = torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=self.device)
+        sfft_solve(self.handle, M, rhs, x, info, self.stream)
+        return x, info
+
+    def subtract(self, ref, sci, x):
+        torch = _torch()
+        self._check_img(ref), self._check_img(sci)
+        D = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        sfft_subtract(self.handle, ref, sci, x, D, self.stream)
+        return D
+
+    def run_pair(self, ref, sci, mask=None, out=None, keep_system=False):
+        torch = _torch()
+        self._check_img(ref), self._check_img(sci)
+        D = out if out is not None else torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        x = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        info = torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=self.device)
+        M = rhs = None
+        if keep_system:
+            M = torch.empty((self.n, self.n), dtype=torch.float64, device=self.device)
+            rhs = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        sfft_run_pair(self.handle, ref, sci, mask, M, rhs, x, info, D, self.stream)
+        return D, x, info, M, rhs
+
+    def run_pair_host(self, ref, sci, mask=None, x_out=None, diff_out=None):
+        """Host (preferably pinned) tensors in and out; synchronises before returning."""
+        torch = _torch()
+        D = diff_out if diff_out is not None else torch.empty(self.shape, dtype=self.dtype)
+        x = x_out if x_out is not None else torch.empty(self.n, dtype=torch.float64)
+        info = sfft_solve_info()
+        sfft_run_pair_host(self.handle, ref, sci, mask, x, info, D, self.stream)
+        return D, x, {"status": info.status, "iters": info.iters, "rel_residual": info.rel_residual,
+                      "min_pivot": info.min_pivot}

@@ -1,0 +1,160 @@
+"""Thin ctypes binding of ``libsfft.so`` (include/sfft.h).
+
+Argument marshalling only: every step of the subtraction runs in the CUDA
+library.  Functions keep the C names; pointers may be given as integers or as
+objects with ``data_ptr()`` (torch tensors), streams as integers or
+``torch.cuda.Stream``.  A negative status raises :class:`SfftError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .build import LIB
+
+SFFT_OK = 0
+SFFT_ERR_INVALID = -1
+SFFT_ERR_OOM = -2
+SFFT_ERR_CUDA = -3
+SFFT_ERR_SINGULAR = -4
+SFFT_ERR_NOT_CONVERGED = -5
+SFFT_ERR_TIMEOUT = -6
+SFFT_ERR_BUSY = -7
+SFFT_ERR_UNSUPPORTED = -8
+
+SFFT_F32, SFFT_F64 = 0, 1
+SFFT_PREC_FP64, SFFT_PREC_MIXED = 0, 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sfft.h")
+
+
+class sfft_config(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in
+                ("n0", "n1", "w0", "w1", "dk", "db", "const_phot_ratio", "dtype", "precision")]
+
+
+class sfft_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("min_pivot", ctypes.c_double)]
+
+
+class SfftError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def library():
+    """Load libsfft.so; fails loudly if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"libsfft.so not built ({LIB}); run paper_2109_09334_gb300.build.build()")
+        lib = ctypes.CDLL(LIB)
+        vp, i32, cfgp = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(sfft_config)
+        lib.sfft_status_string.restype = ctypes.c_char_p
+        lib.sfft_status_string.argtypes = [ctypes.c_int]
+        lib.sfft_num_unknowns.argtypes = [cfgp, ctypes.POINTER(i32)]
+        lib.sfft_plan_create.argtypes = [cfgp, vp, ctypes.POINTER(vp)]
+        lib.sfft_plan_destroy.argtypes = [vp]
+        lib.sfft_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sfft_build_system.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.sfft_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        _lib = lib
+    return _lib
+
+
+def declared_functions():
+    """Names of the functions include/sfft.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sfft_\w+)\s*\(", text, re.M)))
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    if isinstance(x, ctypes.Structure):
+        return ctypes.addressof(x)
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _s(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, where):
+    if rc != SFFT_OK:
+        raise SfftError(rc, where)
+
+
+def status_string(status):
+    return library().sfft_status_string(status).decode()
+
+
+def make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed"):
+    dt = {"float32": SFFT_F32, "f32": SFFT_F32, "float64": SFFT_F64, "f64": SFFT_F64}[str(dtype)]
+    pr = {"fp64": SFFT_PREC_FP64, "mixed": SFFT_PREC_MIXED}[precision]
+    return sfft_config(n0, n1, w0, w1, dk, db, int(bool(const_phot_ratio)), dt, pr)
+
+
+def sfft_num_unknowns(cfg):
+    n = ctypes.c_int32()
+    _check(library().sfft_num_unknowns(ctypes.byref(cfg), ctypes.byref(n)), "sfft_num_unknowns")
+    return n.value
+
+
+def sfft_plan_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    _check(library().sfft_plan_create(ctypes.byref(cfg), _s(stream), ctypes.byref(h)), "sfft_plan_create")
+    return h.value
+
+
+def sfft_plan_destroy(plan):
+    _check(library().sfft_plan_destroy(plan), "sfft_plan_destroy")
+
+
+def sfft_plan_workspace_bytes(plan):
+    b = ctypes.c_uint64()
+    _check(library().sfft_plan_workspace_bytes(plan, ctypes.byref(b)), "sfft_plan_workspace_bytes")
+    return b.value
+
+
+def sfft_build_system(plan, d_ref, d_sci, d_mask, d_M, d_rhs, stream=None):
+    _check(library().sfft_build_system(plan, _p(d_ref), _p(d_sci), _p(d_mask), _p(d_M), _p(d_rhs), _s(stream)),
+           "sfft_build_system")
+
+
+def sfft_solve(plan, d_M, d_rhs, d_x, d_info=None, stream=None):
+    _check(library().sfft_solve(plan, _p(d_M), _p(d_rhs), _p(d_x), _p(d_info), _s(stream)), "sfft_solve")
+
+
+def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):
+    _check(library().sfft_subtract(plan, _p(d_ref), _p(d_sci), _p(d_x), _p(d_diff), _s(stream)), "sfft_subtract")
+
+
+def sfft_run_pair(plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, stream=None):
+    _check(library().sfft_run_pair(plan, _p(d_ref), _p(d_sci), _p(d_mask), _p(d_M), _p(d_rhs), _p(d_x),
+                                   _p(d_info), _p(d_diff), _s(stream)), "sfft_run_pair")
+
+
+def sfft_run_pair_host(plan, h_ref, h_sci, h_mask, h_x, h_info, h_diff, stream=None):
+    _check(library().sfft_run_pair_host(plan, _p(h_ref), _p(h_sci), _p(h_mask), _p(h_x), _p(h_info),
+                                        _p(h_diff), _s(stream)), "sfft_run_pair_host")

@@ -1,0 +1,363 @@
+// api.cu -- the extern "C" entry points declared in include/sfft.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sfft {
+
+// exp(-2 pi i q / n) in FP64
+__global__ void k_twiddle64(int n, cpx<double> *tw) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)q / (double)n, &s, &c);
+        tw[q] = mk(c, s);
+    }
+}
+
+template <typename T>
+__global__ void k_round(int n, const cpx<double> *src, cpx<T> *dst) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        dst[q] = mk((T)src[q].re, (T)src[q].im);
+}
+
+// 1-D DFT of xt^p (FP64, direct sum with the FP64 table), written in the
+// compute type.  perm: output index of bin l (permuted layout for x, natural for y).
+template <typename T>
+__global__ void k_poly_dft(int n, int nout, int pmax, const cpx<double> *tw, int na, int nbk, int permute,
+                           cpx<T> *out) {
+    const int total = (pmax + 1) * nout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int p = e / nout, l = e % nout;
+        double re = 0.0, im = 0.0;
+        for (int x = 0; x < n; ++x) {
+            const double v = ipow(coord<double>(x, n), p);
+            const cpx<double> w = tw[(int)(((long long)l * x) % n)];
+            re += v * w.re;
+            im += v * w.im;
+        }
+        int o = l;
+        if (permute) o = (l % nbk) * na + l / nbk;
+        out[(size_t)p * nout + o] = mk((T)re, (T)im);
+    }
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int validate(const sfft_config *c) {
+    if (!c) return SFFT_ERR_INVALID;
+    if (!is_pow2(c->n0) || !is_pow2(c->n1)) return SFFT_ERR_UNSUPPORTED;
+    if (c->n0 < 16 || c->n1 < 16 || c->n0 > 4096 || c->n1 > 4096) return SFFT_ERR_UNSUPPORTED;
+    if (c->w0 < 0 || c->w1 < 0 || c->dk < 0 || c->db < 0) return SFFT_ERR_INVALID;
+    if (c->dk > 3 || c->db > 3) return SFFT_ERR_UNSUPPORTED;
+    const int na = c->n0 < kMaxNA ? c->n0 : kMaxNA;
+    if (4 * c->w0 + 1 > na || 4 * c->w1 + 1 > c->n1) return SFFT_ERR_UNSUPPORTED;
+    if (c->dtype != SFFT_F32 && c->dtype != SFFT_F64) return SFFT_ERR_INVALID;
+    if (c->precision != SFFT_PREC_FP64 && c->precision != SFFT_PREC_MIXED) return SFFT_ERR_INVALID;
+    return SFFT_OK;
+}
+
+static int unknowns(const sfft_config *c) {
+    const int L = (2 * c->w0 + 1) * (2 * c->w1 + 1);
+    const int nk = n_terms(c->dk), nb = n_terms(c->db);
+    return c->const_phot_ratio ? nk * (L - 1) + 1 + nb : nk * L + nb;
+}
+
+static void free_plan(Plan *p) {
+    void *bufs[] = {p->tw0, p->tw1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
+                    p->lag, p->A, p->dscale, p->r, p->xw, p->yv, p->zv, p->flag, p->M_own, p->rhs_own,
+                    p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+#define SFFT_ALLOC(ptr, bytes)                                        \
+    do {                                                              \
+        if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {    \
+            cudaGetLastError();                                       \
+            free_plan(p);                                             \
+            return SFFT_ERR_OOM;                                      \
+        }                                                             \
+        p->ws_bytes += (bytes);                                       \
+    } while (0)
+
+static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return SFFT_ERR_OOM;
+    memset((void *)p, 0, sizeof(Plan));
+    p->cfg = *cfg;
+    p->n0 = cfg->n0;
+    p->n1 = cfg->n1;
+    p->h1c = cfg->n1 / 2 + 1;
+    p->nk = n_terms(cfg->dk);
+    p->nb = n_terms(cfg->db);
+    p->n = unknowns(cfg);
+    p->L0 = 2 * cfg->w0 + 1;
+    p->L1 = 2 * cfg->w1 + 1;
+    p->na = cfg->n0 < kMaxNA ? cfg->n0 : kMaxNA;
+    p->nbk = cfg->n0 / p->na;
+    p->nimg = p->nk + 1;
+    p->fp64 = cfg->precision == SFFT_PREC_FP64;
+    p->csz = p->fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+    p->last_stream = s;
+    // gather pairs
+    int np = 0, rows = 0;
+    auto push = [&](int kind, int a, int b, int h0) {
+        PairDesc d;
+        d.kind = kind;
+        d.a = a;
+        d.b = b;
+        d.h0 = h0;
+        d.row0 = rows;
+        rows += 2 * h0 + 1;
+        p->host_pairs[np++] = d;
+    };
+    for (int a = 0; a < p->nk; ++a)
+        for (int b = a; b < p->nk; ++b) push(PK_OMEGA, a, b, 2 * cfg->w0);
+    for (int a = 0; a < p->nk; ++a)
+        for (int q = 0; q <= cfg->db; ++q) push(PK_LAMBDA, a, q, cfg->w0);
+    for (int a = 0; a < p->nk; ++a) push(PK_THETA, a, p->nk, cfg->w0);
+    p->npairs = np;
+    p->nrows = rows;
+    p->nmom = (2 * cfg->dk + 1) + (cfg->dk + cfg->db + 1) + (cfg->dk + 1) + (cfg->db + 1);
+
+    const size_t P = (size_t)p->n0 * p->n1;
+    const size_t half = (size_t)p->h1c * p->n0;
+    const size_t csz = p->csz;
+    const size_t rsz = p->fp64 ? sizeof(double) : sizeof(float);
+    const int npo = p->nk * (p->nk + 1) / 2;
+    const size_t lom = (size_t)(4 * cfg->w0 + 1) * (4 * cfg->w1 + 1);
+    const size_t lla = (size_t)(2 * cfg->w0 + 1) * (2 * cfg->w1 + 1);
+    p->lag_om = 0;
+    p->lag_la = (int)(npo * lom);
+    p->lag_th = (int)(p->lag_la + (size_t)p->nk * p->nb * lla);
+    const size_t nlag = p->lag_th + (size_t)p->nk * lla;
+    const size_t n = p->n;
+    (void)P;
+
+    SFFT_ALLOC(p->tw0, p->n0 * csz);
+    SFFT_ALLOC(p->tw1, p->n1 * csz);
+    SFFT_ALLOC(p->xhat, (size_t)(cfg->db + 1) * p->n0 * csz);
+    SFFT_ALLOC(p->yhat, (size_t)(cfg->db + 1) * p->h1c * csz);
+    SFFT_ALLOC(p->F, (size_t)(cfg->dk + 2) * half * csz);
+    SFFT_ALLOC(p->U, (size_t)p->nimg * half * csz);
+    SFFT_ALLOC(p->Q, (size_t)p->nrows * p->h1c * csz);
+    SFFT_ALLOC(p->pairs, (size_t)np * sizeof(PairDesc));
+    SFFT_ALLOC(p->rowmom, (size_t)p->n0 * p->nmom * sizeof(double));
+    SFFT_ALLOC(p->mom, (size_t)(24 * 7 + 16) * sizeof(double));
+    SFFT_ALLOC(p->lag, nlag * sizeof(double));
+    SFFT_ALLOC(p->A, n * n * rsz);
+    SFFT_ALLOC(p->dscale, n * sizeof(double));
+    SFFT_ALLOC(p->r, n * sizeof(double));
+    SFFT_ALLOC(p->xw, (n + 600) * sizeof(double));
+    SFFT_ALLOC(p->yv, n * rsz);
+    SFFT_ALLOC(p->zv, n * rsz);
+    SFFT_ALLOC(p->flag, 4 * sizeof(int));
+    SFFT_ALLOC(p->M_own, n * n * sizeof(double));
+    SFFT_ALLOC(p->rhs_own, n * sizeof(double));
+    SFFT_ALLOC(p->x_own, n * sizeof(double));
+    SFFT_ALLOC(p->info_own, sizeof(sfft_solve_info));
+    SFFT_ALLOC(p->kap, (size_t)p->nk * p->L0 * p->h1c * csz);
+
+    // constant tables
+    cudaError_t err;
+    if ((err = cudaMemcpyAsync(p->pairs, p->host_pairs, np * sizeof(PairDesc), cudaMemcpyHostToDevice, s))) {
+        free_plan(p);
+        return SFFT_ERR_CUDA;
+    }
+    double csum[16];
+    for (int e = 0; e < 8; ++e) {
+        double a = 0.0, b = 0.0;
+        for (int x = 0; x < p->n0; ++x) a += pow((2.0 * x - (p->n0 - 1)) / (p->n0 - 1), e);
+        for (int y = 0; y < p->n1; ++y) b += pow((2.0 * y - (p->n1 - 1)) / (p->n1 - 1), e);
+        csum[e] = a;
+        csum[8 + e] = b;
+    }
+    // csum is copied from a host stack array: make the copy synchronous
+    if ((err = cudaMemcpy(p->mom + 24 * 7, csum, sizeof(csum), cudaMemcpyHostToDevice))) {
+        free_plan(p);
+        return SFFT_ERR_CUDA;
+    }
+    cpx<double> *t64a = nullptr, *t64b = nullptr;
+    if (cudaMalloc((void **)&t64a, p->n0 * sizeof(cpx<double>)) != cudaSuccess ||
+        cudaMalloc((void **)&t64b, p->n1 * sizeof(cpx<double>)) != cudaSuccess) {
+        cudaGetLastError();
+        if (t64a) cudaFree(t64a);
+        free_plan(p);
+        return SFFT_ERR_OOM;
+    }
+    k_twiddle64<<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a);
+    k_twiddle64<<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b);
+    const int bx = ((cfg->db + 1) * p->n0 + 127) / 128, by = ((cfg->db + 1) * p->h1c + 127) / 128;
+    if (p->fp64) {
+        k_round<double><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<double> *)p->tw0);
+        k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<double> *)p->tw1);
+        k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<double> *)p->xhat);
+        k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<double> *)p->yhat);
+    } else {
+        k_round<float><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<float> *)p->tw0);
+        k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<float> *)p->tw1);
+        k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<float> *)p->xhat);
+        k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<float> *)p->yhat);
+    }
+    err = cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(t64a);
+    cudaFree(t64b);
+    if (err != cudaSuccess) {
+        free_plan(p);
+        return SFFT_ERR_CUDA;
+    }
+    *out = p;
+    return SFFT_OK;
+}
+
+static int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return SFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return SFFT_ERR_OOM;
+    return SFFT_ERR_CUDA;
+}
+
+static size_t img_bytes(const Plan *p) {
+    return (size_t)p->n0 * p->n1 * (p->cfg.dtype == SFFT_F64 ? sizeof(double) : sizeof(float));
+}
+
+static int run_pair(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M, double *rhs,
+                    double *x, sfft_solve_info *info, void *diff, cudaStream_t s) {
+    if (!M) M = p->M_own;
+    if (!rhs) rhs = p->rhs_own;
+    if (!x) x = p->x_own;
+    if (!info) info = p->info_own;
+    cudaError_t e = build_system(p, ref, sci, mask, M, rhs, s);
+    if (e == cudaSuccess) e = solve_system(p, M, rhs, x, info, s);
+    if (e == cudaSuccess && mask) e = row_transform(p, ref, sci, nullptr, false, s);
+    if (e == cudaSuccess) e = subtract_from_rows(p, x, diff, s);
+    p->last_stream = s;
+    return status_of(e);
+}
+
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" {
+
+const char *sfft_status_string(int status) {
+    switch (status) {
+        case SFFT_OK: return "ok";
+        case SFFT_ERR_INVALID: return "invalid argument";
+        case SFFT_ERR_OOM: return "out of memory";
+        case SFFT_ERR_CUDA: return "CUDA error";
+        case SFFT_ERR_SINGULAR: return "normal matrix not positive definite";
+        case SFFT_ERR_NOT_CONVERGED: return "iterative refinement did not converge";
+        case SFFT_ERR_TIMEOUT: return "timed out";
+        case SFFT_ERR_BUSY: return "busy";
+        case SFFT_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+int sfft_num_unknowns(const sfft_config *cfg, int32_t *n) {
+    if (!cfg || !n) return SFFT_ERR_INVALID;
+    if (cfg->w0 < 0 || cfg->w1 < 0 || cfg->dk < 0 || cfg->db < 0) return SFFT_ERR_INVALID;
+    *n = unknowns(cfg);
+    return SFFT_OK;
+}
+
+int sfft_plan_create(const sfft_config *cfg, sfft_stream_t stream, sfft_plan_t *out) {
+    if (!out) return SFFT_ERR_INVALID;
+    *out = nullptr;
+    int v = validate(cfg);
+    if (v) return v;
+    Plan *p = nullptr;
+    int rc = create(cfg, (cudaStream_t)stream, &p);
+    if (rc == SFFT_OK) *out = (sfft_plan_t)p;
+    return rc;
+}
+
+int sfft_plan_destroy(sfft_plan_t plan) {
+    if (!plan) return SFFT_OK;
+    Plan *p = (Plan *)plan;
+    cudaStreamSynchronize(p->last_stream);
+    free_plan(p);
+    return SFFT_OK;
+}
+
+int sfft_plan_workspace_bytes(sfft_plan_t plan, uint64_t *bytes) {
+    if (!plan || !bytes) return SFFT_ERR_INVALID;
+    *bytes = ((Plan *)plan)->ws_bytes;
+    return SFFT_OK;
+}
+
+int sfft_build_system(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask,
+                      double *d_M, double *d_rhs, sfft_stream_t stream) {
+    if (!plan || !d_ref || !d_sci || !d_M || !d_rhs) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    p->last_stream = (cudaStream_t)stream;
+    return status_of(build_system(p, d_ref, d_sci, d_mask, d_M, d_rhs, (cudaStream_t)stream));
+}
+
+int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double *d_x, sfft_solve_info *d_info,
+               sfft_stream_t stream) {
+    if (!plan || !d_M || !d_rhs || !d_x) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    p->last_stream = (cudaStream_t)stream;
+    return status_of(solve_system(p, d_M, d_rhs, d_x, d_info, (cudaStream_t)stream));
+}
+
+int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const double *d_x, void *d_diff,
+                  sfft_stream_t stream) {
+    if (!plan || !d_ref || !d_sci || !d_x || !d_diff) return SFFT_ERR_INVALID;
+    if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e = row_transform(p, d_ref, d_sci, nullptr, false, s);
+    if (e == cudaSuccess) e = subtract_from_rows(p, d_x, d_diff, s);
+    return status_of(e);
+}
+
+int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask, double *d_M,
+                  double *d_rhs, double *d_x, sfft_solve_info *d_info, void *d_diff, sfft_stream_t stream) {
+    if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
+    if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    return run_pair((Plan *)plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, (cudaStream_t)stream);
+}
+
+int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci, const uint8_t *h_mask,
+                       double *h_x, sfft_solve_info *h_info, void *h_diff, sfft_stream_t stream) {
+    if (!plan || !h_ref || !h_sci || !h_diff) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ib = img_bytes(p);
+    const size_t P = (size_t)p->n0 * p->n1;
+    if (!p->img_ref) {
+        if (cudaMalloc(&p->img_ref, ib) != cudaSuccess || cudaMalloc(&p->img_sci, ib) != cudaSuccess ||
+            cudaMalloc(&p->img_diff, ib) != cudaSuccess || cudaMalloc((void **)&p->img_mask, P) != cudaSuccess) {
+            cudaGetLastError();
+            return SFFT_ERR_OOM;
+        }
+        p->ws_bytes += 3 * ib + P;
+    }
+    cudaError_t e = cudaMemcpyAsync(p->img_ref, h_ref, ib, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->img_sci, h_sci, ib, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h_mask) e = cudaMemcpyAsync(p->img_mask, h_mask, P, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return status_of(e);
+    int rc = run_pair(p, p->img_ref, p->img_sci, h_mask ? p->img_mask : nullptr, nullptr, nullptr, nullptr,
+                      nullptr, p->img_diff, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(h_diff, p->img_diff, ib, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_x) e = cudaMemcpyAsync(h_x, p->x_own, p->n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_info)
+        e = cudaMemcpyAsync(h_info, p->info_own, sizeof(sfft_solve_info), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return status_of(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,642 @@
+// build.cu -- construction of the normal equations (Eq. 18-24 via App. B).
+//
+// Pipeline (all on the plan's stream):
+//   k_rows     row pass: zero-fill with the mask, weight by yt^j, real FFT of
+//              every row along y for j = 0..dk and of S; writes the row
+//              transforms transposed ([image][m][x], x contiguous) and the
+//              per-row moment sums used for the lag-zero entries.
+//   k_moments  FP64 moments sum_x xt^u * (row moment) (Eq. B11, B15 and the
+//              lag-zero values of Omega, Lambda, Theta).
+//   k_cols     column pass: weight by xt^i, FFT along x, and store every
+//              spectrum permuted so that the bins l = lb + NB*r (r < NA) of one
+//              residue class lb are contiguous.
+//   k_gather   for each column m and residue class lb: spectrum products
+//              conj(U_a) U_b with the DC bin removed, an NA-point inverse DFT
+//              over r, and the outer sum over lb with twiddles exp(2 pi i lb
+//              rho/N0), accumulated with two-sum compensation (pruned inverse
+//              DFT along x, only |rho| <= 2w (Omega) or w (Lambda, Theta)).
+//   k_stage2   the remaining sum over m with exp(2 pi i m rho/N1) (and the
+//              1-D spectrum of y^q for Lambda), compensated, to FP64 lag tables.
+//   k_assemble the index maps of Eq. B5, B7, B9, B11, B13, B15 into M and rhs.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "internal.h"
+
+namespace sfft {
+
+constexpr int kMaxMom = 24;  // per-row moments for dk, db <= 3
+constexpr int kUMax = 7;     // powers of xt in the moment tables (u <= 6)
+
+struct MomLayout {
+    int fRR, fR, fRS, fS, n;
+};
+__host__ __device__ inline MomLayout mom_layout(int dk, int db) {
+    MomLayout m;
+    m.fRR = 0;
+    m.fR = 2 * dk + 1;
+    m.fRS = m.fR + dk + db + 1;
+    m.fS = m.fRS + dk + 1;
+    m.n = m.fS + db + 1;
+    return m;
+}
+
+template <typename I>
+__device__ __forceinline__ double load_img(const I *p, size_t k) { return (double)p[k]; }
+
+// ---------------------------------------------------------------------------
+// Row pass.  Block: TR rows; sequences per row: yt^j * Rm (j <= dk) and Sm,
+// packed two per complex FFT (real and imaginary part) and separated after.
+template <typename T, typename I>
+__global__ void k_rows(int n0, int n1, int dk, int db, int TR, const I *__restrict__ R,
+                       const I *__restrict__ S, const uint8_t *__restrict__ mask,
+                       cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1, int want_mom,
+                       double *__restrict__ rowmom) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // TR * n1
+    cpx<T> *scr = Z + (size_t)TR * n1;                 // n1
+    Acc<T> *red = reinterpret_cast<Acc<T> *>(scr + n1); // (nthr/32) * kMaxMom
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int x0b = blockIdx.x * TR;
+    const int h1c = n1 / 2 + 1;
+    const int nseq = dk + 2;
+    const int nfft = (nseq + 1) / 2;
+    const MomLayout ml = mom_layout(dk, db);
+
+    for (int f = 0; f < nfft; ++f) {
+        const int sa = 2 * f, sb = 2 * f + 1;
+        for (int r = 0; r < TR; ++r) {
+            const int x0 = x0b + r;
+            const size_t rowoff = (size_t)x0 * n1;
+            // per-thread partial moments (plain sums of n1/nthr terms), then a
+            // compensated block reduction
+            T pRR[7], pR[7], pRS[4], pS[4];
+#pragma unroll
+            for (int v = 0; v < 7; ++v) pRR[v] = pR[v] = (T)0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pRS[v] = pS[v] = (T)0;
+            const bool mom = want_mom && f == 0;
+            for (int y = tid; y < n1; y += nthr) {
+                T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
+                T rv = (T)load_img(R, rowoff + y) * keep;
+                T sv = (T)load_img(S, rowoff + y) * keep;
+                T yt = coord<T>(y, n1);
+                T va, vb;
+                va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
+                vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
+                Z[(size_t)r * n1 + y] = mk(va, vb);
+                if (mom) {
+                    T p = (T)1;
+#pragma unroll
+                    for (int v = 0; v < 7; ++v) {
+                        pRR[v] += rv * rv * p;
+                        pR[v] += rv * p;
+                        if (v < 4) {
+                            pRS[v] += rv * sv * p;
+                            pS[v] += sv * p;
+                        }
+                        p *= yt;
+                    }
+                }
+            }
+            if (mom) {
+                const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+                for (int k = 0; k < 22; ++k) {
+                    // family layout of the row moments: RR (v <= 2dk), R (v <= dk+db),
+                    // RS (v <= dk), S (v <= db)
+                    T val;
+                    int dst;
+                    if (k < 7) { val = pRR[k]; dst = (k <= 2 * dk) ? ml.fRR + k : -1; }
+                    else if (k < 14) { val = pR[k - 7]; dst = (k - 7 <= dk + db) ? ml.fR + k - 7 : -1; }
+                    else if (k < 18) { val = pRS[k - 14]; dst = (k - 14 <= dk) ? ml.fRS + k - 14 : -1; }
+                    else { val = pS[k - 18]; dst = (k - 18 <= db) ? ml.fS + k - 18 : -1; }
+                    if (dst >= 0) {
+                        Acc<T> a;
+                        a.zero();
+                        a.add(val);
+                        for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
+                        if (lane == 0) red[warp * kMaxMom + dst] = a;
+                    }
+                }
+                __syncthreads();
+                if (tid < ml.n) {
+                    Acc<T> a = red[tid];
+                    for (int w = 1; w < nw; ++w) a.add(red[w * kMaxMom + tid]);
+                    rowmom[(size_t)x0 * ml.n + tid] = a.wide();
+                }
+            }
+            __syncthreads();
+            cpx<T> *res = block_fft(Z + (size_t)r * n1, scr, n1, tw1, n1, -1, tid, nthr);
+            if (res != Z + (size_t)r * n1) {
+                for (int y = tid; y < n1; y += nthr) Z[(size_t)r * n1 + y] = res[y];
+                __syncthreads();
+            }
+        }
+        // separate the two real transforms and write them transposed
+        const int total = h1c * TR;
+        for (int idx = tid; idx < total; idx += nthr) {
+            const int m = idx / TR, r = idx - m * TR;
+            cpx<T> z = Z[(size_t)r * n1 + m];
+            cpx<T> zc = conj(Z[(size_t)r * n1 + (m == 0 ? 0 : n1 - m)]);
+            cpx<T> A = scale(z + zc, (T)0.5);
+            cpx<T> B = mul_i(scale(z - zc, (T)0.5), -1);
+            const size_t o = (size_t)m * n0 + x0b + r;
+            F[(size_t)sa * h1c * n0 + o] = A;
+            if (sb < nseq) F[(size_t)sb * h1c * n0 + o] = B;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mom[k][u] = sum_x0 xt0^u * rowmom[x0][k]   (FP64)
+__global__ void k_moments(int n0, int nmom, const double *__restrict__ rowmom, double *__restrict__ mom) {
+    const int k = blockIdx.x / kUMax, u = blockIdx.x % kUMax;
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < n0; x += blockDim.x) {
+        double xt = coord<double>(x, n0);
+        acc += ipow(xt, u) * rowmom[(size_t)x * nmom + k];
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        mom[(size_t)k * kUMax + u] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass.  Block (m, src): src <= dk is the row transform of yt^src * Rm,
+// src = dk+1 that of Sm.  Output image t = term (i, src) for i <= dk - src, or
+// t = nk for S.  Layout U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
+template <typename T>
+__global__ void k_cols(int n0, int n1, int dk, int na, int nbk, const cpx<T> *__restrict__ F,
+                       cpx<T> *__restrict__ U, const cpx<T> *__restrict__ tw0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int stride = n0 + nbk;
+    cpx<T> *sA = reinterpret_cast<cpx<T> *>(smem_raw);
+    cpx<T> *sB = sA + stride;
+    cpx<T> *sC = sB + stride;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int m = blockIdx.x, src = blockIdx.y;
+    const int h1c = n1 / 2 + 1;
+    const int nk = n_terms(dk);
+    const cpx<T> *col = F + ((size_t)src * h1c + m) * n0;
+    for (int x = tid; x < n0; x += nthr) sA[x] = col[x];
+    __syncthreads();
+    const int ni = (src <= dk) ? (dk - src + 1) : 1;
+    for (int i = 0; i < ni; ++i) {
+        const int t = (src <= dk) ? term_index(i, src) : nk;
+        for (int x = tid; x < n0; x += nthr) {
+            T w = ipow(coord<T>(x, n0), i);
+            sB[x] = scale(sA[x], w);
+        }
+        __syncthreads();
+        cpx<T> *res = block_fft(sB, sC, n0, tw0, n0, -1, tid, nthr);
+        cpx<T> *pad = (res == sB) ? sC : sB;
+        // padded transpose: bin l -> pad[(l % nbk) * (na + 1) + l / nbk]
+        for (int l = tid; l < n0; l += nthr) pad[(l % nbk) * (na + 1) + l / nbk] = res[l];
+        __syncthreads();
+        cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
+        for (int o = tid; o < n0; o += nthr) {
+            const int lb = o / na, r = o - lb * na;
+            out[o] = pad[lb * (na + 1) + r];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather: products and the split pruned inverse DFT along x.
+//
+// NA = 8*G.  Group of G lanes per product; lane r1 holds P(r1 + G*r2) for
+// r2 = 0..7.  Y(s2 + 8*s1) = sum_r1 wG^(r1 s1) w^(r1 s2) sum_r2 w8^(r2 s2) P(r1 + G r2),
+// w = exp(2 pi i / NA): an 8-point DFT in registers, a twiddle, a transpose
+// through shared memory and a G-point DFT.
+template <typename T>
+__device__ __forceinline__ void dft8(cpx<T> (&v)[8], int sgn) {
+    const T c = (T)0.70710678118654752440;
+    cpx<T> a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = v[k] + v[k + 4];
+        b[k] = v[k] - v[k + 4];
+    }
+    // b[k] *= exp(sgn 2 pi i k / 8)
+    b[1] = cmul(b[1], mk(c, sgn * c));
+    b[2] = mul_i(b[2], sgn);
+    b[3] = cmul(b[3], mk(-c, sgn * c));
+    dft4(a[0], a[1], a[2], a[3], sgn);
+    dft4(b[0], b[1], b[2], b[3], sgn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+    }
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void dftG(cpx<T> (&v)[G], int sgn) {
+    if constexpr (G == 1) {
+    } else if constexpr (G == 2) {
+        cpx<T> a = v[0] + v[1], b = v[0] - v[1];
+        v[0] = a;
+        v[1] = b;
+    } else if constexpr (G == 4) {
+        dft4(v[0], v[1], v[2], v[3], sgn);
+    } else {
+        dft8(v, sgn);
+    }
+}
+
+template <typename T, int G, int SLOTS>
+__global__ void k_gather(int n0, int n1, int dk, int db, int nbk, int npairs,
+                         const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
+                         const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
+                         cpx<T> *__restrict__ Q) {
+    constexpr int NA = 8 * G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = n_terms(dk);
+    const int nimg = nk + 1;
+    const int nxp = db + 1;
+    cpx<T> *sU = reinterpret_cast<cpx<T> *>(smem_raw);   // (nimg + nxp) * NA
+    cpx<T> *sT = sU + (size_t)(nimg + nxp) * NA;         // groups * NA (transposes)
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ngroups = nthr / G;
+    const int grp = tid / G, lane = tid - grp * G;
+    const int m = blockIdx.x;
+    const int h1c = n1 / 2 + 1;
+    const size_t colstride = (size_t)h1c * n0;
+
+    PairDesc pd[SLOTS];
+    bool act[SLOTS];
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        int pi = grp + k * ngroups;
+        act[k] = pi < npairs;
+        if (act[k]) pd[k] = pairs[pi];
+        else pd[k].kind = -1;
+    }
+    CAcc<T> acc[SLOTS][8];
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k)
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[k][o].zero();
+
+    cpx<T> *tg = sT + (size_t)grp * NA;
+    for (int lb = 0; lb < nbk; ++lb) {
+        // stage this residue class of every image and of the x^p spectra
+        for (int e = tid; e < (nimg + nxp) * NA; e += nthr) {
+            const int img = e / NA, r = e - img * NA;
+            cpx<T> v;
+            if (img < nimg) v = U[(size_t)img * colstride + (size_t)m * n0 + (size_t)lb * NA + r];
+            else v = xhat[(size_t)(img - nimg) * n0 + (size_t)lb * NA + r];
+            sU[e] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) {
+            // every lane of the warp reaches the __syncwarp calls; only active
+            // groups do the work
+            if (act[k]) {
+                const cpx<T> *A = sU + (size_t)pd[k].a * NA;
+                const cpx<T> *B = (pd[k].kind == PK_LAMBDA) ? sU + (size_t)(nimg + pd[k].b) * NA
+                                                            : sU + (size_t)pd[k].b * NA;
+                cpx<T> v[8];
+#pragma unroll
+                for (int r2 = 0; r2 < 8; ++r2) {
+                    const int r = lane + G * r2;
+                    v[r2] = cmulc(A[r], B[r]);
+                }
+                if (m == 0 && lb == 0 && lane == 0) v[0] = mk((T)0, (T)0);  // DC bin removed
+                dft8(v, 1);
+                // twiddle w^(r1 s2), w = exp(2 pi i / NA): table index r1*s2*(n0/NA)
+#pragma unroll
+                for (int s2 = 1; s2 < 8; ++s2) v[s2] = cmul(v[s2], conj(tw0[(lane * s2) * (n0 / NA)]));
+#pragma unroll
+                for (int s2 = 0; s2 < 8; ++s2) tg[s2 * G + lane] = v[s2];
+            }
+            __syncwarp();
+            if (act[k]) {
+                const int h0 = pd[k].h0;
+                // lane handles s2 = lane + G*c for c < 8/G; G-point DFT over r1
+#pragma unroll
+                for (int c = 0; c < 8 / G; ++c) {
+                    const int s2 = lane + G * c;
+                    cpx<T> u[G];
+#pragma unroll
+                    for (int r1 = 0; r1 < G; ++r1) u[r1] = tg[s2 * G + r1];
+                    dftG<T, G>(u, 1);
+#pragma unroll
+                    for (int s1 = 0; s1 < G; ++s1) {
+                        const int rp = s2 + 8 * s1;  // rho mod NA
+                        int rho;
+                        if (rp <= h0) rho = rp;
+                        else if (rp >= NA - h0) rho = rp - NA;
+                        else continue;
+                        const int q = imod(lb * rho, n0);
+                        acc[k][c * G + s1].add(cmul(u[s1], conj(tw0[q])));
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    // write stage-1 results: row = row0 + rho + h0
+#pragma unroll
+    for (int k = 0; k < SLOTS; ++k) {
+        if (!act[k]) continue;
+#pragma unroll
+        for (int c = 0; c < 8 / G; ++c) {
+            const int s2 = lane + G * c;
+#pragma unroll
+            for (int s1 = 0; s1 < G; ++s1) {
+                const int rp = s2 + 8 * s1;
+                const int h0 = pd[k].h0;
+                int rho;
+                if (rp <= h0) rho = rp;
+                else if (rp >= NA - h0) rho = rp - NA;
+                else continue;
+                const CAcc<T> &a = acc[k][c * G + s1];
+                Q[(size_t)(pd[k].row0 + rho + h0) * h1c + m] = mk((T)a.re.value(), (T)a.im.value());
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: sum over m.  One block per stage-1 row.
+template <typename T>
+__global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npairs,
+                         const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ Q,
+                         const cpx<T> *__restrict__ yhat, const cpx<T> *__restrict__ tw1,
+                         double *__restrict__ lag, int off_om, int off_la, int off_th) {
+    const int row = blockIdx.x;
+    // find the pair of this row
+    int pi = 0;
+    for (int k = 0; k < npairs; ++k)
+        if (row >= pairs[k].row0 && row < pairs[k].row0 + 2 * pairs[k].h0 + 1) pi = k;
+    const PairDesc pd = pairs[pi];
+    const int rho0 = row - pd.row0 - pd.h0;
+    const int h1c = n1 / 2 + 1;
+    const int nk = n_terms(dk);
+    const int nbt = n_terms(db);
+    const int h1 = (pd.kind == PK_OMEGA) ? 2 * w1 : w1;
+    const int nr1 = 2 * h1 + 1;
+    int nq = 1;
+    if (pd.kind == PK_LAMBDA) nq = db - pd.b + 1;  // q = 0..db-p
+    const int nout = nr1 * nq;
+    const cpx<T> *q = Q + (size_t)row * h1c;
+    const double invP = 1.0 / ((double)n0 * (double)n1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = warp; o < nout; o += nw) {
+        const int qi = o / nr1, rho1 = o - qi * nr1 - h1;
+        Acc<T> a;
+        a.zero();
+        for (int mm = lane; mm < h1c; mm += 32) {
+            cpx<T> v = q[mm];
+            if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)qi * h1c + mm]);
+            cpx<T> e = conj(tw1[imod(mm * rho1, n1)]);
+            T wm = (mm == 0 || (2 * mm == n1)) ? (T)1 : (T)2;
+            a.add(wm * (v.re * e.re - v.im * e.im));
+        }
+        for (int s = 16; s > 0; s >>= 1) shfl_add(a, s);
+        if (lane == 0) {
+            double val = a.wide() * invP;
+            size_t idx;
+            if (pd.kind == PK_OMEGA) {
+                // pair index among a <= b
+                const int ia = pd.a, ib = pd.b;
+                const int pidx = ia * nk - ia * (ia - 1) / 2 + (ib - ia);
+                idx = off_om + ((size_t)pidx * (4 * w0 + 1) + (rho0 + 2 * w0)) * (4 * w1 + 1) + (rho1 + 2 * w1);
+            } else if (pd.kind == PK_LAMBDA) {
+                const int s = term_index(pd.b, qi);  // (p, q)
+                idx = off_la + (((size_t)pd.a * nbt + s) * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
+            } else {
+                idx = off_th + ((size_t)pd.a * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
+            }
+            lag[idx] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Assembly of M and rhs (Eq. B5, B7, B9, B11, B13, B15).
+struct Unk {
+    int kern, t, a, b;
+};
+__device__ __forceinline__ Unk decode(int u, int w0, int w1, int nk, int cpr) {
+    const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
+    const int per = cpr ? L - 1 : L;
+    const int ctr = (L - 1) / 2;
+    Unk r;
+    int off;
+    if (u < L) {
+        r.t = 0;
+        off = u;
+    } else if (u - L < (nk - 1) * per) {
+        const int v = u - L;
+        r.t = 1 + v / per;
+        off = v % per;
+        if (cpr && off >= ctr) ++off;
+    } else {
+        r.kern = 0;
+        r.t = u - L - (nk - 1) * per;
+        r.a = r.b = 0;
+        return r;
+    }
+    r.kern = 1;
+    r.a = off / L1 - w0;
+    r.b = off % L1 - w1;
+    return r;
+}
+
+struct LagView {
+    const double *lag;
+    int off_om, off_la, off_th;
+    int w0, w1, nk, nbt;
+    // FFT-derived Omega_{t u}(rho) (DC removed) for any ordered pair
+    __device__ double om(int t, int u, int r0, int r1) const {
+        if (t > u) {
+            int z = t;
+            t = u;
+            u = z;
+            r0 = -r0;
+            r1 = -r1;
+        }
+        const int pidx = t * nk - t * (t - 1) / 2 + (u - t);
+        return lag[off_om + ((size_t)pidx * (4 * w0 + 1) + (r0 + 2 * w0)) * (4 * w1 + 1) + (r1 + 2 * w1)];
+    }
+    __device__ double la(int t, int s, int r0, int r1) const {
+        return lag[off_la + (((size_t)t * nbt + s) * (2 * w0 + 1) + (r0 + w0)) * (2 * w1 + 1) + (r1 + w1)];
+    }
+    __device__ double th(int t, int r0, int r1) const {
+        return lag[off_th + ((size_t)t * (2 * w0 + 1) + (r0 + w0)) * (2 * w1 + 1) + (r1 + w1)];
+    }
+};
+
+__global__ void k_assemble(int n, int w0, int w1, int dk, int db, int cpr, LagView lv,
+                           const double *__restrict__ mom, const double *__restrict__ csum,
+                           double *__restrict__ M, double *__restrict__ rhs) {
+    const MomLayout ml = mom_layout(dk, db);
+    const int nk = n_terms(dk);
+    const size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total + n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        if (e >= total) {  // rhs
+            const int row = (int)(e - total);
+            Unk ur = decode(row, w0, w1, nk, cpr);
+            double v;
+            int i, j;
+            term_ij(ur.t, &i, &j);
+            if (ur.kern) {
+                if (ur.a == 0 && ur.b == 0) v = mom[(size_t)(ml.fRS + j) * kUMax + i];  // Theta(0,0)
+                else v = lv.th(ur.t, ur.a, ur.b) - lv.th(ur.t, 0, 0);
+            } else {
+                v = mom[(size_t)(ml.fS + j) * kUMax + i];  // E (Eq. B15)
+            }
+            rhs[row] = v;
+            continue;
+        }
+        const int row = (int)(e / n), col = (int)(e % n);
+        Unk ur = decode(row, w0, w1, nk, cpr), uc = decode(col, w0, w1, nk, cpr);
+        int ri, rj, ci, cj;
+        term_ij(ur.t, &ri, &rj);
+        term_ij(uc.t, &ci, &cj);
+        double v;
+        if (ur.kern && uc.kern) {
+            const bool rz = (ur.a == 0 && ur.b == 0), cz = (uc.a == 0 && uc.b == 0);
+            if (rz && cz) {
+                v = mom[(size_t)(ml.fRR + rj + cj) * kUMax + (ri + ci)];  // Omega(0,0)
+            } else if (rz) {
+                v = lv.om(ur.t, uc.t, -uc.a, -uc.b) - lv.om(ur.t, uc.t, 0, 0);
+            } else if (cz) {
+                v = lv.om(ur.t, uc.t, ur.a, ur.b) - lv.om(ur.t, uc.t, 0, 0);
+            } else {
+                v = lv.om(ur.t, uc.t, ur.a - uc.a, ur.b - uc.b) - lv.om(ur.t, uc.t, ur.a, ur.b) -
+                    lv.om(ur.t, uc.t, -uc.a, -uc.b) + lv.om(ur.t, uc.t, 0, 0);
+            }
+        } else if (ur.kern) {  // B (Eq. B7)
+            int p, q;
+            term_ij(uc.t, &p, &q);
+            if (ur.a == 0 && ur.b == 0) v = mom[(size_t)(ml.fR + rj + q) * kUMax + (ri + p)];
+            else v = lv.la(ur.t, uc.t, ur.a, ur.b) - lv.la(ur.t, uc.t, 0, 0);
+        } else if (uc.kern) {  // B~ (Eq. B9)
+            int p, q;
+            term_ij(ur.t, &p, &q);
+            if (uc.a == 0 && uc.b == 0) v = mom[(size_t)(ml.fR + cj + q) * kUMax + (ci + p)];
+            else v = lv.la(uc.t, ur.t, uc.a, uc.b) - lv.la(uc.t, ur.t, 0, 0);
+        } else {  // C (Eq. B11): separable sums of coordinate powers
+            int p, q, p2, q2;
+            term_ij(ur.t, &p, &q);
+            term_ij(uc.t, &p2, &q2);
+            v = csum[p + p2] * csum[8 + q + q2];
+        }
+        M[e] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, typename I>
+static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
+                               bool moments, cudaStream_t s) {
+    const int TR = p->fp64 ? 2 : 4;
+    const int nthr = 256;
+    size_t smem = ((size_t)TR + 1) * p->n1 * sizeof(cpx<T>) + (nthr / 32) * kMaxMom * sizeof(Acc<T>);
+    auto kern = k_rows<T, I>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<p->n0 / TR, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, TR, (const I *)ref,
+                                       (const I *)sci, mask, (cpx<T> *)p->F, (const cpx<T> *)p->tw1,
+                                       moments ? 1 : 0, p->rowmom);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_build_rest(Plan *p, double *M, double *rhs, cudaStream_t s) {
+    cudaError_t err;
+    const MomLayout ml = mom_layout(p->cfg.dk, p->cfg.db);
+    k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
+    if ((err = cudaGetLastError())) return err;
+    {
+        size_t smem = 3 * (size_t)(p->n0 + p->nbk) * sizeof(cpx<T>);
+        auto kern = k_cols<T>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        dim3 grid(p->h1c, p->cfg.dk + 2);
+        kern<<<grid, 256, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, (const cpx<T> *)p->F,
+                                     (cpx<T> *)p->U, (const cpx<T> *)p->tw0);
+        if ((err = cudaGetLastError())) return err;
+    }
+    {
+        const int G = p->na / 8;
+        const int nimg = p->nimg, nxp = p->cfg.db + 1;
+        int slots = 1;
+        while (slots < 4 && (p->npairs + slots - 1) / slots > 16) ++slots;
+        int ngroups = (p->npairs + slots - 1) / slots;
+        // threads must fill whole warps
+        int nthr = ngroups * G;
+        nthr = ((nthr + 31) / 32) * 32;
+        ngroups = nthr / G;
+        size_t smem = ((size_t)(nimg + nxp) * p->na + (size_t)ngroups * p->na) * sizeof(cpx<T>);
+        void (*kern)(int, int, int, int, int, int, const PairDesc *, const cpx<T> *, const cpx<T> *,
+                     const cpx<T> *, cpx<T> *) = nullptr;
+#define SFFT_PICK(GG, SS) \
+    if (G == GG && slots == SS) kern = k_gather<T, GG, SS>;
+        SFFT_PICK(8, 1) SFFT_PICK(8, 2) SFFT_PICK(8, 3) SFFT_PICK(8, 4)
+        SFFT_PICK(4, 1) SFFT_PICK(4, 2) SFFT_PICK(4, 3) SFFT_PICK(4, 4)
+        SFFT_PICK(2, 1) SFFT_PICK(2, 2) SFFT_PICK(2, 3) SFFT_PICK(2, 4)
+#undef SFFT_PICK
+        if (!kern) return cudaErrorInvalidValue;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->nbk, p->npairs, p->pairs,
+                                        (const cpx<T> *)p->U, (const cpx<T> *)p->xhat,
+                                        (const cpx<T> *)p->tw0, (cpx<T> *)p->Q);
+        if ((err = cudaGetLastError())) return err;
+    }
+    k_stage2<T><<<p->nrows, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db,
+                                         p->npairs, p->pairs, (const cpx<T> *)p->Q,
+                                         (const cpx<T> *)p->yhat, (const cpx<T> *)p->tw1, p->lag,
+                                         p->lag_om, p->lag_la, p->lag_th);
+    if ((err = cudaGetLastError())) return err;
+    LagView lv;
+    lv.lag = p->lag;
+    lv.off_om = p->lag_om;
+    lv.off_la = p->lag_la;
+    lv.off_th = p->lag_th;
+    lv.w0 = p->cfg.w0;
+    lv.w1 = p->cfg.w1;
+    lv.nk = p->nk;
+    lv.nbt = p->nb;
+    const size_t total = (size_t)p->n * p->n + p->n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db,
+                                      p->cfg.const_phot_ratio, lv, p->mom, p->mom + (size_t)kMaxMom * kUMax,
+                                      M, rhs);
+    return cudaGetLastError();
+}
+
+cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8_t *mask, bool moments,
+                          cudaStream_t s) {
+    const bool img64 = p->cfg.dtype == SFFT_F64;
+    if (p->fp64) {
+        return img64 ? launch_rows<double, double>(p, ref, sci, mask, moments, s)
+                     : launch_rows<double, float>(p, ref, sci, mask, moments, s);
+    }
+    return img64 ? launch_rows<float, double>(p, ref, sci, mask, moments, s)
+                 : launch_rows<float, float>(p, ref, sci, mask, moments, s);
+}
+
+cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M,
+                         double *rhs, cudaStream_t s) {
+    cudaError_t err = row_transform(p, ref, sci, mask, true, s);
+    if (err) return err;
+    return p->fp64 ? launch_build_rest<double>(p, M, rhs, s) : launch_build_rest<float>(p, M, rhs, s);
+}
+
+}  // namespace sfft

@@ -1,0 +1,76 @@
+// internal.h -- plan layout and kernel launchers shared by the SFFT sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sfft.h"
+
+namespace sfft {
+
+// Inner length of the split pruned inverse DFT along x (frequency l = lb + NB*r,
+// r in [0, NA)): min(64, n0).
+constexpr int kMaxNA = 64;
+
+enum PairKind { PK_OMEGA = 0, PK_LAMBDA = 1, PK_THETA = 2 };
+
+// One spectrum product transformed in the gather: conj(U_a) * V_b where V_b
+// is an image spectrum (Omega: b = R-term, Theta: b = S) or the 1-D spectrum
+// of x^p (Lambda).  h0 = lag half-range along x.
+struct PairDesc {
+    int kind, a, b, h0;
+    int row0;  // first row of this pair in the stage-1 table Q[row][m]
+};
+
+struct Plan {
+    sfft_config cfg;
+    int n0, n1, h1c;       // h1c = n1/2 + 1 half-spectrum columns
+    int nk, nb, n;         // kernel terms, background terms, unknowns
+    int L0, L1;            // 2w+1
+    int na, nbk;           // split: n0 = na * nbk
+    int nimg;              // R-terms + S
+    int npairs, nrows;     // gather pairs; stage-1 rows (sum of 2*h0+1)
+    int nmom;              // per-row moment values
+    bool fp64;             // compute in double
+    size_t csz;            // sizeof(cpx<compute type>)
+
+    // device workspace
+    void *tw0, *tw1;       // twiddle tables exp(-2 pi i q / n), length n0 and n1 (compute type)
+    void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
+    void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
+    void *F;               // [(dk+2)][m][x] row transforms (compute type)
+    void *U;               // [nimg][m][lb][r] full spectra, permuted (compute type); reused for Dt
+    void *Q;               // [nrows][m] stage-1 results (compute type complex)
+    PairDesc *pairs;       // device copy
+    double *rowmom;        // [n0][nmom] per-row moment sums
+    double *mom;           // moments table (see build.cu)
+    double *lag;           // lag tables (Omega, Lambda, Theta), FP64
+    int lag_om, lag_la, lag_th;  // offsets into lag
+    // solve workspace
+    void *A;               // n*n factor (compute type)
+    double *dscale;        // n Jacobi scales
+    double *r, *xw;        // n residual, n iterate
+    void *yv, *zv;         // n vectors (compute type)
+    int *flag;             // device status word for the solve
+    // owned buffers for run_pair(_host)
+    double *M_own, *rhs_own, *x_own;
+    sfft_solve_info *info_own;
+    void *img_ref, *img_sci, *img_diff;
+    uint8_t *img_mask;
+    void *kap;             // [nk][L0][m] kernel row spectra (compute type)
+    size_t ws_bytes;
+    cudaStream_t last_stream;
+    PairDesc host_pairs[256];
+};
+
+// launchers (return cudaError_t of the last launch)
+cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M,
+                         double *rhs, cudaStream_t s);
+cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
+                          bool moments, cudaStream_t s);
+cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
+                         sfft_solve_info *info, cudaStream_t s);
+cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s);
+cudaError_t plan_tables(Plan *p, cudaStream_t s);
+
+}  // namespace sfft

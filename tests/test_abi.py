@@ -1,0 +1,58 @@
+"""The C ABI library loads and exports every function include/sfft.h declares.
+
+No GPU: only host-side entry points are called (status strings, unknown counts).
+"""
+import ctypes
+
+import pytest
+
+import oracle
+from paper_2109_09334_gb300 import binding
+from paper_2109_09334_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return binding.library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = binding.declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/sfft.h but not exported"
+
+
+def test_status_strings(lib):
+    for code in range(-8, 1):
+        s = binding.status_string(code)
+        assert isinstance(s, str) and s
+    assert binding.status_string(-4).startswith("normal matrix")
+
+
+@pytest.mark.parametrize("w0,w1,dk,db,cpr", [(4, 4, 0, 0, 1), (6, 6, 1, 1, 0), (8, 8, 2, 2, 1),
+                                             (8, 8, 2, 2, 0), (0, 0, 3, 3, 1), (1, 3, 2, 1, 1)])
+def test_num_unknowns_matches_oracle(lib, w0, w1, dk, db, cpr):
+    cfg = binding.make_config(64, 64, w0, w1, dk, db, cpr)
+    assert binding.sfft_num_unknowns(cfg) == oracle.num_unknowns(oracle.OracleConfig(64, 64, w0, w1, dk, db, cpr))
+
+
+def test_num_unknowns_rejects_negative(lib):
+    cfg = binding.make_config(64, 64, -1, 2, 0, 0, 1)
+    with pytest.raises(binding.SfftError) as e:
+        binding.sfft_num_unknowns(cfg)
+    assert e.value.status == binding.SFFT_ERR_INVALID
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(binding.sfft_config) == 9 * 4
+    assert ctypes.sizeof(binding.sfft_solve_info) == 24
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """The product path has no fallback: without the CUDA library it raises."""
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(ImportError):
+        binding.library()

@@ -1,0 +1,183 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated per result):
+  * plain FP64 path: rel. Frobenius error of M and rhs <= 1e-10, coefficient
+    rel. error <= 1e-8, difference-image RMS deviation <= 1e-6 sigma;
+  * mixed path (FP32 FFTs/products, compensated sums, FP32 Cholesky + FP64
+    refinement): rel. error of M and rhs <= 1e-5; the solver is checked
+    against an FP64 solve of the same GPU-built system (<= 1e-8); the
+    difference image RMS deviation from the oracle's is <= 1e-3 sigma.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import random_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIGMA = 5.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300.build import build
+    build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_run(R, S, w0, w1, dk, db, cpr, precision, dtype, mask=None):
+    from paper_2109_09334_gb300 import SfftPlan, info_from_bytes
+    n0, n1 = R.shape
+    plan = SfftPlan(n0, n1, w0, w1, dk, db, cpr, dtype=dtype, precision=precision)
+    tdt = torch.float32 if dtype == "float32" else torch.float64
+    Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda", tdt)
+    St = torch.from_numpy(np.ascontiguousarray(S)).to("cuda", tdt)
+    mt = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
+    D, x, info, M, rhs = plan.run_pair(Rt, St, mask=mt, keep_system=True)
+    torch.cuda.synchronize()
+    out = dict(D=D.double().cpu().numpy(), x=x.cpu().numpy(), M=M.cpu().numpy(), rhs=rhs.cpu().numpy(),
+               info=info_from_bytes(info.cpu().numpy()), plan=plan, R=Rt, S=St)
+    return out
+
+
+def small_pair(n0, n1, seed):
+    R = random_field(n0, n1, seed)
+    S = 0.8 * np.roll(R, (1, -1), axis=(0, 1)) + 0.3 * random_field(n0, n1, seed + 7)
+    return R, S
+
+
+SMALL = [
+    # n0, n1, w0, w1, dk, db, cpr, masked
+    (16, 16, 1, 1, 0, 0, 1, False),
+    (16, 32, 2, 1, 1, 1, 0, False),
+    (32, 16, 1, 2, 2, 1, 1, True),
+    (64, 64, 3, 3, 1, 2, 1, False),
+    (64, 32, 2, 3, 2, 2, 0, True),
+    (128, 64, 4, 2, 3, 3, 1, False),
+    (64, 128, 5, 6, 0, 3, 1, True),
+    (256, 64, 0, 0, 2, 2, 1, False),
+]
+
+
+@pytest.mark.parametrize("case", SMALL)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_cases_against_oracle(case, precision):
+    n0, n1, w0, w1, dk, db, cpr, masked = case
+    R, S = small_pair(n0, n1, seed=n0 + 3 * n1 + w0)
+    mask = None
+    if masked:
+        mask = (np.random.default_rng(n0).random((n0, n1)) > 0.15).astype(np.uint8)
+    c = oracle.OracleConfig(n0, n1, w0, w1, dk, db, bool(cpr))
+    Mo, ro = oracle.build_system(R, S, c, mask=mask)
+    xo = oracle.cholesky_solve(Mo, ro)
+    Do = oracle.subtract(R, S, xo, c)
+    dtype = "float64" if precision == "fp64" else "float32"
+    g = gpu_run(R, S, w0, w1, dk, db, cpr, precision, dtype, mask)
+    assert g["info"]["status"] == 0, g["info"]
+    if precision == "fp64":
+        assert rel(g["M"], Mo) <= 1e-10
+        assert rel(g["rhs"], ro) <= 1e-10
+        assert rel(g["x"], xo) <= 1e-8
+        assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
+    else:
+        # inputs rounded to float32 on both sides for the system check
+        R32, S32 = R.astype(np.float32).astype(np.float64), S.astype(np.float32).astype(np.float64)
+        Mo32, ro32 = oracle.build_system(R32, S32, c, mask=mask)
+        assert rel(g["M"], Mo32) <= 1e-5
+        assert rel(g["rhs"], ro32) <= 1e-5
+        xs = np.linalg.solve(g["M"], g["rhs"])
+        assert rel(g["x"], xs) <= 1e-8
+        Do32 = oracle.subtract(R32, S32, oracle.cholesky_solve(Mo32, ro32), c)
+        assert np.sqrt(np.mean((g["D"] - Do32) ** 2)) <= 1e-3 * SIGMA
+    g["plan"].close()
+
+
+def test_pair256_fp64_full():
+    """256^2 float64 pair, w=4, D_K=D_B=0, constant ratio (82 unknowns), plain FP64 path."""
+    spec = synth.PAIR256
+    R, S = synth.make_pair(spec, seed=1)
+    f = spec.fit
+    c = oracle.OracleConfig(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio)
+    Mo, ro = oracle.build_system(R, S, c)
+    xo = oracle.cholesky_solve(Mo, ro)
+    Do = oracle.subtract(R, S, xo, c)
+    g = gpu_run(R, S, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, "fp64", "float64")
+    assert g["M"].shape == (82, 82)
+    assert g["info"]["status"] == 0
+    assert rel(g["M"], Mo) <= 1e-10 and rel(g["rhs"], ro) <= 1e-10
+    assert rel(g["x"], xo) <= 1e-8
+    assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
+    g["plan"].close()
+
+
+def test_pair1024_mixed_full():
+    """1024^2 float32 pair, w=6, D_K=D_B=1, varying ratio (510 unknowns), mixed path."""
+    spec = synth.PAIR1024
+    R, S = synth.make_pair(spec, seed=2)
+    f = spec.fit
+    c = oracle.OracleConfig(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio)
+    R64, S64 = R.astype(np.float64), S.astype(np.float64)
+    Mo, ro = oracle.build_system(R64, S64, c)
+    xo = oracle.cholesky_solve(Mo, ro)
+    Do = oracle.subtract(R64, S64, xo, c)
+    g = gpu_run(R, S, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, "mixed", "float32")
+    assert g["M"].shape == (510, 510)
+    assert g["info"]["status"] == 0, g["info"]
+    assert rel(g["M"], Mo) <= 1e-5
+    assert rel(g["rhs"], ro) <= 1e-5
+    assert rel(g["x"], np.linalg.solve(g["M"], g["rhs"])) <= 1e-8
+    assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-3 * SIGMA
+    g["plan"].close()
+
+
+def test_singular_reference_reports_status():
+    """R == 0 makes every kernel column vanish: the solve reports SINGULAR."""
+    R = np.zeros((32, 32))
+    S = random_field(32, 32, 5)
+    g = gpu_run(R, S, 1, 1, 0, 0, 1, "fp64", "float64")
+    assert g["info"]["status"] == -4
+    g["plan"].close()
+
+
+def test_invalid_configs_rejected():
+    from paper_2109_09334_gb300 import SfftError, SfftPlan
+    with pytest.raises(SfftError):
+        SfftPlan(100, 64, 2, 2, 0, 0, 1)        # not a power of two
+    with pytest.raises(SfftError):
+        SfftPlan(64, 64, 16, 2, 0, 0, 1)        # lag range beyond the inner transform
+    with pytest.raises(SfftError):
+        SfftPlan(64, 64, 2, 2, 4, 0, 1)         # D_K > 3
+
+
+def test_host_entry_point_matches_device():
+    R, S = small_pair(64, 64, 9)
+    g = gpu_run(R, S, 2, 2, 1, 1, 1, "mixed", "float32")
+    plan = g["plan"]
+    Rh = torch.from_numpy(R.astype(np.float32)).pin_memory()
+    Sh = torch.from_numpy(S.astype(np.float32)).pin_memory()
+    D, x, info = plan.run_pair_host(Rh, Sh)
+    assert info["status"] == 0
+    np.testing.assert_array_equal(D.double().numpy(), g["D"])
+    np.testing.assert_array_equal(x.numpy(), g["x"])
+    plan.close()
+
+
+def test_mask_of_ones_equals_no_mask_and_repeat_is_bitwise():
+    R, S = small_pair(64, 64, 12)
+    a = gpu_run(R, S, 3, 3, 2, 1, 0, "mixed", "float32")
+    b = gpu_run(R, S, 3, 3, 2, 1, 0, "mixed", "float32", mask=np.ones((64, 64), np.uint8))
+    c = gpu_run(R, S, 3, 3, 2, 1, 0, "mixed", "float32")
+    np.testing.assert_array_equal(a["M"], b["M"])
+    np.testing.assert_array_equal(a["D"], b["D"])
+    np.testing.assert_array_equal(a["M"], c["M"])
+    np.testing.assert_array_equal(a["x"], c["x"])
+    for g in (a, b, c):
+        g["plan"].close()
