@@ -1,0 +1,441 @@
+"""Benchmark: image-pair subtractions/s at 4096^2 through the GB300 SFFT path.
+
+One step = one whole image pair through the hot path (build the system,
+solve it, subtract) on device-resident inputs.  Default workload: the
+4096^2 float32 wide-field pair (20000 sources, w=8, D_K=D_B=2, constant
+photometric ratio, 1735 unknowns), mixed precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: independent pairs per rank (replicas, weak scaling, no
+collective on the data path); value = all pairs / max time over ranks.
+The reference arm times the FP64 CPU oracle on the host cores.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "image-pair subtractions/s at 4096^2 (build + solve + subtract)"
+UNIT = "pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pair4096")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stages", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(spec, precision):
+    f = spec.fit
+    return {"workload": f"{spec.name}: {spec.n0}x{spec.n1} {spec.dtype} pair, {spec.n_src} sources, "
+                        f"w={f.w0}, D_K={f.dk}, D_B={f.db}, const_phot_ratio={f.const_phot_ratio}",
+            "image": [spec.n0, spec.n1], "w": f.w0, "dk": f.dk, "db": f.db,
+            "const_phot_ratio": f.const_phot_ratio, "precision": precision,
+            "l2": "not flushed: each step touches ~1.3 GB (inputs 134 MB + workspace), > 129 MB L2; "
+                  "two input pairs alternate"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample: central crop with the same fit parameters)
+
+def oracle_sample(R, S, spec, crop):
+    import numpy as np
+    import oracle
+    n0, n1 = spec.n0, spec.n1
+    c0, c1 = (n0 - crop) // 2, (n1 - crop) // 2
+    Rc = np.ascontiguousarray(R[c0:c0 + crop, c1:c1 + crop], dtype=np.float64)
+    Sc = np.ascontiguousarray(S[c0:c0 + crop, c1:c1 + crop], dtype=np.float64)
+    f = spec.fit
+    cfg = oracle.OracleConfig(crop, crop, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio)
+    t0 = time.perf_counter()
+    M, rhs = oracle.build_system(Rc, Sc, cfg)
+    t1 = time.perf_counter()
+    x = oracle.cholesky_solve(M, rhs)
+    t2 = time.perf_counter()
+    oracle.subtract(Rc, Sc, x, cfg)
+    t3 = time.perf_counter()
+    scale = (n0 * n1) / float(crop * crop)
+    # lag sums and the stencil scale with the pixel count; the n x n solve does not
+    full = scale * ((t1 - t0) + (t3 - t2)) + (t2 - t1)
+    return {"t_build": t1 - t0, "t_solve": t2 - t1, "t_sub": t3 - t2, "scale": scale, "t_pair": full}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# per-stage algorithmic bytes (compulsory reads + writes of each stage's kernels)
+
+def stage_bytes(spec, n):
+    f = spec.fit
+    P = spec.n0 * spec.n1
+    H = (spec.n1 // 2 + 1) * spec.n0
+    c = 8                                  # FP32 complex
+    b = 4 if spec.dtype == "float32" else 8
+    nk = (f.dk + 1) * (f.dk + 2) // 2
+    nimg = nk + 1
+    nrows = (nk * (nk + 1) // 2) * (4 * f.w0 + 1) + nk * (f.db + 1) * (2 * f.w0 + 1) + nk * (2 * f.w0 + 1)
+    h1c = spec.n1 // 2 + 1
+    return {
+        "rows": 2 * P * b + (f.dk + 2) * H * c,
+        "cols": (f.dk + 2) * H * c + nimg * H * c,
+        "gather": nimg * H * c + nrows * h1c * c,
+        "lags": nrows * h1c * c + n * n * 8,
+        "solve": 2 * n * n * 8,
+        "subtract": (f.dk + 2) * H * c + 2 * H * c + P * b,
+    }
+
+
+def stage_flops(spec, n):
+    """Arithmetic of each stage in FP32 operations (an FMA counts 2)."""
+    import math
+    f = spec.fit
+    n0, n1 = spec.n0, spec.n1
+    h1c = n1 // 2 + 1
+    nk = (f.dk + 1) * (f.dk + 2) // 2
+    nimg = nk + 1
+    na = min(64, n0)
+    units = h1c * (n0 // na)
+    n_om = nk * (nk + 1) // 2
+    n_other = nk * (f.db + 1) + nk
+    # per pair and residue class: products, two 8-point DFTs, twiddles, compensated outer sums
+    per_unit = lambda lags: na * 6 + 2 * 60 * (na // 8) + 7 * 6 * (na // 8) + lags * 18
+    nfft_rows = (f.dk + 3) // 2
+    return {
+        "rows": n0 * nfft_rows * 5 * n1 * math.log2(n1) + 60 * n0 * n1,
+        "cols": h1c * nimg * 5 * n0 * math.log2(n0),
+        "gather": units * (n_om * per_unit(4 * f.w0 + 1) + n_other * per_unit(2 * f.w0 + 1)),
+        "lags": 0.0,
+        "solve": n ** 3 / 3.0,
+        "subtract": h1c * n0 * nk * (2 * f.w0 + 1) * 8 + (n0 // 2) * 5 * n1 * math.log2(n1),
+    }
+
+
+def fp32_peak_tflops(sm_mhz):
+    """CUDA-core FP32 peak: 152 SMs x 128 lanes x 2 (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def survey_alg_bytes(spec):
+    """Bytes the method itself must move per pair: read R, S once, write and read
+    each forward spectrum once, read the R and S spectra again, write D."""
+    f = spec.fit
+    P = spec.n0 * spec.n1
+    H = (spec.n1 // 2 + 1) * spec.n0
+    b = 4 if spec.dtype == "float32" else 8
+    nk = (f.dk + 1) * (f.dk + 2) // 2
+    nb = (f.db + 1) * (f.db + 2) // 2
+    return 3 * b * P + 2 * b * H * (3 * (nk + 1) + nb)
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if its source hash matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    if ent.get("source_sha") != source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2109_09334_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synth
+    from paper_2109_09334_gb300 import SfftPlan, binding
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    spec = synth.SPECS[args.workload]
+    f = spec.fit
+    # two distinct input pairs per rank (seeded by rank) alternate between steps
+    pairs = [synth.make_pair(spec, seed=100 + 2 * rank + k) for k in range(2)]
+    plan = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
+                    precision=args.precision)
+    stream = plan.stream
+    dev_pairs = [(torch.from_numpy(R).to(dev), torch.from_numpy(S).to(dev)) for R, S in pairs]
+    D = torch.empty((spec.n0, spec.n1), dtype=dev_pairs[0][0].dtype, device=dev)
+    x = torch.empty(plan.n, dtype=torch.float64, device=dev)
+    info = torch.zeros(24, dtype=torch.uint8, device=dev)
+
+    def step(k):
+        Rt, St = dev_pairs[k & 1]
+        binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, x, info, D, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    from paper_2109_09334_gb300 import info_from_bytes
+    inf = info_from_bytes(info.cpu().numpy())
+    if inf["status"] != 0:
+        raise RuntimeError(f"solve status {inf}")
+
+    bus = None
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = binding.sfft_plan_launch_count(plan.handle)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.25)
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step(k)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = binding.sfft_plan_launch_count(plan.handle) - launches0
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+    P = spec.n0 * spec.n1
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+              "data": "synthetic (seeded star fields shaped like the paper's wide-field pairs)",
+              "config": workload_config(spec, args.precision), "gpu_launches": int(launches),
+              "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                         "reasons": clocks["reasons"], "samples": clocks["samples"]},
+              "mpix_per_s": value * P / 1e6,
+              "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+              "solve": inf}
+
+    # per-stage times: replay each stage of the last pair with events on the plan's stream
+    if not args.no_stages:
+        reps = 20
+        stage_ms = {}
+        for sid, name in enumerate(binding.STAGE_NAMES):
+            binding.sfft_replay_stage(plan.handle, sid, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                binding.sfft_replay_stage(plan.handle, sid, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            stage_ms[name] = e0.elapsed_time(e1) / reps
+        # restore a consistent state for the e2e run
+        step(0)
+        torch.cuda.synchronize()
+        sb = stage_bytes(spec, plan.n)
+        peak, peak_kind = measured_peaks()
+        top = max(stage_ms, key=stage_ms.get)
+        tot = sum(stage_ms.values())
+        result["stages_ms"] = {k: round(v, 4) for k, v in stage_ms.items()}
+        result["stages_share"] = {k: round(v / tot, 3) for k, v in stage_ms.items()}
+        kern = {"rows": "k_rows", "cols": "k_cols", "gather": "k_gather", "lags": "k_stage2",
+                "solve": "Cholesky + refinement kernels", "subtract": "k_sub_cols + k_rows_inv"}[top]
+        sf = stage_flops(spec, plan.n)
+        clk = clocks["sm_max_mhz"] or 2070.0
+        alu_peak = fp32_peak_tflops(clk)
+        t_s = stage_ms[top] / 1e3
+        t_hbm = sb[top] / (peak * 1e9)
+        t_alu = sf[top] / (alu_peak * 1e12)
+        if t_hbm >= t_alu:
+            ach = sb[top] / t_s / 1e9
+            result["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak, "traffic": load_traffic(kern), "kernel": kern,
+                                  "stage": top, "alg_bytes_per_launch": sb[top],
+                                  "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"}
+        else:
+            ach = sf[top] / t_s / 1e12
+            result["roofline"] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                                  "frac": ach / alu_peak, "traffic": load_traffic(kern), "kernel": kern,
+                                  "stage": top, "alg_flops_per_launch": sf[top], "alg_bytes_per_launch": sb[top],
+                                  "peak_source": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {clk:.0f} MHz"}
+        ba = survey_alg_bytes(spec)
+        result["pair_roofline"] = {"alg_bytes_per_pair": ba, "achieved_GBs": ba / (ms_step / 1e3) / 1e9,
+                                   "frac": ba / (ms_step / 1e3) / 1e9 / peak}
+
+    # end to end through the host entry point: pinned host buffers, copies inside the timed region
+    if not args.no_e2e:
+        Rh = torch.from_numpy(pairs[0][0]).pin_memory()
+        Sh = torch.from_numpy(pairs[0][1]).pin_memory()
+        Dh = torch.empty((spec.n0, spec.n1), dtype=Rh.dtype).pin_memory()
+        xh = torch.empty(plan.n, dtype=torch.float64).pin_memory()
+        plan.run_pair_host(Rh, Sh, x_out=xh, diff_out=Dh)
+        ke = max(3, min(args.steps, 30))
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            _, _, inf2 = plan.run_pair_host(Rh, Sh, x_out=xh, diff_out=Dh)
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        bi = Rh.numel() * Rh.element_size() * 2
+        bo = Dh.numel() * Dh.element_size() + xh.numel() * 8 + 24
+        result["e2e"] = {"value": world * ke / te, "unit": UNIT, "h2d_bytes_per_step": bi,
+                         "d2h_bytes_per_step": bo, "steps": ke}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        R, S = pairs[0]
+        smp = oracle_sample(R, S, spec, crop=1024 if spec.n0 >= 2048 else spec.n0)
+        result["cpu_baseline"] = {"value": 1.0 / smp["t_pair"], "unit": UNIT, "cores": oracle.threads(),
+                                  "kind": "oracle",
+                                  "sample": f"FP64 oracle build + Cholesky + subtract on the central "
+                                            f"{int(round((spec.n0 * spec.n1 / smp['scale']) ** 0.5))}^2 crop "
+                                            f"with the same fit (n={plan.n}); lag-sum and stencil time scaled "
+                                            f"x{smp['scale']:.0f} by pixel count, solve time as measured",
+                                  "t_sample_s": round(smp["t_build"] + smp["t_solve"] + smp["t_sub"], 2)}
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    spec = synth.SPECS[args.workload]
+    R, S = synth.make_pair(spec, seed=100)
+    crop = 256 if spec.n0 >= 512 else spec.n0
+    for _ in range(args.warmup):
+        oracle_sample(R, S, spec, crop)
+    times = []
+    for _ in range(args.steps):
+        times.append(oracle_sample(R, S, spec, crop)["t_pair"])
+    t = float(np.mean(times))
+    value = 1.0 / t
+    sample = (f"FP64 oracle build + Cholesky + subtract on the central {crop}^2 crop with the same fit; "
+              f"lag-sum and stencil time scaled x{spec.n0 * spec.n1 // (crop * crop)} by pixel count")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(spec, "fp64 oracle"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

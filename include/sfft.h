@@ -68,7 +68,7 @@ typedef enum {
 
 /* Fit parameters of one image pair (Sec. 3.3 and Table A1). */
 typedef struct {
-    int32_t n0, n1;           /* image size; each a power of two in [16, 8192] */
+    int32_t n0, n1;           /* image size; each a power of two in [16, 4096] */
     int32_t w0, w1;           /* kernel half-widths: L0 = 2*w0+1, L1 = 2*w1+1 (Eq. 3-4) */
     int32_t dk;               /* kernel polynomial degree D_K (Eq. 6), 0..3 */
     int32_t db;               /* background polynomial degree D_B (Eq. 2), 0..3 */
@@ -166,6 +166,31 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci,
 int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci,
                        const uint8_t *h_mask, double *h_x, sfft_solve_info *h_info,
                        void *h_diff, sfft_stream_t stream);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+/* Stages of one pair, as re-enqueued by sfft_replay_stage. */
+typedef enum {
+    SFFT_STAGE_ROWS = 0,     /* masked row FFTs of yt^j R and S, per-row moments */
+    SFFT_STAGE_COLS = 1,     /* moment sums and column FFTs of xt^i (row transforms) */
+    SFFT_STAGE_GATHER = 2,   /* spectrum products and pruned inverse DFT along x */
+    SFFT_STAGE_LAGS = 3,     /* frequency sums along y to the lag tables; assembly of M, rhs */
+    SFFT_STAGE_SOLVE = 4,    /* Cholesky and refinement */
+    SFFT_STAGE_SUBTRACT = 5  /* the difference image (after a masked build, preceded by
+                                the row FFTs of the unmasked pair) */
+} sfft_stage;
+
+/* Number of kernels this plan has enqueued since it was created. */
+int sfft_plan_launch_count(sfft_plan_t plan, uint64_t *count);
+
+/*
+ * Enqueue one stage of the most recent sfft_run_pair on this plan again, on
+ * the same buffers (which must still be valid), for timing a stage alone.
+ * Stages after the replayed one are not re-run; a replayed stage overwrites
+ * the same intermediate and output buffers with the same values.
+ * SFFT_ERR_INVALID if no pair has run on the plan or stage is unknown.
+ */
+int sfft_replay_stage(sfft_plan_t plan, int stage, sfft_stream_t stream);
 
 #ifdef __cplusplus
 }

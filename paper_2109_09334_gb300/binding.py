@@ -24,6 +24,8 @@ SFFT_ERR_BUSY = -7
 SFFT_ERR_UNSUPPORTED = -8
 
 SFFT_F32, SFFT_F64 = 0, 1
+SFFT_STAGE_ROWS, SFFT_STAGE_COLS, SFFT_STAGE_GATHER, SFFT_STAGE_LAGS, SFFT_STAGE_SOLVE, SFFT_STAGE_SUBTRACT = range(6)
+STAGE_NAMES = ["rows", "cols", "gather", "lags", "solve", "subtract"]
 SFFT_PREC_FP64, SFFT_PREC_MIXED = 0, 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sfft.h")
@@ -67,6 +69,8 @@ def library():
         lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
         _lib = lib
     return _lib
 
@@ -158,3 +162,13 @@ def sfft_run_pair(plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, s
 def sfft_run_pair_host(plan, h_ref, h_sci, h_mask, h_x, h_info, h_diff, stream=None):
     _check(library().sfft_run_pair_host(plan, _p(h_ref), _p(h_sci), _p(h_mask), _p(h_x), _p(h_info),
                                         _p(h_diff), _s(stream)), "sfft_run_pair_host")
+
+
+def sfft_plan_launch_count(plan):
+    c = ctypes.c_uint64()
+    _check(library().sfft_plan_launch_count(plan, ctypes.byref(c)), "sfft_plan_launch_count")
+    return c.value
+
+
+def sfft_replay_stage(plan, stage, stream=None):
+    _check(library().sfft_replay_stage(plan, int(stage), _s(stream)), "sfft_replay_stage")

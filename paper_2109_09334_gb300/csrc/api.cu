@@ -70,7 +70,7 @@ static int unknowns(const sfft_config *c) {
 
 static void free_plan(Plan *p) {
     void *bufs[] = {p->tw0, p->tw1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
-                    p->lag, p->A, p->dscale, p->r, p->xw, p->yv, p->zv, p->flag, p->M_own, p->rhs_own,
+                    p->lag, p->A, p->Wm, p->Tm, p->dscale, p->r, p->xw, p->yv, p->zv, p->flag, p->M_own, p->rhs_own,
                     p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -153,11 +153,18 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->mom, (size_t)(24 * 7 + 16) * sizeof(double));
     SFFT_ALLOC(p->lag, nlag * sizeof(double));
     SFFT_ALLOC(p->A, n * n * rsz);
+    SFFT_ALLOC(p->Wm, n * n * rsz);
+    SFFT_ALLOC(p->Tm, n * n * rsz);
+    p->solve_grid = solve_grid_size(p->fp64);
+    if (p->solve_grid <= 0 || p->solve_grid > 256) {
+        free_plan(p);
+        return SFFT_ERR_CUDA;
+    }
     SFFT_ALLOC(p->dscale, n * sizeof(double));
     SFFT_ALLOC(p->r, n * sizeof(double));
-    SFFT_ALLOC(p->xw, (n + 600) * sizeof(double));
-    SFFT_ALLOC(p->yv, n * rsz);
-    SFFT_ALLOC(p->zv, n * rsz);
+    SFFT_ALLOC(p->xw, (n + 800) * sizeof(double));  // x, stats, per-block partials, kernel sums
+    SFFT_ALLOC(p->yv, (size_t)((n + 31) / 32) * 32 * 32 * rsz);  // diagonal-block inverses
+    SFFT_ALLOC(p->zv, solve_vec_elems((int)n) * rsz);
     SFFT_ALLOC(p->flag, 4 * sizeof(int));
     SFFT_ALLOC(p->M_own, n * n * sizeof(double));
     SFFT_ALLOC(p->rhs_own, n * sizeof(double));
@@ -234,6 +241,14 @@ static int run_pair(Plan *p, const void *ref, const void *sci, const uint8_t *ma
     if (!rhs) rhs = p->rhs_own;
     if (!x) x = p->x_own;
     if (!info) info = p->info_own;
+    p->last_ref = ref;
+    p->last_sci = sci;
+    p->last_mask = mask;
+    p->last_M = M;
+    p->last_rhs = rhs;
+    p->last_x = x;
+    p->last_info = info;
+    p->last_diff = diff;
     cudaError_t e = build_system(p, ref, sci, mask, M, rhs, s);
     if (e == cudaSuccess) e = solve_system(p, M, rhs, x, info, s);
     if (e == cudaSuccess && mask) e = row_transform(p, ref, sci, nullptr, false, s);
@@ -293,6 +308,34 @@ int sfft_plan_workspace_bytes(sfft_plan_t plan, uint64_t *bytes) {
     if (!plan || !bytes) return SFFT_ERR_INVALID;
     *bytes = ((Plan *)plan)->ws_bytes;
     return SFFT_OK;
+}
+
+int sfft_plan_launch_count(sfft_plan_t plan, uint64_t *count) {
+    if (!plan || !count) return SFFT_ERR_INVALID;
+    *count = ((Plan *)plan)->launches;
+    return SFFT_OK;
+}
+
+int sfft_replay_stage(sfft_plan_t plan, int stage, sfft_stream_t stream) {
+    if (!plan) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    if (!p->last_ref || !p->last_diff) return SFFT_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    cudaError_t e;
+    switch (stage) {
+        case SFFT_STAGE_ROWS: e = row_transform(p, p->last_ref, p->last_sci, p->last_mask, true, s); break;
+        case SFFT_STAGE_COLS:
+        case SFFT_STAGE_GATHER:
+        case SFFT_STAGE_LAGS: e = build_stage(p, stage, p->last_M, p->last_rhs, s); break;
+        case SFFT_STAGE_SOLVE: e = solve_system(p, p->last_M, p->last_rhs, p->last_x, p->last_info, s); break;
+        case SFFT_STAGE_SUBTRACT:  // as in sfft_run_pair: unmasked row FFTs only after a masked build
+            e = p->last_mask ? row_transform(p, p->last_ref, p->last_sci, nullptr, false, s) : cudaSuccess;
+            if (e == cudaSuccess) e = subtract_from_rows(p, p->last_x, p->last_diff, s);
+            break;
+        default: return SFFT_ERR_INVALID;
+    }
+    return status_of(e);
 }
 
 int sfft_build_system(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask,

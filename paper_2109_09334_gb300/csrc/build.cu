@@ -254,118 +254,170 @@ __device__ __forceinline__ void dftG(cpx<T> (&v)[G], int sgn) {
     }
 }
 
-template <typename T, int G, int SLOTS>
-__global__ void k_gather(int n0, int n1, int dk, int db, int nbk, int npairs,
-                         const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
-                         const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
-                         cpx<T> *__restrict__ Q) {
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// One block per column m; one group of G lanes per spectrum product.  The
+// residue-class tiles (NA bins of every image and of the x^p spectra) are
+// double-buffered in shared memory with cp.async; image tiles are padded so
+// that the groups of a warp read different banks, and the 8x8 transposes are
+// XOR-swizzled.  Outer twiddles exp(2 pi i lb rho / N0) come from a per-block
+// shared table.  Each output keeps a plain FP32 partial over kFold residue
+// classes that is folded into a two-sum accumulator.
+constexpr int kPad = 8;   // complex elements of padding per image tile / transpose region
+constexpr int kFold = 4;  // residue classes per plain partial sum
+
+// NS output slots per lane: 8 in general; 5 when every lag half-range is at most
+// 16 and G = 8 (then only s1 in {0, 1, 2, 6, 7} can be needed).
+template <int G, int NS>
+__device__ __forceinline__ int out_slot(int c, int s1) {
+    if constexpr (NS == 8) return c * G + s1;
+    else return s1 < 3 ? s1 : (s1 >= 6 ? s1 - 3 : -1);
+}
+
+template <typename T, int G, int NS>
+__global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_gather(int n0, int n1, int dk, int db, int nbk, int npairs, int hmax,
+                                                const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
+                                                const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
+                                                cpx<T> *__restrict__ Q) {
     constexpr int NA = 8 * G;
+    constexpr int NAP = NA + kPad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = n_terms(dk);
     const int nimg = nk + 1;
     const int nxp = db + 1;
-    cpx<T> *sU = reinterpret_cast<cpx<T> *>(smem_raw);   // (nimg + nxp) * NA
-    cpx<T> *sT = sU + (size_t)(nimg + nxp) * NA;         // groups * NA (transposes)
+    const int tile = (nimg + nxp) * NAP;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ngroups = nthr / G;
+    cpx<T> *sU = reinterpret_cast<cpx<T> *>(smem_raw);  // 2 * tile (double buffer)
+    cpx<T> *sT = sU + 2 * (size_t)tile;                 // ngroups * NAP (transposes)
+    cpx<T> *sW = sT + (size_t)ngroups * NAP;            // nbk * (2 hmax + 1) outer twiddles
     const int grp = tid / G, lane = tid - grp * G;
     const int m = blockIdx.x;
     const int h1c = n1 / 2 + 1;
     const size_t colstride = (size_t)h1c * n0;
-
-    PairDesc pd[SLOTS];
-    bool act[SLOTS];
-#pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        int pi = grp + k * ngroups;
-        act[k] = pi < npairs;
-        if (act[k]) pd[k] = pairs[pi];
-        else pd[k].kind = -1;
+    const int pidx = blockIdx.y * ngroups + grp;  // products split over blockIdx.y chunks
+    const bool act = pidx < npairs;
+    PairDesc pd;
+    if (act) pd = pairs[pidx];
+    else {
+        pd.kind = 0;
+        pd.a = pd.b = pd.h0 = pd.row0 = 0;
     }
-    CAcc<T> acc[SLOTS][8];
+    const int h0 = pd.h0;
+    const int wrow = 2 * hmax + 1;
+    for (int e = tid; e < nbk * wrow; e += nthr) {
+        const int lb = e / wrow, rho = e - lb * wrow - hmax;
+        sW[e] = conj(tw0[(lb * rho) & (n0 - 1)]);
+    }
+    // inner twiddles w^(r1 s2), w = exp(2 pi i / NA), for this lane (r1 = lane)
+    cpx<T> wi[8];
 #pragma unroll
-    for (int k = 0; k < SLOTS; ++k)
+    for (int s2 = 0; s2 < 8; ++s2) wi[s2] = conj(tw0[(lane * s2) * (n0 / NA)]);
+    CAcc<T> acc[NS];
+    cpx<T> part[NS];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) acc[k][o].zero();
-
-    cpx<T> *tg = sT + (size_t)grp * NA;
+    for (int o = 0; o < NS; ++o) {
+        acc[o].zero();
+        part[o] = mk((T)0, (T)0);
+    }
+    cpx<T> *tg = sT + (size_t)grp * NAP;
+    constexpr int kPer16 = 16 / (int)sizeof(cpx<T>);
+    constexpr int kChunksPerImg = NA / kPer16;
+    const int chunks = (nimg + nxp) * kChunksPerImg;
+    auto prefetch = [&](int lb, int buf) {
+        cpx<T> *dst = sU + (size_t)buf * tile;
+        for (int c = tid; c < chunks; c += nthr) {
+            const int img = c / kChunksPerImg, r = (c - img * kChunksPerImg) * kPer16;
+            const cpx<T> *src = (img < nimg) ? U + (size_t)img * colstride + (size_t)m * n0 + (size_t)lb * NA + r
+                                             : xhat + (size_t)(img - nimg) * n0 + (size_t)lb * NA + r;
+            cp_async16(dst + (size_t)img * NAP + r, src);
+        }
+        cp_async_commit();
+    };
+    prefetch(0, 0);
     for (int lb = 0; lb < nbk; ++lb) {
-        // stage this residue class of every image and of the x^p spectra
-        for (int e = tid; e < (nimg + nxp) * NA; e += nthr) {
-            const int img = e / NA, r = e - img * NA;
-            cpx<T> v;
-            if (img < nimg) v = U[(size_t)img * colstride + (size_t)m * n0 + (size_t)lb * NA + r];
-            else v = xhat[(size_t)(img - nimg) * n0 + (size_t)lb * NA + r];
-            sU[e] = v;
+        if (lb + 1 < nbk) {
+            prefetch(lb + 1, (lb + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const cpx<T> *buf = sU + (size_t)(lb & 1) * tile;
+        if (act) {
+            const cpx<T> *A = buf + (size_t)pd.a * NAP;
+            const cpx<T> *B = (pd.kind == PK_LAMBDA) ? buf + (size_t)(nimg + pd.b) * NAP : buf + (size_t)pd.b * NAP;
+            cpx<T> v[8];
 #pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-            // every lane of the warp reaches the __syncwarp calls; only active
-            // groups do the work
-            if (act[k]) {
-                const cpx<T> *A = sU + (size_t)pd[k].a * NA;
-                const cpx<T> *B = (pd[k].kind == PK_LAMBDA) ? sU + (size_t)(nimg + pd[k].b) * NA
-                                                            : sU + (size_t)pd[k].b * NA;
-                cpx<T> v[8];
+            for (int r2 = 0; r2 < 8; ++r2) {
+                const int r = lane + G * r2;
+                v[r2] = cmulc(A[r], B[r]);
+            }
+            if (m == 0 && lb == 0 && lane == 0) v[0] = mk((T)0, (T)0);  // DC bin removed
+            dft8(v, 1);
 #pragma unroll
-                for (int r2 = 0; r2 < 8; ++r2) {
-                    const int r = lane + G * r2;
-                    v[r2] = cmulc(A[r], B[r]);
-                }
-                if (m == 0 && lb == 0 && lane == 0) v[0] = mk((T)0, (T)0);  // DC bin removed
-                dft8(v, 1);
-                // twiddle w^(r1 s2), w = exp(2 pi i / NA): table index r1*s2*(n0/NA)
+            for (int s2 = 1; s2 < 8; ++s2) v[s2] = cmul(v[s2], wi[s2]);
+            if (G == 8) {
 #pragma unroll
-                for (int s2 = 1; s2 < 8; ++s2) v[s2] = cmul(v[s2], conj(tw0[(lane * s2) * (n0 / NA)]));
+                for (int s2 = 0; s2 < 8; ++s2) tg[s2 * 8 + (lane ^ s2)] = v[s2];
+            } else {
 #pragma unroll
                 for (int s2 = 0; s2 < 8; ++s2) tg[s2 * G + lane] = v[s2];
             }
-            __syncwarp();
-            if (act[k]) {
-                const int h0 = pd[k].h0;
-                // lane handles s2 = lane + G*c for c < 8/G; G-point DFT over r1
+        }
+        __syncwarp();
+        if (act) {
+            const cpx<T> *wrow_lb = sW + (size_t)lb * wrow + hmax;
+            // lane handles s2 = lane + G*c for c < 8/G; G-point DFT over r1
 #pragma unroll
-                for (int c = 0; c < 8 / G; ++c) {
-                    const int s2 = lane + G * c;
-                    cpx<T> u[G];
+            for (int c = 0; c < 8 / G; ++c) {
+                const int s2 = lane + G * c;
+                cpx<T> u[G];
 #pragma unroll
-                    for (int r1 = 0; r1 < G; ++r1) u[r1] = tg[s2 * G + r1];
-                    dftG<T, G>(u, 1);
+                for (int r1 = 0; r1 < G; ++r1) u[r1] = (G == 8) ? tg[s2 * 8 + (r1 ^ s2)] : tg[s2 * G + r1];
+                dftG<T, G>(u, 1);
 #pragma unroll
-                    for (int s1 = 0; s1 < G; ++s1) {
-                        const int rp = s2 + 8 * s1;  // rho mod NA
-                        int rho;
-                        if (rp <= h0) rho = rp;
-                        else if (rp >= NA - h0) rho = rp - NA;
-                        else continue;
-                        const int q = imod(lb * rho, n0);
-                        acc[k][c * G + s1].add(cmul(u[s1], conj(tw0[q])));
-                    }
+                for (int s1 = 0; s1 < G; ++s1) {
+                    const int rp = s2 + 8 * s1;  // rho mod NA
+                    int rho;
+                    if (rp <= h0) rho = rp;
+                    else if (rp >= NA - h0) rho = rp - NA;
+                    else continue;
+                    const int o = out_slot<G, NS>(c, s1);
+                    if (o >= 0) part[o] = part[o] + cmul(u[s1], wrow_lb[rho]);
                 }
             }
-            __syncwarp();
-        }
-        __syncthreads();
-    }
-    // write stage-1 results: row = row0 + rho + h0
+            if ((lb % kFold) == kFold - 1 || lb == nbk - 1) {
 #pragma unroll
-    for (int k = 0; k < SLOTS; ++k) {
-        if (!act[k]) continue;
-#pragma unroll
-        for (int c = 0; c < 8 / G; ++c) {
-            const int s2 = lane + G * c;
-#pragma unroll
-            for (int s1 = 0; s1 < G; ++s1) {
-                const int rp = s2 + 8 * s1;
-                const int h0 = pd[k].h0;
-                int rho;
-                if (rp <= h0) rho = rp;
-                else if (rp >= NA - h0) rho = rp - NA;
-                else continue;
-                const CAcc<T> &a = acc[k][c * G + s1];
-                Q[(size_t)(pd[k].row0 + rho + h0) * h1c + m] = mk((T)a.re.value(), (T)a.im.value());
+                for (int o = 0; o < NS; ++o) {
+                    acc[o].add(part[o]);
+                    part[o] = mk((T)0, (T)0);
+                }
             }
+        }
+        __syncthreads();  // the buffer of this step is refilled two steps later
+    }
+    if (!act) return;
+#pragma unroll
+    for (int c = 0; c < 8 / G; ++c) {
+        const int s2 = lane + G * c;
+#pragma unroll
+        for (int s1 = 0; s1 < G; ++s1) {
+            const int rp = s2 + 8 * s1;
+            int rho;
+            if (rp <= h0) rho = rp;
+            else if (rp >= NA - h0) rho = rp - NA;
+            else continue;
+            const int o = out_slot<G, NS>(c, s1);
+            if (o < 0) continue;
+            const CAcc<T> &a = acc[o];
+            Q[(size_t)(pd.row0 + rho + h0) * h1c + m] = mk((T)a.re.value(), (T)a.im.value());
         }
     }
 }
@@ -554,54 +606,63 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     kern<<<p->n0 / TR, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, TR, (const I *)ref,
                                        (const I *)sci, mask, (cpx<T> *)p->F, (const cpx<T> *)p->tw1,
                                        moments ? 1 : 0, p->rowmom);
+    p->launches++;
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_build_rest(Plan *p, double *M, double *rhs, cudaStream_t s) {
-    cudaError_t err;
+static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     const MomLayout ml = mom_layout(p->cfg.dk, p->cfg.db);
     k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
-    if ((err = cudaGetLastError())) return err;
-    {
-        size_t smem = 3 * (size_t)(p->n0 + p->nbk) * sizeof(cpx<T>);
-        auto kern = k_cols<T>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        dim3 grid(p->h1c, p->cfg.dk + 2);
-        kern<<<grid, 256, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, (const cpx<T> *)p->F,
-                                     (cpx<T> *)p->U, (const cpx<T> *)p->tw0);
-        if ((err = cudaGetLastError())) return err;
-    }
-    {
-        const int G = p->na / 8;
-        const int nimg = p->nimg, nxp = p->cfg.db + 1;
-        int slots = 1;
-        while (slots < 4 && (p->npairs + slots - 1) / slots > 16) ++slots;
-        int ngroups = (p->npairs + slots - 1) / slots;
-        // threads must fill whole warps
-        int nthr = ngroups * G;
-        nthr = ((nthr + 31) / 32) * 32;
-        ngroups = nthr / G;
-        size_t smem = ((size_t)(nimg + nxp) * p->na + (size_t)ngroups * p->na) * sizeof(cpx<T>);
-        void (*kern)(int, int, int, int, int, int, const PairDesc *, const cpx<T> *, const cpx<T> *,
-                     const cpx<T> *, cpx<T> *) = nullptr;
-#define SFFT_PICK(GG, SS) \
-    if (G == GG && slots == SS) kern = k_gather<T, GG, SS>;
-        SFFT_PICK(8, 1) SFFT_PICK(8, 2) SFFT_PICK(8, 3) SFFT_PICK(8, 4)
-        SFFT_PICK(4, 1) SFFT_PICK(4, 2) SFFT_PICK(4, 3) SFFT_PICK(4, 4)
-        SFFT_PICK(2, 1) SFFT_PICK(2, 2) SFFT_PICK(2, 3) SFFT_PICK(2, 4)
-#undef SFFT_PICK
-        if (!kern) return cudaErrorInvalidValue;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->nbk, p->npairs, p->pairs,
-                                        (const cpx<T> *)p->U, (const cpx<T> *)p->xhat,
-                                        (const cpx<T> *)p->tw0, (cpx<T> *)p->Q);
-        if ((err = cudaGetLastError())) return err;
-    }
-    k_stage2<T><<<p->nrows, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db,
-                                         p->npairs, p->pairs, (const cpx<T> *)p->Q,
-                                         (const cpx<T> *)p->yhat, (const cpx<T> *)p->tw1, p->lag,
-                                         p->lag_om, p->lag_la, p->lag_th);
+    p->launches++;
+    size_t smem = 3 * (size_t)(p->n0 + p->nbk) * sizeof(cpx<T>);
+    auto kern = k_cols<T>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(p->h1c, p->cfg.dk + 2);
+    kern<<<grid, 256, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, (const cpx<T> *)p->F, (cpx<T> *)p->U,
+                                 (const cpx<T> *)p->tw0);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
+    const int G = p->na / 8;
+    const int nimg = p->nimg, nxp = p->cfg.db + 1;
+    // one group of G lanes per product, whole warps, at most 384 threads per
+    // block; more products go to further blocks along y
+    const int max_groups = 384 / G;
+    const int nchunks = (p->npairs + max_groups - 1) / max_groups;
+    const int per_chunk = (p->npairs + nchunks - 1) / nchunks;
+    int nthr = per_chunk * G;
+    nthr = ((nthr + 31) / 32) * 32;
+    const int ngroups = nthr / G;
+    const int hmax = 2 * p->cfg.w0;
+    const int nap = p->na + kPad;
+    size_t smem = (2 * (size_t)(nimg + nxp) * nap + (size_t)ngroups * nap + (size_t)p->nbk * (2 * hmax + 1)) *
+                  sizeof(cpx<T>);
+    void (*kern)(int, int, int, int, int, int, int, const PairDesc *, const cpx<T> *, const cpx<T> *,
+                 const cpx<T> *, cpx<T> *) = nullptr;
+    if (G == 8) kern = (hmax <= 16) ? k_gather<T, 8, 5> : k_gather<T, 8, 8>;
+    if (G == 4) kern = k_gather<T, 4, 8>;
+    if (G == 2) kern = k_gather<T, 2, 8>;
+    if (!kern) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(p->h1c, nchunks);
+    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->nbk, p->npairs, hmax, p->pairs,
+                                  (const cpx<T> *)p->U, (const cpx<T> *)p->xhat, (const cpx<T> *)p->tw0,
+                                  (cpx<T> *)p->Q);
+    p->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) {
+    cudaError_t err;
+    k_stage2<T><<<p->nrows, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db, p->npairs,
+                                         p->pairs, (const cpx<T> *)p->Q, (const cpx<T> *)p->yhat,
+                                         (const cpx<T> *)p->tw1, p->lag, p->lag_om, p->lag_la, p->lag_th);
+    p->launches++;
     if ((err = cudaGetLastError())) return err;
     LagView lv;
     lv.lag = p->lag;
@@ -615,10 +676,19 @@ static cudaError_t launch_build_rest(Plan *p, double *M, double *rhs, cudaStream
     const size_t total = (size_t)p->n * p->n + p->n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db,
-                                      p->cfg.const_phot_ratio, lv, p->mom, p->mom + (size_t)kMaxMom * kUMax,
-                                      M, rhs);
+    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db, p->cfg.const_phot_ratio,
+                                      lv, p->mom, p->mom + (size_t)kMaxMom * kUMax, M, rhs);
+    p->launches++;
     return cudaGetLastError();
+}
+
+cudaError_t build_stage(Plan *p, int stage, double *M, double *rhs, cudaStream_t s) {
+    switch (stage) {
+        case 1: return p->fp64 ? launch_cols<double>(p, s) : launch_cols<float>(p, s);
+        case 2: return p->fp64 ? launch_gather<double>(p, s) : launch_gather<float>(p, s);
+        case 3: return p->fp64 ? launch_lags<double>(p, M, rhs, s) : launch_lags<float>(p, M, rhs, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8_t *mask, bool moments,
@@ -635,8 +705,8 @@ cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8
 cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M,
                          double *rhs, cudaStream_t s) {
     cudaError_t err = row_transform(p, ref, sci, mask, true, s);
-    if (err) return err;
-    return p->fp64 ? launch_build_rest<double>(p, M, rhs, s) : launch_build_rest<float>(p, M, rhs, s);
+    for (int stage = 1; stage <= 3 && err == cudaSuccess; ++stage) err = build_stage(p, stage, M, rhs, s);
+    return err;
 }
 
 }  // namespace sfft

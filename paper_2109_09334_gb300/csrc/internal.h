@@ -48,9 +48,12 @@ struct Plan {
     int lag_om, lag_la, lag_th;  // offsets into lag
     // solve workspace
     void *A;               // n*n factor (compute type)
+    void *Wm, *Tm;         // n*n: W = L^-1 and a GEMM temporary (compute type)
+    int solve_grid;        // blocks of the cooperative solve kernel (one per SM)
     double *dscale;        // n Jacobi scales
     double *r, *xw;        // n residual, n iterate
-    void *yv, *zv;         // n vectors (compute type)
+    void *yv;              // [n/32][32][32] inverses of the diagonal Cholesky blocks (compute type)
+    void *zv;              // n vector (compute type)
     int *flag;             // device status word for the solve
     // owned buffers for run_pair(_host)
     double *M_own, *rhs_own, *x_own;
@@ -59,6 +62,13 @@ struct Plan {
     uint8_t *img_mask;
     void *kap;             // [nk][L0][m] kernel row spectra (compute type)
     size_t ws_bytes;
+    uint64_t launches;     // kernels this plan has enqueued
+    // buffers of the most recent run_pair (for sfft_replay_stage)
+    const void *last_ref, *last_sci;
+    const uint8_t *last_mask;
+    double *last_M, *last_rhs, *last_x;
+    sfft_solve_info *last_info;
+    void *last_diff;
     cudaStream_t last_stream;
     PairDesc host_pairs[256];
 };
@@ -68,8 +78,11 @@ cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_
                          double *rhs, cudaStream_t s);
 cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
                           bool moments, cudaStream_t s);
+cudaError_t build_stage(Plan *p, int stage, double *M, double *rhs, cudaStream_t s);
 cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
                          sfft_solve_info *info, cudaStream_t s);
+int solve_grid_size(bool fp64);
+size_t solve_vec_elems(int n);
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s);
 cudaError_t plan_tables(Plan *p, cudaStream_t s);
 

@@ -78,7 +78,10 @@ __global__ void k_kernel_table(int n1, int nk, int w0, int w1, int cpr, const do
     }
 }
 
-// One block per column m: D~(., m) into Dt[m][x].
+// One block per column m: D~(., m) into Dt[m][x].  For each y-power j the
+// row transforms of yt^j R are staged in shared memory; the kernel row
+// spectra of the terms (i, j) are combined per tap by Horner's rule in the
+// source row's coordinate, sum_i kap_(i,j)(a, m) xt(x - a)^i.
 template <typename T>
 __global__ void k_sub_cols(int n0, int n1, int dk, int db, int w0, int nbkg_off, const cpx<T> *__restrict__ F,
                            const cpx<T> *__restrict__ kap, const cpx<T> *__restrict__ yhat,
@@ -86,35 +89,39 @@ __global__ void k_sub_cols(int n0, int n1, int dk, int db, int w0, int nbkg_off,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T> *col = reinterpret_cast<cpx<T> *>(smem_raw);  // n0
     cpx<T> *kp = col + n0;                                // nk * L0
+    T *xts = reinterpret_cast<T *>(kp + n_terms(dk) * (2 * w0 + 1));  // n0 coordinates
     constexpr int kMaxPer = 32;
     const int m = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
     const int h1c = n1 / 2 + 1, L0 = 2 * w0 + 1;
     const int nk = n_terms(dk), nbt = n_terms(db);
     const int per = n0 / nthr;  // outputs per thread (n0 multiple of nthr)
+    const int msk = n0 - 1;     // n0 is a power of two
     for (int e = tid; e < nk * L0; e += nthr) kp[e] = kap[(size_t)e * h1c + m];
+    for (int e = tid; e < n0; e += nthr) {
+        xts[e] = coord<T>(e, n0);
+        col[e] = F[((size_t)(dk + 1) * h1c + m) * n0 + e];
+    }
+    __syncthreads();
     cpx<T> acc[kMaxPer];
     // S~ minus the background B~(x, m) = sum_pq b_pq xt^p Y^q(m)
-    for (int e = tid; e < n0; e += nthr) col[e] = F[((size_t)(dk + 1) * h1c + m) * n0 + e];
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kMaxPer; ++k) {
         if (k < per) {
             const int x0 = tid + k * nthr;
             cpx<T> v = col[x0];
-            const T xt = coord<T>(x0, n0);
+            const T xt = xts[x0];
             for (int s = 0; s < nbt; ++s) {
                 int p, q;
                 term_ij(s, &p, &q);
                 const T bpq = (T)x[nbkg_off + s];
-                cpx<T> yq = yhat[(size_t)q * h1c + m];
-                T wgt = bpq * ipow(xt, p);
-                v = v - scale(yq, wgt);
+                v = v - scale(yhat[(size_t)q * h1c + m], bpq * ipow(xt, p));
             }
             acc[k] = v;
         }
     }
     __syncthreads();
     for (int j = 0; j <= dk; ++j) {
+        const int deg = dk - j;  // terms (i, j) for i = 0..deg
         for (int e = tid; e < n0; e += nthr) col[e] = F[((size_t)j * h1c + m) * n0 + e];
         __syncthreads();
 #pragma unroll
@@ -123,15 +130,12 @@ __global__ void k_sub_cols(int n0, int n1, int dk, int db, int w0, int nbkg_off,
                 const int x0 = tid + k * nthr;
                 cpx<T> v = acc[k];
                 for (int a = -w0; a <= w0; ++a) {
-                    const int src = imod(x0 - a, n0);
+                    const int src = (x0 - a) & msk;
                     const cpx<T> g = col[src];
-                    const T xs = coord<T>(src, n0);
-                    T pw = (T)1;
-                    for (int i = 0; i + j <= dk; ++i) {
-                        const cpx<T> kv = kp[term_index(i, j) * L0 + (a + w0)];
-                        v = v - scale(cmul(kv, g), pw);
-                        pw *= xs;
-                    }
+                    const T xs = xts[src];
+                    cpx<T> kv = kp[term_index(deg, j) * L0 + (a + w0)];
+                    for (int i = deg - 1; i >= 0; --i) kv = scale(kv, xs) + kp[term_index(i, j) * L0 + (a + w0)];
+                    v = v - cmul(kv, g);
                 }
                 acc[k] = v;
             }
@@ -180,7 +184,8 @@ __global__ void k_rows_inv(int n0, int n1, const cpx<T> *__restrict__ Dt, const 
 template <typename T>
 static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
     cudaError_t err;
-    double *ksum = p->xw + p->n + 520;  // scratch after the solve's partials
+    double *ksum = p->xw + p->n + 700;  // after the solve's statistics and partial sums
+    p->launches += 4;
     k_kernel_sums<<<p->nk, 256, 0, s>>>(p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x, ksum);
     const size_t tot = (size_t)p->nk * p->L0 * p->h1c;
     int blocks = (int)((tot + 255) / 256);
@@ -192,7 +197,7 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
         int nthr = 256;
         while (p->n0 / nthr > 32) nthr *= 2;
         if (nthr > p->n0) nthr = p->n0;
-        size_t smem = ((size_t)p->n0 + (size_t)p->nk * p->L0) * sizeof(cpx<T>);
+        size_t smem = ((size_t)p->n0 + (size_t)p->nk * p->L0) * sizeof(cpx<T>) + (size_t)p->n0 * sizeof(T);
         cudaFuncSetAttribute(k_sub_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int nbkg_off = p->n - p->nb;
         k_sub_cols<T><<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
