@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft16.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -46,107 +47,115 @@ template <typename I>
 __device__ __forceinline__ double load_img(const I *p, size_t k) { return (double)p[k]; }
 
 // ---------------------------------------------------------------------------
-// Row pass.  Block: TR rows; sequences per row: yt^j * Rm (j <= dk) and Sm,
-// packed two per complex FFT (real and imaginary part) and separated after.
+// Row pass.  Block: TR rows, one group of G = n1/16 threads per row.  The two
+// real sequences of a packed complex FFT (yt^j * Rm for j <= dk, then Sm) are
+// transformed together and separated after; the transforms are written
+// transposed ([image][m][x]) for the column pass.
 template <typename T, typename I>
-__global__ void k_rows(int n0, int n1, int dk, int db, int TR, const I *__restrict__ R,
-                       const I *__restrict__ S, const uint8_t *__restrict__ mask,
-                       cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1, int want_mom,
-                       double *__restrict__ rowmom) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, int n1, int dk, int TR, const I *__restrict__ R,
+                                               const I *__restrict__ S, const uint8_t *__restrict__ mask,
+                                               cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // TR * n1
-    cpx<T> *scr = Z + (size_t)TR * n1;                 // n1
-    Acc<T> *red = reinterpret_cast<Acc<T> *>(scr + n1); // (nthr/32) * kMaxMom
+    const int G = n1 / 16;
+    const int np = padded_len(n1);
+    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n1
+    cpx<T> *Z = tw + n1;                                 // TR * np
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int x0b = blockIdx.x * TR;
-    const int h1c = n1 / 2 + 1;
+    const int grp = tid / G, gt = tid - grp * G;
     const int nseq = dk + 2;
     const int nfft = (nseq + 1) / 2;
-    const MomLayout ml = mom_layout(dk, db);
+    // packed pair index fastest: blocks that read the same rows run together
+    const int f = blockIdx.x % nfft;
+    const int x0b = (blockIdx.x / nfft) * TR;
+    const int sa = 2 * f, sb = 2 * f + 1;
+    cpx<T> *zr = Z + (size_t)grp * np;
+    for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
+    {
+        const size_t rowoff = (size_t)(x0b + grp) * n1;
+        for (int y = gt; y < n1; y += G) {
+            const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
+            const T rv = (T)load_img(R, rowoff + y) * keep;
+            const T sv = (T)load_img(S, rowoff + y) * keep;
+            const T yt = coord<T>(y, n1);
+            const T va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
+            const T vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
+            zr[pad16(y)] = mk(va, vb);
+        }
+    }
+    __syncthreads();
+    group_fft(zr, n1, -1, tw, n1, gt, G);
+    // separate the two real transforms and write them transposed
+    const int h1c = n1 / 2 + 1;
+    const int total = h1c * TR;
+    cpx<T> *Fa = F + (size_t)sa * h1c * n0 + x0b;
+    cpx<T> *Fb = F + (size_t)sb * h1c * n0 + x0b;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int m = idx / TR, r = idx - m * TR;
+        const cpx<T> *zz = Z + (size_t)r * np;
+        const cpx<T> z = zz[pad16(m)];
+        const cpx<T> zc = conj(zz[pad16((n1 - m) & (n1 - 1))]);
+        const size_t o = (size_t)m * n0 + r;
+        Fa[o] = scale(z + zc, (T)0.5);
+        if (sb < nseq) Fb[o] = mul_i(scale(z - zc, (T)0.5), -1);
+    }
+}
 
-    for (int f = 0; f < nfft; ++f) {
-        const int sa = 2 * f, sb = 2 * f + 1;
-        for (int r = 0; r < TR; ++r) {
-            const int x0 = x0b + r;
-            const size_t rowoff = (size_t)x0 * n1;
-            // per-thread partial moments (plain sums of n1/nthr terms), then a
-            // compensated block reduction
-            T pRR[7], pR[7], pRS[4], pS[4];
+// ---------------------------------------------------------------------------
+// Per-row moment sums (for the lag-zero entries, C and E): one block per row,
+// plain per-thread partials, then a two-sum reduction across the block.
+//   RR_v = sum_y Rm^2 yt^v (v <= 2dk), R_v = sum_y Rm yt^v (v <= dk+db),
+//   RS_v = sum_y Rm Sm yt^v (v <= dk), S_v = sum_y Sm yt^v (v <= db).
+template <typename T, typename I>
+__global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, const I *__restrict__ S,
+                              const uint8_t *__restrict__ mask, double *__restrict__ rowmom) {
+    __shared__ Acc<T> red[32][kMaxMom];
+    const int x0 = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
+    const size_t rowoff = (size_t)x0 * n1;
+    const MomLayout ml = mom_layout(dk, db);
+    T pRR[7], pR[7], pRS[4], pS[4];
 #pragma unroll
-            for (int v = 0; v < 7; ++v) pRR[v] = pR[v] = (T)0;
+    for (int v = 0; v < 7; ++v) pRR[v] = pR[v] = (T)0;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) pRS[v] = pS[v] = (T)0;
-            const bool mom = want_mom && f == 0;
-            for (int y = tid; y < n1; y += nthr) {
-                T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
-                T rv = (T)load_img(R, rowoff + y) * keep;
-                T sv = (T)load_img(S, rowoff + y) * keep;
-                T yt = coord<T>(y, n1);
-                T va, vb;
-                va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
-                vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
-                Z[(size_t)r * n1 + y] = mk(va, vb);
-                if (mom) {
-                    T p = (T)1;
+    for (int v = 0; v < 4; ++v) pRS[v] = pS[v] = (T)0;
+    for (int y = tid; y < n1; y += nthr) {
+        const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
+        const T rv = (T)load_img(R, rowoff + y) * keep;
+        const T sv = (T)load_img(S, rowoff + y) * keep;
+        const T yt = coord<T>(y, n1);
+        T p = (T)1;
 #pragma unroll
-                    for (int v = 0; v < 7; ++v) {
-                        pRR[v] += rv * rv * p;
-                        pR[v] += rv * p;
-                        if (v < 4) {
-                            pRS[v] += rv * sv * p;
-                            pS[v] += sv * p;
-                        }
-                        p *= yt;
-                    }
-                }
+        for (int v = 0; v < 7; ++v) {
+            pRR[v] += rv * rv * p;
+            pR[v] += rv * p;
+            if (v < 4) {
+                pRS[v] += rv * sv * p;
+                pS[v] += sv * p;
             }
-            if (mom) {
-                const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-#pragma unroll
-                for (int k = 0; k < 22; ++k) {
-                    // family layout of the row moments: RR (v <= 2dk), R (v <= dk+db),
-                    // RS (v <= dk), S (v <= db)
-                    T val;
-                    int dst;
-                    if (k < 7) { val = pRR[k]; dst = (k <= 2 * dk) ? ml.fRR + k : -1; }
-                    else if (k < 14) { val = pR[k - 7]; dst = (k - 7 <= dk + db) ? ml.fR + k - 7 : -1; }
-                    else if (k < 18) { val = pRS[k - 14]; dst = (k - 14 <= dk) ? ml.fRS + k - 14 : -1; }
-                    else { val = pS[k - 18]; dst = (k - 18 <= db) ? ml.fS + k - 18 : -1; }
-                    if (dst >= 0) {
-                        Acc<T> a;
-                        a.zero();
-                        a.add(val);
-                        for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
-                        if (lane == 0) red[warp * kMaxMom + dst] = a;
-                    }
-                }
-                __syncthreads();
-                if (tid < ml.n) {
-                    Acc<T> a = red[tid];
-                    for (int w = 1; w < nw; ++w) a.add(red[w * kMaxMom + tid]);
-                    rowmom[(size_t)x0 * ml.n + tid] = a.wide();
-                }
-            }
-            __syncthreads();
-            cpx<T> *res = block_fft(Z + (size_t)r * n1, scr, n1, tw1, n1, -1, tid, nthr);
-            if (res != Z + (size_t)r * n1) {
-                for (int y = tid; y < n1; y += nthr) Z[(size_t)r * n1 + y] = res[y];
-                __syncthreads();
-            }
+            p *= yt;
         }
-        // separate the two real transforms and write them transposed
-        const int total = h1c * TR;
-        for (int idx = tid; idx < total; idx += nthr) {
-            const int m = idx / TR, r = idx - m * TR;
-            cpx<T> z = Z[(size_t)r * n1 + m];
-            cpx<T> zc = conj(Z[(size_t)r * n1 + (m == 0 ? 0 : n1 - m)]);
-            cpx<T> A = scale(z + zc, (T)0.5);
-            cpx<T> B = mul_i(scale(z - zc, (T)0.5), -1);
-            const size_t o = (size_t)m * n0 + x0b + r;
-            F[(size_t)sa * h1c * n0 + o] = A;
-            if (sb < nseq) F[(size_t)sb * h1c * n0 + o] = B;
+    }
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+    for (int k = 0; k < 22; ++k) {
+        T val;
+        int dst;
+        if (k < 7) { val = pRR[k]; dst = (k <= 2 * dk) ? ml.fRR + k : -1; }
+        else if (k < 14) { val = pR[k - 7]; dst = (k - 7 <= dk + db) ? ml.fR + k - 7 : -1; }
+        else if (k < 18) { val = pRS[k - 14]; dst = (k - 14 <= dk) ? ml.fRS + k - 14 : -1; }
+        else { val = pS[k - 18]; dst = (k - 18 <= db) ? ml.fS + k - 18 : -1; }
+        if (dst >= 0) {
+            Acc<T> a;
+            a.zero();
+            a.add(val);
+            for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
+            if (lane == 0) red[warp][dst] = a;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (tid < ml.n) {
+        Acc<T> a = red[0][tid];
+        for (int w = 1; w < nw; ++w) a.add(red[w][tid]);
+        rowmom[(size_t)x0 * ml.n + tid] = a.wide();
     }
 }
 
@@ -171,43 +180,42 @@ __global__ void k_moments(int n0, int nmom, const double *__restrict__ rowmom, d
 }
 
 // ---------------------------------------------------------------------------
-// Column pass.  Block (m, src): src <= dk is the row transform of yt^src * Rm,
-// src = dk+1 that of Sm.  Output image t = term (i, src) for i <= dk - src, or
-// t = nk for S.  Layout U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
+// Column pass.  Block (m, chunk): GI output images in parallel, one group of
+// G = n0/16 threads each.  Image t < nk is the term (i, j): the row transform
+// of yt^j * Rm weighted by xt^i; t = nk is Sm.  Output layout
+// U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
 template <typename T>
-__global__ void k_cols(int n0, int n1, int dk, int na, int nbk, const cpx<T> *__restrict__ F,
-                       cpx<T> *__restrict__ U, const cpx<T> *__restrict__ tw0) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, int n1, int dk, int na, int nbk, int GI,
+                                               const cpx<T> *__restrict__ F, cpx<T> *__restrict__ U,
+                                               const cpx<T> *__restrict__ tw0g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int stride = n0 + nbk;
-    cpx<T> *sA = reinterpret_cast<cpx<T> *>(smem_raw);
-    cpx<T> *sB = sA + stride;
-    cpx<T> *sC = sB + stride;
+    const int G = n0 / 16;
+    const int np = padded_len(n0);
+    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n0
+    cpx<T> *Z = tw + n0;                                 // GI * np
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int m = blockIdx.x, src = blockIdx.y;
+    const int grp = tid / G, gt = tid - grp * G;
+    const int m = blockIdx.x;
     const int h1c = n1 / 2 + 1;
     const int nk = n_terms(dk);
-    const cpx<T> *col = F + ((size_t)src * h1c + m) * n0;
-    for (int x = tid; x < n0; x += nthr) sA[x] = col[x];
+    const int t = blockIdx.y * GI + grp;
+    const bool act = t <= nk;
+    for (int q = tid; q < n0; q += nthr) tw[q] = tw0g[q];
+    cpx<T> *zr = Z + (size_t)grp * np;
+    if (act) {
+        int i = 0, j = dk + 1;
+        if (t < nk) term_ij(t, &i, &j);
+        const cpx<T> *col = F + ((size_t)j * h1c + m) * n0;
+        for (int x = gt; x < n0; x += G) zr[pad16(x)] = scale(col[x], ipow(coord<T>(x, n0), i));
+    }
     __syncthreads();
-    const int ni = (src <= dk) ? (dk - src + 1) : 1;
-    for (int i = 0; i < ni; ++i) {
-        const int t = (src <= dk) ? term_index(i, src) : nk;
-        for (int x = tid; x < n0; x += nthr) {
-            T w = ipow(coord<T>(x, n0), i);
-            sB[x] = scale(sA[x], w);
-        }
-        __syncthreads();
-        cpx<T> *res = block_fft(sB, sC, n0, tw0, n0, -1, tid, nthr);
-        cpx<T> *pad = (res == sB) ? sC : sB;
-        // padded transpose: bin l -> pad[(l % nbk) * (na + 1) + l / nbk]
-        for (int l = tid; l < n0; l += nthr) pad[(l % nbk) * (na + 1) + l / nbk] = res[l];
-        __syncthreads();
+    group_fft(zr, n0, -1, tw, n0, gt, G);
+    if (act) {
         cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
-        for (int o = tid; o < n0; o += nthr) {
+        for (int o = gt; o < n0; o += G) {
             const int lb = o / na, r = o - lb * na;
-            out[o] = pad[lb * (na + 1) + r];
+            out[o] = zr[pad16(lb + nbk * r)];
         }
-        __syncthreads();
     }
 }
 
@@ -218,28 +226,6 @@ __global__ void k_cols(int n0, int n1, int dk, int na, int nbk, const cpx<T> *__
 // r2 = 0..7.  Y(s2 + 8*s1) = sum_r1 wG^(r1 s1) w^(r1 s2) sum_r2 w8^(r2 s2) P(r1 + G r2),
 // w = exp(2 pi i / NA): an 8-point DFT in registers, a twiddle, a transpose
 // through shared memory and a G-point DFT.
-template <typename T>
-__device__ __forceinline__ void dft8(cpx<T> (&v)[8], int sgn) {
-    const T c = (T)0.70710678118654752440;
-    cpx<T> a[4], b[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        a[k] = v[k] + v[k + 4];
-        b[k] = v[k] - v[k + 4];
-    }
-    // b[k] *= exp(sgn 2 pi i k / 8)
-    b[1] = cmul(b[1], mk(c, sgn * c));
-    b[2] = mul_i(b[2], sgn);
-    b[3] = cmul(b[3], mk(-c, sgn * c));
-    dft4(a[0], a[1], a[2], a[3], sgn);
-    dft4(b[0], b[1], b[2], b[3], sgn);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[2 * k] = a[k];
-        v[2 * k + 1] = b[k];
-    }
-}
-
 template <typename T, int G>
 __device__ __forceinline__ void dftG(cpx<T> (&v)[G], int sgn) {
     if constexpr (G == 1) {
@@ -598,15 +584,24 @@ __global__ void k_assemble(int n, int w0, int w1, int dk, int db, int cpr, LagVi
 template <typename T, typename I>
 static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
                                bool moments, cudaStream_t s) {
-    const int TR = p->fp64 ? 2 : 4;
-    const int nthr = 256;
-    size_t smem = ((size_t)TR + 1) * p->n1 * sizeof(cpx<T>) + (nthr / 32) * kMaxMom * sizeof(Acc<T>);
+    const int G = p->n1 / 16;
+    int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
+    if (TR > 16) TR = 16;
+    if (TR > p->n0) TR = p->n0;
+    auto smem_of = [&](int tr) { return ((size_t)p->n1 + (size_t)tr * padded_len(p->n1)) * sizeof(cpx<T>); };
+    while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
+    const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<p->n0 / TR, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, TR, (const I *)ref,
-                                       (const I *)sci, mask, (cpx<T> *)p->F, (const cpx<T> *)p->tw1,
-                                       moments ? 1 : 0, p->rowmom);
+    const int nfft = (p->cfg.dk + 3) / 2;
+    kern<<<(p->n0 / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, TR, (const I *)ref, (const I *)sci,
+                                                   mask, (cpx<T> *)p->F, (const cpx<T> *)p->tw1);
     p->launches++;
+    if (moments) {
+        k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
+                                                  p->rowmom);
+        p->launches++;
+    }
     return cudaGetLastError();
 }
 
@@ -615,12 +610,21 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     const MomLayout ml = mom_layout(p->cfg.dk, p->cfg.db);
     k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
     p->launches++;
-    size_t smem = 3 * (size_t)(p->n0 + p->nbk) * sizeof(cpx<T>);
+    const int G = p->n0 / 16;
+    int GI = (sizeof(T) == 4 ? 1024 : 512) / G;
+    if (GI > 4) GI = 4;
+    const int nimg = p->nk + 1;
+    if (GI > nimg) GI = nimg;
+    size_t smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+    while (GI > 1 && smem > 200 * 1024) {
+        --GI;
+        smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+    }
     auto kern = k_cols<T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(p->h1c, p->cfg.dk + 2);
-    kern<<<grid, 256, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, (const cpx<T> *)p->F, (cpx<T> *)p->U,
-                                 (const cpx<T> *)p->tw0);
+    dim3 grid(p->h1c, (nimg + GI - 1) / GI);
+    kern<<<grid, GI * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, GI, (const cpx<T> *)p->F,
+                                    (cpx<T> *)p->U, (const cpx<T> *)p->tw0);
     p->launches++;
     return cudaGetLastError();
 }

@@ -29,6 +29,30 @@ __device__ __forceinline__ void dft4(cpx<T> &v0, cpx<T> &v1, cpx<T> &v2, cpx<T> 
     v3 = b - d;
 }
 
+// 8-point DFT with sign sgn on v (natural order in and out): a radix-2 split
+// into two 4-point DFTs.
+template <typename T>
+__device__ __forceinline__ void dft8(cpx<T> (&v)[8], int sgn) {
+    const T c = (T)0.70710678118654752440;
+    cpx<T> a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a[k] = v[k] + v[k + 4];
+        b[k] = v[k] - v[k + 4];
+    }
+    // b[k] *= exp(sgn 2 pi i k / 8)
+    b[1] = cmul(b[1], mk(c, sgn * c));
+    b[2] = mul_i(b[2], sgn);
+    b[3] = cmul(b[3], mk(-c, sgn * c));
+    dft4(a[0], a[1], a[2], a[3], sgn);
+    dft4(b[0], b[1], b[2], b[3], sgn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = b[k];
+    }
+}
+
 // Transform the n values in buf (shared memory); scratch is another n-element
 // shared buffer.  All threads of the block participate (tid, nthr) and must
 // call it together.  Returns the buffer that holds the result (buf or

@@ -1,0 +1,117 @@
+// fft16.cuh -- register-based FFTs in shared memory, radix-16 passes.
+//
+// A transform of length n = 2^e is done by one group of gsize threads on a
+// padded shared buffer: element i lives at i + (i >> 4), which keeps the
+// strided accesses of every pass free of bank conflicts.  Stockham
+// auto-sort passes: an optional first pass of radix 2, 4 or 8 (so that the
+// rest is a whole number of radix-16 passes), then radix-16 passes, each
+// thread holding one butterfly's 16 values in registers.  Passes are in
+// place: all loads of a pass complete (block barrier) before its stores.
+// Twiddles exp(sgn 2 pi i q / n_tab) come from a shared table of n_tab
+// entries (tw[q] = exp(-2 pi i q / n_tab); the inverse uses conjugates).
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace sfft {
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4); }
+
+template <typename T>
+__device__ __forceinline__ cpx<T> tw_get(const cpx<T> *tw, int q, int sgn) {
+    const cpx<T> w = tw[q];
+    return sgn < 0 ? w : mk(w.re, -w.im);
+}
+
+// in-place DFT of 2, 4, 8 or 16 values with sign sgn, natural output order
+template <typename T>
+__device__ __forceinline__ void dft2(cpx<T> &a, cpx<T> &b) {
+    const cpx<T> s = a + b, d = a - b;
+    a = s;
+    b = d;
+}
+
+template <typename T>
+__device__ __forceinline__ void dft16(cpx<T> (&v)[16], int sgn) {
+    // X[k2 + 4 k1] = sum_r1 W4^(r1 k1) W16^(r1 k2) sum_r2 W4^(r2 k2) v[r1 + 4 r2]
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, c2 = (T)0.70710678118654752440;
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) dft4(v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12], sgn);
+    // now v[r1 + 4 k2] = Y[r1][k2]; twiddle by W16^(r1 k2)
+    const T sg = (T)sgn;
+    v[1 + 4 * 1] = cmul(v[5], mk(c1, sg * s1));   // r1=1,k2=1: m=1
+    v[1 + 4 * 2] = cmul(v[9], mk(c2, sg * c2));   // m=2
+    v[1 + 4 * 3] = cmul(v[13], mk(s1, sg * c1));  // m=3
+    v[2 + 4 * 1] = cmul(v[6], mk(c2, sg * c2));   // m=2
+    v[2 + 4 * 2] = mul_i(v[10], sgn);             // m=4
+    v[2 + 4 * 3] = cmul(v[14], mk(-c2, sg * c2)); // m=6
+    v[3 + 4 * 1] = cmul(v[7], mk(s1, sg * c1));   // m=3
+    v[3 + 4 * 2] = cmul(v[11], mk(-c2, sg * c2)); // m=6
+    v[3 + 4 * 3] = cmul(v[15], mk(-c1, -sg * s1));// m=9
+    // DFT4 over r1 for each k2, in place: v[4 k2 + k1] = X[k2 + 4 k1]
+    // (transposed slot order; see slot16)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) dft4(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3], sgn);
+}
+
+// register slot of output X[r] after dft16
+__device__ __forceinline__ constexpr int slot16(int r) { return (r & 3) * 4 + (r >> 2); }
+
+// One Stockham pass of radix R on the padded buffer.  All threads of the
+// block call it (block barriers inside); gtid/gsize index the group.
+template <typename T, int R>
+__device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, const cpx<T> *tw, int tw_n, int gtid,
+                                         int gsize) {
+    const int nb = n / R;  // butterflies
+    const int stride = (tw_n / n) * (n / (R * ns));
+    constexpr int kMaxPer = 16 / R;  // butterflies per thread (gsize = n / 16)
+    cpx<T> v[kMaxPer][R];
+#pragma unroll
+    for (int u = 0; u < kMaxPer; ++u) {
+        const int j = gtid + u * gsize;
+        if (j < nb) {
+            const int k = j & (ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u][r] = buf[pad16(j + r * nb)];
+            if (ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], tw_get(tw, r * k * stride, sgn));
+            }
+            if constexpr (R == 16) dft16(v[u], sgn);
+            else if constexpr (R == 8) dft8(v[u], sgn);
+            else if constexpr (R == 4) dft4(v[u][0], v[u][1], v[u][2], v[u][3], sgn);
+            else dft2(v[u][0], v[u][1]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kMaxPer; ++u) {
+        const int j = gtid + u * gsize;
+        if (j < nb) {
+            const int k = j & (ns - 1);
+            const int o = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[pad16(o + r * ns)] = v[u][(R == 16) ? slot16(r) : r];
+        }
+    }
+    __syncthreads();
+}
+
+// Whole transform of length n (power of two, 16 <= n <= 4096) on the padded
+// buffer; the block must call it with the same n in every group.
+template <typename T>
+__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *tw, int tw_n, int gtid, int gsize) {
+    const int e = 31 - __clz(n);
+    int ns = 1;
+    switch (e & 3) {
+        case 1: fft_pass<T, 2>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 2; break;
+        case 2: fft_pass<T, 4>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 4; break;
+        case 3: fft_pass<T, 8>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 8; break;
+        default: break;
+    }
+    for (; ns < n; ns *= 16) fft_pass<T, 16>(buf, n, ns, sgn, tw, tw_n, gtid, gsize);
+}
+
+}  // namespace sfft

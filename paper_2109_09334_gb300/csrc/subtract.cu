@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft16.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -147,37 +148,41 @@ __global__ void k_sub_cols(int n0, int n1, int dk, int db, int w0, int nbkg_off,
         if (k < per) Dt[(size_t)m * n0 + tid + k * nthr] = acc[k];
 }
 
-// Inverse real FFT of rows: block handles TR = 4 rows, two per complex FFT.
+// Inverse real FFT of rows: NG groups of G = n1/16 threads per block, each
+// group transforms two rows at once (real and imaginary part of one complex
+// FFT of the Hermitian-extended row spectra).
 template <typename T, typename I>
-__global__ void k_rows_inv(int n0, int n1, const cpx<T> *__restrict__ Dt, const cpx<T> *__restrict__ tw1,
-                           I *__restrict__ D) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0, int n1, int NG, const cpx<T> *__restrict__ Dt,
+                                                   const cpx<T> *__restrict__ tw1g, I *__restrict__ D) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *a = reinterpret_cast<cpx<T> *>(smem_raw);
-    cpx<T> *b = a + n1;
+    const int G = n1 / 16;
+    const int np = padded_len(n1);
+    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n1
+    cpx<T> *Z = tw + n1;                                 // NG * np
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const int grp = tid / G, gt = tid - grp * G;
     const int half = n1 / 2;
     const T inv = (T)1 / (T)n1;
-    for (int pr = 0; pr < 2; ++pr) {
-        const int xa = blockIdx.x * 4 + 2 * pr, xb = xa + 1;
-        for (int mm = tid; mm < n1; mm += nthr) {
-            cpx<T> A, B;
-            if (mm <= half) {
-                A = Dt[(size_t)mm * n0 + xa];
-                B = Dt[(size_t)mm * n0 + xb];
-            } else {
-                A = conj(Dt[(size_t)(n1 - mm) * n0 + xa]);
-                B = conj(Dt[(size_t)(n1 - mm) * n0 + xb]);
-            }
-            a[mm] = A + mul_i(B, 1);
+    const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
+    for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
+    cpx<T> *zr = Z + (size_t)grp * np;
+    for (int mm = gt; mm < n1; mm += G) {
+        cpx<T> A, B;
+        if (mm <= half) {
+            A = Dt[(size_t)mm * n0 + xa];
+            B = Dt[(size_t)mm * n0 + xb];
+        } else {
+            A = conj(Dt[(size_t)(n1 - mm) * n0 + xa]);
+            B = conj(Dt[(size_t)(n1 - mm) * n0 + xb]);
         }
-        __syncthreads();
-        cpx<T> *res = block_fft(a, b, n1, tw1, n1, 1, tid, nthr);
-        for (int y = tid; y < n1; y += nthr) {
-            cpx<T> z = res[y];
-            D[(size_t)xa * n1 + y] = (I)(z.re * inv);
-            D[(size_t)xb * n1 + y] = (I)(z.im * inv);
-        }
-        __syncthreads();
+        zr[pad16(mm)] = A + mul_i(B, 1);
+    }
+    __syncthreads();
+    group_fft(zr, n1, 1, tw, n1, gt, G);
+    for (int y = gt; y < n1; y += G) {
+        const cpx<T> z = zr[pad16(y)];
+        D[(size_t)xa * n1 + y] = (I)(z.re * inv);
+        D[(size_t)xb * n1 + y] = (I)(z.im * inv);
     }
 }
 
@@ -206,15 +211,24 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
         if ((err = cudaGetLastError())) return err;
     }
     {
-        size_t smem = 2 * (size_t)p->n1 * sizeof(cpx<T>);
+        const int G = p->n1 / 16;
+        int NG = (sizeof(T) == 4 ? 1024 : 512) / G;
+        if (NG > 4) NG = 4;
+        if (NG > p->n0 / 2) NG = p->n0 / 2;
+        size_t smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+        while (NG > 1 && smem > 200 * 1024) {
+            NG /= 2;
+            smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+        }
+        const int blocks = p->n0 / (2 * NG);
         if (p->cfg.dtype == SFFT_F64) {
             cudaFuncSetAttribute(k_rows_inv<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_rows_inv<T, double><<<p->n0 / 4, 256, smem, s>>>(p->n0, p->n1, (const cpx<T> *)p->U,
-                                                               (const cpx<T> *)p->tw1, (double *)diff);
+            k_rows_inv<T, double><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, NG, (const cpx<T> *)p->U,
+                                                                (const cpx<T> *)p->tw1, (double *)diff);
         } else {
             cudaFuncSetAttribute(k_rows_inv<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_rows_inv<T, float><<<p->n0 / 4, 256, smem, s>>>(p->n0, p->n1, (const cpx<T> *)p->U,
-                                                              (const cpx<T> *)p->tw1, (float *)diff);
+            k_rows_inv<T, float><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, NG, (const cpx<T> *)p->U,
+                                                               (const cpx<T> *)p->tw1, (float *)diff);
         }
     }
     return cudaGetLastError();
