@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
                                                cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
-    const int np = padded_len(n1);
+    const int np = padded_len(n1) + 4;  // +4: rows start in different banks
     cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n1
     cpx<T> *Z = tw + n1;                                 // TR * np
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -71,15 +71,28 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     cpx<T> *zr = Z + (size_t)grp * np;
     for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
     {
+        // thread gt loads pixels [16 gt, 16 gt + 16) of its row (all loads in flight)
         const size_t rowoff = (size_t)(x0b + grp) * n1;
-        for (int y = gt; y < n1; y += G) {
-            const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
-            const T rv = (T)load_img(R, rowoff + y) * keep;
-            const T sv = (T)load_img(S, rowoff + y) * keep;
-            const T yt = coord<T>(y, n1);
-            const T va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
-            const T vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
-            zr[pad16(y)] = mk(va, vb);
+        const int y0 = 16 * gt;
+        T rv[16], sv[16];
+        load16<T, I>(R + rowoff + y0, rv);
+        load16<T, I>(S + rowoff + y0, sv);
+        if (mask != nullptr) {
+            const uint4 mv = __ldg(reinterpret_cast<const uint4 *>(mask + rowoff + y0));
+            const unsigned mw[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const bool keep = ((mw[c >> 2] >> (8 * (c & 3))) & 0xffu) != 0u;
+                rv[c] = keep ? rv[c] : (T)0;
+                sv[c] = keep ? sv[c] : (T)0;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const T yt = coord<T>(y0 + c, n1);
+            const T va = (sa <= dk) ? rv[c] * ipow(yt, sa) : sv[c];
+            const T vb = (sb <= dk) ? rv[c] * ipow(yt, sb) : (sb == dk + 1 ? sv[c] : (T)0);
+            zr[pad16(y0 + c)] = mk(va, vb);
         }
     }
     __syncthreads();
@@ -203,18 +216,27 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, in
     for (int q = tid; q < n0; q += nthr) tw[q] = tw0g[q];
     cpx<T> *zr = Z + (size_t)grp * np;
     if (act) {
+        // thread gt loads elements [16 gt, 16 gt + 16) of the column (all in flight)
         int i = 0, j = dk + 1;
         if (t < nk) term_ij(t, &i, &j);
-        const cpx<T> *col = F + ((size_t)j * h1c + m) * n0;
-        for (int x = gt; x < n0; x += G) zr[pad16(x)] = scale(col[x], ipow(coord<T>(x, n0), i));
+        const cpx<T> *col = F + ((size_t)j * h1c + m) * n0 + 16 * gt;
+        cpx<T> v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = col[c];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int x = 16 * gt + c;
+            zr[pad16(x)] = scale(v[c], ipow(coord<T>(x, n0), i));
+        }
     }
     __syncthreads();
-    group_fft(zr, n0, -1, tw, n0, gt, G);
+    // the last pass stores bin l = lb + NB*r at lb*(NA+1) + r
+    group_fft(zr, n0, -1, tw, n0, gt, G, nbk, na);
     if (act) {
         cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
         for (int o = gt; o < n0; o += G) {
             const int lb = o / na, r = o - lb * na;
-            out[o] = zr[pad16(lb + nbk * r)];
+            out[o] = zr[lb * (na + 1) + r];
         }
     }
 }
@@ -588,7 +610,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
     if (TR > 16) TR = 16;
     if (TR > p->n0) TR = p->n0;
-    auto smem_of = [&](int tr) { return ((size_t)p->n1 + (size_t)tr * padded_len(p->n1)) * sizeof(cpx<T>); };
+    auto smem_of = [&](int tr) { return ((size_t)p->n1 + (size_t)tr * (padded_len(p->n1) + 4)) * sizeof(cpx<T>); };
     while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
     const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;

@@ -59,11 +59,18 @@ __device__ __forceinline__ void dft16(cpx<T> (&v)[16], int sgn) {
 // register slot of output X[r] after dft16
 __device__ __forceinline__ constexpr int slot16(int r) { return (r & 3) * 4 + (r >> 2); }
 
+// Store position of output l: the padded natural layout, or (perm_nb > 0)
+// the residue-class layout [l mod perm_nb][l / perm_nb] with rows of
+// perm_na + 1 elements.
+__device__ __forceinline__ int out_pos(int l, int perm_nb, int perm_na) {
+    return perm_nb > 0 ? (l % perm_nb) * (perm_na + 1) + l / perm_nb : pad16(l);
+}
+
 // One Stockham pass of radix R on the padded buffer.  All threads of the
 // block call it (block barriers inside); gtid/gsize index the group.
 template <typename T, int R>
 __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, const cpx<T> *tw, int tw_n, int gtid,
-                                         int gsize) {
+                                         int gsize, int perm_nb = 0, int perm_na = 0) {
     const int nb = n / R;  // butterflies
     const int stride = (tw_n / n) * (n / (R * ns));
     constexpr int kMaxPer = 16 / R;  // butterflies per thread (gsize = n / 16)
@@ -93,25 +100,69 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
             const int k = j & (ns - 1);
             const int o = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[pad16(o + r * ns)] = v[u][(R == 16) ? slot16(r) : r];
+            for (int r = 0; r < R; ++r) buf[out_pos(o + r * ns, perm_nb, perm_na)] = v[u][(R == 16) ? slot16(r) : r];
         }
     }
     __syncthreads();
 }
 
 // Whole transform of length n (power of two, 16 <= n <= 4096) on the padded
-// buffer; the block must call it with the same n in every group.
+// buffer; the block must call it with the same n in every group.  With
+// perm_nb > 0 the last pass stores in the residue-class layout (out_pos).
 template <typename T>
-__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *tw, int tw_n, int gtid, int gsize) {
+__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *tw, int tw_n, int gtid, int gsize,
+                          int perm_nb = 0, int perm_na = 0) {
     const int e = 31 - __clz(n);
     int ns = 1;
+    const bool only_first = (e >> 2) == 0;  // no radix-16 pass follows
     switch (e & 3) {
-        case 1: fft_pass<T, 2>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 2; break;
-        case 2: fft_pass<T, 4>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 4; break;
-        case 3: fft_pass<T, 8>(buf, n, ns, sgn, tw, tw_n, gtid, gsize); ns = 8; break;
+        case 1:
+            fft_pass<T, 2>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            ns = 2;
+            break;
+        case 2:
+            fft_pass<T, 4>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            ns = 4;
+            break;
+        case 3:
+            fft_pass<T, 8>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            ns = 8;
+            break;
         default: break;
     }
-    for (; ns < n; ns *= 16) fft_pass<T, 16>(buf, n, ns, sgn, tw, tw_n, gtid, gsize);
+    for (; ns < n; ns *= 16) {
+        const bool last = ns * 16 >= n;
+        fft_pass<T, 16>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, last ? perm_nb : 0, perm_na);
+    }
+}
+
+// 16 consecutive values of type I from global memory into registers as T,
+// with 16-byte vector loads (p must be 16-byte aligned).
+template <typename T, typename I>
+__device__ __forceinline__ void load16(const I *__restrict__ p, T (&out)[16]) {
+    if constexpr (sizeof(I) == 4) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+        float4 a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = __ldg(q + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            out[4 * k] = (T)a[k].x;
+            out[4 * k + 1] = (T)a[k].y;
+            out[4 * k + 2] = (T)a[k].z;
+            out[4 * k + 3] = (T)a[k].w;
+        }
+    } else {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+        double2 a[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = __ldg(q + k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            out[2 * k] = (T)a[k].x;
+            out[2 * k + 1] = (T)a[k].y;
+        }
+    }
 }
 
 }  // namespace sfft

@@ -79,73 +79,80 @@ __global__ void k_kernel_table(int n1, int nk, int w0, int w1, int cpr, const do
     }
 }
 
-// One block per column m: D~(., m) into Dt[m][x].  For each y-power j the
-// row transforms of yt^j R are staged in shared memory; the kernel row
-// spectra of the terms (i, j) are combined per tap by Horner's rule in the
-// source row's coordinate, sum_i kap_(i,j)(a, m) xt(x - a)^i.
+// One block per column m: D~(., m) into Dt[m][x].  Thread t computes the Q
+// consecutive outputs x0 = Q t .. Q t + Q - 1.  For each kernel term (i, j)
+// the weighted column W(x) = xt^i F_j(x, m) is staged in shared memory (one
+// pad element after every Q, so the threads' strided accesses hit distinct
+// banks) and the L0 taps slide a Q-value window over it: one shared load and
+// Q complex multiply-adds per tap.  Q = 4 for FP32, 8 for FP64, so that
+// n0 = 4096 needs at most 1024 (FP32) or 512 (FP64) threads.
 template <typename T>
-__global__ void k_sub_cols(int n0, int n1, int dk, int db, int w0, int nbkg_off, const cpx<T> *__restrict__ F,
-                           const cpx<T> *__restrict__ kap, const cpx<T> *__restrict__ yhat,
-                           const double *__restrict__ x, cpx<T> *__restrict__ Dt) {
+__host__ __device__ constexpr int sub_q() { return sizeof(T) == 4 ? 4 : 8; }
+
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0, int n1, int dk, int db, int w0,
+                                                                         int nbkg_off, const cpx<T> *__restrict__ F,
+                                                                         const cpx<T> *__restrict__ kap,
+                                                                         const cpx<T> *__restrict__ yhat,
+                                                                         const double *__restrict__ x,
+                                                                         cpx<T> *__restrict__ Dt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T> *col = reinterpret_cast<cpx<T> *>(smem_raw);  // n0
-    cpx<T> *kp = col + n0;                                // nk * L0
-    T *xts = reinterpret_cast<T *>(kp + n_terms(dk) * (2 * w0 + 1));  // n0 coordinates
-    constexpr int kMaxPer = 32;
-    const int m = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
-    const int h1c = n1 / 2 + 1, L0 = 2 * w0 + 1;
     const int nk = n_terms(dk), nbt = n_terms(db);
-    const int per = n0 / nthr;  // outputs per thread (n0 multiple of nthr)
-    const int msk = n0 - 1;     // n0 is a power of two
+    const int L0 = 2 * w0 + 1;
+    cpx<T> *kp = reinterpret_cast<cpx<T> *>(smem_raw);  // nk * L0
+    constexpr int Q = sub_q<T>();
+    cpx<T> *W = kp + nk * L0;  // n0 + n0 / Q (padded)
+    auto padq = [](int v) { return v + v / Q; };
+    const int m = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
+    const int h1c = n1 / 2 + 1;
+    const int msk = n0 - 1;  // n0 is a power of two
+    const int x0 = Q * tid;
     for (int e = tid; e < nk * L0; e += nthr) kp[e] = kap[(size_t)e * h1c + m];
-    for (int e = tid; e < n0; e += nthr) {
-        xts[e] = coord<T>(e, n0);
-        col[e] = F[((size_t)(dk + 1) * h1c + m) * n0 + e];
-    }
-    __syncthreads();
-    cpx<T> acc[kMaxPer];
+    T xt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) xt[q] = coord<T>(x0 + q, n0);
     // S~ minus the background B~(x, m) = sum_pq b_pq xt^p Y^q(m)
+    cpx<T> acc[Q];
+    {
+        const cpx<T> *Sc = F + ((size_t)(dk + 1) * h1c + m) * n0 + x0;
 #pragma unroll
-    for (int k = 0; k < kMaxPer; ++k) {
-        if (k < per) {
-            const int x0 = tid + k * nthr;
-            cpx<T> v = col[x0];
-            const T xt = xts[x0];
-            for (int s = 0; s < nbt; ++s) {
-                int p, q;
-                term_ij(s, &p, &q);
-                const T bpq = (T)x[nbkg_off + s];
-                v = v - scale(yhat[(size_t)q * h1c + m], bpq * ipow(xt, p));
-            }
-            acc[k] = v;
+        for (int q = 0; q < Q; ++q) acc[q] = Sc[q];
+        for (int s = 0; s < nbt; ++s) {
+            int p, qq;
+            term_ij(s, &p, &qq);
+            const cpx<T> yq = yhat[(size_t)qq * h1c + m];
+            const T bpq = (T)x[nbkg_off + s];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) acc[q] = acc[q] - scale(yq, bpq * ipow(xt[q], p));
         }
     }
-    __syncthreads();
     for (int j = 0; j <= dk; ++j) {
-        const int deg = dk - j;  // terms (i, j) for i = 0..deg
-        for (int e = tid; e < n0; e += nthr) col[e] = F[((size_t)j * h1c + m) * n0 + e];
-        __syncthreads();
+        cpx<T> f[Q];
+        const cpx<T> *Fj = F + ((size_t)j * h1c + m) * n0 + x0;
 #pragma unroll
-        for (int k = 0; k < kMaxPer; ++k) {
-            if (k < per) {
-                const int x0 = tid + k * nthr;
-                cpx<T> v = acc[k];
-                for (int a = -w0; a <= w0; ++a) {
-                    const int src = (x0 - a) & msk;
-                    const cpx<T> g = col[src];
-                    const T xs = xts[src];
-                    cpx<T> kv = kp[term_index(deg, j) * L0 + (a + w0)];
-                    for (int i = deg - 1; i >= 0; --i) kv = scale(kv, xs) + kp[term_index(i, j) * L0 + (a + w0)];
-                    v = v - cmul(kv, g);
-                }
-                acc[k] = v;
+        for (int q = 0; q < Q; ++q) f[q] = Fj[q];
+        for (int i = 0; i + j <= dk; ++i) {
+            __syncthreads();  // previous term's window reads are done
+#pragma unroll
+            for (int q = 0; q < Q; ++q) W[padq(x0 + q)] = scale(f[q], ipow(xt[q], i));
+            __syncthreads();
+            const cpx<T> *kt = kp + term_index(i, j) * L0;
+            cpx<T> win[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) win[q] = W[padq((x0 - w0 + q) & msk)];
+            for (int a = w0; a >= -w0; --a) {
+                const cpx<T> kv = kt[a + w0];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc[q] = acc[q] - cmul(kv, win[q]);
+#pragma unroll
+                for (int q = 0; q + 1 < Q; ++q) win[q] = win[q + 1];
+                win[Q - 1] = W[padq((x0 + Q - a) & msk)];
             }
         }
-        __syncthreads();
     }
+    cpx<T> *out = Dt + (size_t)m * n0 + x0;
 #pragma unroll
-    for (int k = 0; k < kMaxPer; ++k)
-        if (k < per) Dt[(size_t)m * n0 + tid + k * nthr] = acc[k];
+    for (int q = 0; q < Q; ++q) out[q] = acc[q];
 }
 
 // Inverse real FFT of rows: NG groups of G = n1/16 threads per block, each
@@ -166,16 +173,23 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0
     const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
     for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
     cpx<T> *zr = Z + (size_t)grp * np;
-    for (int mm = gt; mm < n1; mm += G) {
-        cpx<T> A, B;
-        if (mm <= half) {
-            A = Dt[(size_t)mm * n0 + xa];
-            B = Dt[(size_t)mm * n0 + xb];
-        } else {
-            A = conj(Dt[(size_t)(n1 - mm) * n0 + xa]);
-            B = conj(Dt[(size_t)(n1 - mm) * n0 + xb]);
+    {
+        // 16 frequencies per thread, all loads in flight
+        cpx<T> A[16], B[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int mm = gt + c * G;
+            const int mr = (mm <= half) ? mm : n1 - mm;
+            A[c] = Dt[(size_t)mr * n0 + xa];
+            B[c] = Dt[(size_t)mr * n0 + xb];
         }
-        zr[pad16(mm)] = A + mul_i(B, 1);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int mm = gt + c * G;
+            const cpx<T> a = (mm <= half) ? A[c] : conj(A[c]);
+            const cpx<T> b = (mm <= half) ? B[c] : conj(B[c]);
+            zr[pad16(mm)] = a + mul_i(b, 1);
+        }
     }
     __syncthreads();
     group_fft(zr, n1, 1, tw, n1, gt, G);
@@ -199,10 +213,8 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
                                              ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
     if ((err = cudaGetLastError())) return err;
     {
-        int nthr = 256;
-        while (p->n0 / nthr > 32) nthr *= 2;
-        if (nthr > p->n0) nthr = p->n0;
-        size_t smem = ((size_t)p->n0 + (size_t)p->nk * p->L0) * sizeof(cpx<T>) + (size_t)p->n0 * sizeof(T);
+        const int nthr = p->n0 / sub_q<T>();
+        const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
         cudaFuncSetAttribute(k_sub_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int nbkg_off = p->n - p->nb;
         k_sub_cols<T><<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
