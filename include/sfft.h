@@ -138,6 +138,35 @@ int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double 
                sfft_solve_info *d_info, sfft_stream_t stream);
 
 /*
+ * sfft_solve without a plan and without allocating: the paper has no
+ * counterpart; this is an engineering variant of sfft_solve for callers that
+ * cannot allocate device memory at call time.  Examples are a pipeline that
+ * has handed all of the device's memory to its own pool, where a cudaMalloc
+ * would fail, and a service that keeps other streams busy, where cudaFree
+ * would synchronise the device and stall them.  It is also for a system
+ * assembled elsewhere, which would otherwise need a plan whose creation
+ * allocates the whole image workspace.  Same algorithm and results as
+ * sfft_solve.
+ *   d_M, d_rhs : n*n and n doubles in device memory (read only).
+ *   n          : 1 <= n <= SFFT_SOLVE_STATIC_MAX_N; larger n returns
+ *                SFFT_ERR_UNSUPPORTED before any device work.
+ *   precision  : SFFT_PREC_FP64 or SFFT_PREC_MIXED (as sfft_config.precision).
+ *   d_x        : n doubles.  d_info : device sfft_solve_info, or NULL.
+ * Workspace: one file-scope device array per device, 16.25 MiB
+ * (2 SFFT_SOLVE_STATIC_MAX_N^2 doubles + 256 KiB), placed by the CUDA driver
+ * when the library's module is loaded.  Nothing in it needs to start at
+ * zero, because each call resets its own status flags first.  Calls whose
+ * executions overlap on one device share the array and race: order them on
+ * one stream, or make one wait for the other.  The first call on each device
+ * (made with that device current) does one-time setup.  It looks up the
+ * array's address and sizes the cooperative grid, checking both results.
+ * Make that call before any stream capture begins.
+ */
+#define SFFT_SOLVE_STATIC_MAX_N 1024
+int sfft_solve_static(const double *d_M, const double *d_rhs, int32_t n, int32_t precision,
+                      double *d_x, sfft_solve_info *d_info, sfft_stream_t stream);
+
+/*
  * Difference image of Eq. 12-13 from the UNMASKED pair (two-step process of
  * Sec. 3): D = S - sum_ij (R^ij o k_ij) - sum_pq b_pq T^pq, evaluated in
  * Fourier space along y and as an L0-tap circular stencil along x.

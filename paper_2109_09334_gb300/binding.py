@@ -27,6 +27,7 @@ SFFT_F32, SFFT_F64 = 0, 1
 SFFT_STAGE_ROWS, SFFT_STAGE_COLS, SFFT_STAGE_GATHER, SFFT_STAGE_LAGS, SFFT_STAGE_SOLVE, SFFT_STAGE_SUBTRACT = range(6)
 STAGE_NAMES = ["rows", "cols", "gather", "lags", "solve", "subtract"]
 SFFT_PREC_FP64, SFFT_PREC_MIXED = 0, 1
+SFFT_SOLVE_STATIC_MAX_N = 1024
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sfft.h")
 
@@ -66,6 +67,7 @@ def library():
         lib.sfft_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_build_system.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sfft_solve_static.argtypes = [vp, vp, i32, i32, vp, vp, vp]
         lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -148,6 +150,15 @@ def sfft_build_system(plan, d_ref, d_sci, d_mask, d_M, d_rhs, stream=None):
 
 def sfft_solve(plan, d_M, d_rhs, d_x, d_info=None, stream=None):
     _check(library().sfft_solve(plan, _p(d_M), _p(d_rhs), _p(d_x), _p(d_info), _s(stream)), "sfft_solve")
+
+
+def sfft_solve_static(d_M, d_rhs, n, precision, d_x, d_info=None, stream=None):
+    """Solve without a plan on the library's static workspace (n <= SFFT_SOLVE_STATIC_MAX_N)."""
+    prec = {"fp64": SFFT_PREC_FP64, "mixed": SFFT_PREC_MIXED}.get(precision, precision)
+    rc = library().sfft_solve_static(_p(d_M), _p(d_rhs), int(n), int(prec), _p(d_x), _p(d_info), _s(stream))
+    if rc == SFFT_ERR_UNSUPPORTED and int(n) > SFFT_SOLVE_STATIC_MAX_N:
+        raise SfftError(rc, f"sfft_solve_static: n={int(n)} exceeds SFFT_SOLVE_STATIC_MAX_N={SFFT_SOLVE_STATIC_MAX_N}")
+    _check(rc, "sfft_solve_static")
 
 
 def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):

@@ -83,6 +83,18 @@ cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
                          sfft_solve_info *info, cudaStream_t s);
 int solve_grid_size(bool fp64);
 size_t solve_vec_elems(int n);
+// Solve workspace given by the caller instead of a plan (sizes for n
+// unknowns in the compute type: A, W n*n; zv solve_vec_elems(n); dsc, r n
+// doubles; xw n + 8 + 2*grid doubles; flag 4 ints).
+struct SolveBuffers {
+    int n, grid;
+    bool fp64;
+    void *A, *W, *zv;
+    double *dsc, *r, *xw;
+    int *flag;
+};
+cudaError_t solve_on_buffers(const SolveBuffers &b, const double *M, const double *rhs, double *x,
+                             sfft_solve_info *info, cudaStream_t s);
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s);
 cudaError_t plan_tables(Plan *p, cudaStream_t s);
 

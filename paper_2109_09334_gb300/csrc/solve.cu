@@ -465,4 +465,37 @@ cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
     return p->fp64 ? solve_t<double>(p, M, rhs, x, info, s) : solve_t<float>(p, M, rhs, x, info, s);
 }
 
+template <typename T>
+static cudaError_t solve_buf_t(const SolveBuffers &b, const double *M, const double *rhs, double *x,
+                               sfft_solve_info *info, cudaStream_t st) {
+    SolveArgs<T> a;
+    a.n = b.n;
+    a.nblk = (b.n + kNB - 1) / kNB;
+    a.M = M;
+    a.rhs = rhs;
+    a.dsc = b.dsc;
+    a.x = b.xw;
+    a.r = b.r;
+    a.stats = b.xw + b.n;
+    a.part = b.xw + b.n + 8;
+    a.A = (T *)b.A;
+    a.W = (T *)b.W;
+    a.z = (T *)b.zv;
+    a.y = (T *)b.zv + b.n;
+    a.wseg = (T *)b.zv + 2 * (size_t)b.n;
+    a.flag = b.flag;
+    a.xout = x;
+    a.info = info;
+    k_solve_reset<<<1, 1, 0, st>>>(b.flag, a.stats);
+    cudaError_t err = cudaGetLastError();
+    if (err) return err;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((void *)k_solve_coop<T>, b.grid, kThreads, args, solve_dyn_smem(b.fp64), st);
+}
+
+cudaError_t solve_on_buffers(const SolveBuffers &b, const double *M, const double *rhs, double *x,
+                             sfft_solve_info *info, cudaStream_t s) {
+    return b.fp64 ? solve_buf_t<double>(b, M, rhs, x, info, s) : solve_buf_t<float>(b, M, rhs, x, info, s);
+}
+
 }  // namespace sfft

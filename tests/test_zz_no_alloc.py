@@ -1,0 +1,101 @@
+"""sfft_solve_static (the solve on the library's static device workspace)
+against sfft_solve on a plan.
+
+The file name sorts last so that it runs after every other test has used the
+library, and it needs nothing from them: it also passes alone.  Tolerance:
+both entry points run the same kernels on the same system, so the
+coefficients agree to within 1e-12 of max |theta| (they are expected to be
+bitwise equal; the bound leaves room for nothing but rounding).
+"""
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+from synth import random_field
+
+torch = pytest.importorskip("torch")
+
+# n0, n1, w, dk, db, const_phot_ratio: n = 487 and n = 1015 (near the maximum)
+CASES = [
+    (256, 256, 4, 2, 2, 1),
+    (128, 128, 6, 2, 2, 1),
+]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_09334_gb300 import binding
+    from paper_2109_09334_gb300.build import build
+    build()
+    return binding.library()
+
+
+def test_max_n_matches_header(lib):
+    from paper_2109_09334_gb300 import binding
+    with open(binding.HEADER) as f:
+        m = re.search(r"#define\s+SFFT_SOLVE_STATIC_MAX_N\s+(\d+)", f.read())
+    assert m and int(m.group(1)) == binding.SFFT_SOLVE_STATIC_MAX_N
+
+
+def test_rejects_bad_arguments_before_device_work(lib):
+    """Argument checks return before any CUDA call, so this runs without a GPU."""
+    from paper_2109_09334_gb300 import binding as B
+    fake = 4096  # never dereferenced: every call below is rejected first
+    big = B.SFFT_SOLVE_STATIC_MAX_N + 1
+    assert lib.sfft_solve_static(fake, fake, big, B.SFFT_PREC_FP64, fake, None, None) == B.SFFT_ERR_UNSUPPORTED
+    assert lib.sfft_solve_static(fake, fake, 0, B.SFFT_PREC_FP64, fake, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_static(fake, fake, -3, B.SFFT_PREC_MIXED, fake, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_static(fake, fake, 16, 7, fake, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_static(None, fake, 16, B.SFFT_PREC_FP64, fake, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_static(fake, None, 16, B.SFFT_PREC_FP64, fake, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_static(fake, fake, 16, B.SFFT_PREC_FP64, None, None, None) == B.SFFT_ERR_INVALID
+    with pytest.raises(B.SfftError, match="exceeds SFFT_SOLVE_STATIC_MAX_N"):
+        B.sfft_solve_static(fake, fake, big, "fp64", fake)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_solve_matches_plan_solve(lib, case, precision):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, binding as B, info_from_bytes
+    n0, n1, w, dk, db, cpr = case
+    R = random_field(n0, n1, seed=n0 + w)
+    S = 0.8 * np.roll(R, (1, -1), axis=(0, 1)) + 0.3 * random_field(n0, n1, seed=n0 + w + 7)
+    plan = SfftPlan(n0, n1, w, w, dk, db, cpr, dtype="float64", precision=precision)
+    Rt = torch.from_numpy(R).to("cuda", torch.float64)
+    St = torch.from_numpy(S).to("cuda", torch.float64)
+    M, rhs = plan.build_system(Rt, St)
+    n = plan.n
+    assert n <= B.SFFT_SOLVE_STATIC_MAX_N
+    x_ref, info_ref = plan.solve(M, rhs)
+
+    stream = plan.stream
+    isz = ctypes.sizeof(B.sfft_solve_info)
+    xs = [torch.full((n,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    infos = [torch.zeros(isz, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    # two calls in a row on one stream; device memory must not change across the second
+    B.sfft_solve_static(M, rhs, n, precision, xs[0], infos[0], stream)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    B.sfft_solve_static(M, rhs, n, precision, xs[1], infos[1], stream)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, "sfft_solve_static changed the device's free memory"
+
+    xr = x_ref.cpu().numpy()
+    ir = info_from_bytes(info_ref.cpu().numpy())
+    assert ir["status"] == B.SFFT_OK
+    scale = float(np.abs(xr).max())
+    for x, info in zip(xs, infos):
+        xv = x.cpu().numpy()
+        iv = info_from_bytes(info.cpu().numpy())
+        assert iv["status"] == B.SFFT_OK, iv
+        assert iv["iters"] == ir["iters"]
+        assert np.all(np.isfinite(xv))
+        assert float(np.abs(xv - xr).max()) <= 1e-12 * scale
+    plan.close()
