@@ -1,7 +1,10 @@
 """Benchmark: image-pair subtractions/s at 4096^2 through the GB300 SFFT path.
 
 One step = one whole image pair through the hot path (build the system,
-solve it, subtract) on device-resident inputs.  Default workload: the
+solve it, subtract) on device-resident inputs.  The headline runs the
+serving path (sfft_submit: --depth pairs in flight, their systems solved
+--batch at a time in one launch); the one-pair-at-a-time path
+(sfft_run_pair) is reported beside it, with its per-pair latency.  Default workload: the
 4096^2 float32 wide-field pair (20000 sources, w=8, D_K=D_B=2, constant
 photometric ratio, 1735 unknowns), mixed precision.
 
@@ -41,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
+    ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
+    ap.add_argument("--batch", type=int, default=4, help="systems solved per launch in the serving path")
     return ap.parse_args()
 
 
@@ -277,26 +282,63 @@ def run_ours(args):
     except Exception:
         bus = None
     sampler = ClockSampler(bus)
+
+    # serving path: args.depth pairs in flight; outputs alternate between two buffer sets
+    from paper_2109_09334_gb300 import SfftServer
+    srv = SfftServer(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
+                     precision=args.precision, depth=args.depth, batch=args.batch)
+    cur = torch.cuda.current_stream(dev)
+    outs = [(torch.empty_like(D), torch.empty_like(x), torch.zeros_like(info)) for _ in range(2)]
+
+    def submit(k):
+        Rt, St = dev_pairs[k & 1]
+        Dk, xk, ik = outs[k & 1]
+        return srv.submit(Rt, St, diff=Dk, x=xk, info=ik, stream=cur)[0]
+
+    for k in range(args.warmup):
+        t = submit(k)
+    srv.wait(t)
+    for _, _, ik in outs:
+        inf_s = info_from_bytes(ik.cpu().numpy())
+        if inf_s["status"] != 0:
+            raise RuntimeError(f"solve status {inf_s}")
+
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     launches0 = binding.sfft_plan_launch_count(plan.handle)
+    slaunch0 = srv.launch_count
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.25)
+    # sequential: one pair at a time on one stream (per-pair latency)
     evs[0].record(stream)
     for k in range(args.steps):
         step(k)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    launches = binding.sfft_plan_launch_count(plan.handle) - launches0
-    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
+    # serving: the timed region is ordered on `cur` before the first and after the last request
+    es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    es0.record(cur)
+    for k in range(args.steps):
+        t = submit(k)
+    srv.stream_wait(t, cur)
+    es1.record(cur)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    srv.wait(t)
+    launches = srv.launch_count - slaunch0
+    seq_launches = binding.sfft_plan_launch_count(plan.handle) - launches0
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    seq_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = es0.elapsed_time(es1)
+    if world > 1:
+        t = torch.tensor([total_ms, seq_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms, seq_ms = float(t[0].item()), float(t[1].item())
     value = world * args.steps / (total_ms / 1e3)
     ms_step = total_ms / args.steps
     P = spec.n0 * spec.n1
@@ -309,7 +351,11 @@ def run_ours(args):
               "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                          "reasons": clocks["reasons"], "samples": clocks["samples"]},
               "mpix_per_s": value * P / 1e6,
-              "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+              "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                             "note": "one pair alone (sfft_run_pair), device-timed per step"},
+              "serving": {"api": "sfft_submit", "depth": args.depth, "batch": args.batch, "ms_per_pair": ms_step},
+              "sequential": {"api": "sfft_run_pair", "value": world * args.steps / (seq_ms / 1e3),
+                             "ms_per_pair": seq_ms / args.steps, "gpu_launches": int(seq_launches)},
               "solve": inf}
 
     # per-stage times: replay each stage of the last pair with events on the plan's stream
@@ -359,28 +405,49 @@ def run_ours(args):
         result["pair_roofline"] = {"alg_bytes_per_pair": ba, "achieved_GBs": ba / (ms_step / 1e3) / 1e9,
                                    "frac": ba / (ms_step / 1e3) / 1e9 / peak}
 
-    # end to end through the host entry point: pinned host buffers, copies inside the timed region
+    # end to end through the serving API with host requests: pinned host buffers, the
+    # host->device copies of each pair's inputs and the device->host copies of its
+    # difference image, coefficients and status inside the timed region
     if not args.no_e2e:
-        Rh = torch.from_numpy(pairs[0][0]).pin_memory()
-        Sh = torch.from_numpy(pairs[0][1]).pin_memory()
-        Dh = torch.empty((spec.n0, spec.n1), dtype=Rh.dtype).pin_memory()
-        xh = torch.empty(plan.n, dtype=torch.float64).pin_memory()
-        plan.run_pair_host(Rh, Sh, x_out=xh, diff_out=Dh)
-        ke = max(3, min(args.steps, 30))
+        pin = [(torch.from_numpy(R).pin_memory(), torch.from_numpy(S).pin_memory()) for R, S in pairs]
+        hout = [(torch.empty((spec.n0, spec.n1), dtype=pin[0][0].dtype).pin_memory(),
+                 torch.empty(plan.n, dtype=torch.float64).pin_memory(),
+                 torch.zeros(24, dtype=torch.uint8).pin_memory()) for _ in range(args.depth + 1)]
+
+        def submit_host(k):
+            Rh, Sh = pin[k & 1]
+            Dh, xh, ih = hout[k % len(hout)]
+            return srv.submit(Rh, Sh, diff=Dh, x=xh, info=ih)[0]
+
+        # a request's host outputs are reused only after it has completed
+        def run_host(count):
+            tickets = []
+            for k in range(count):
+                if k >= len(hout):
+                    srv.wait(tickets[k - len(hout)])
+                tickets.append(submit_host(k))
+            srv.wait(tickets[-1])
+
+        run_host(3)
+        ke = max(3, min(args.steps, 50))
         if world > 1:
             torch.distributed.barrier()
         t0 = time.perf_counter()
-        for _ in range(ke):
-            _, _, inf2 = plan.run_pair_host(Rh, Sh, x_out=xh, diff_out=Dh)
+        run_host(ke)
         te = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([te], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             te = float(t.item())
+        inf_h = info_from_bytes(hout[(ke - 1) % len(hout)][2].numpy())
+        if inf_h["status"] != 0:
+            raise RuntimeError(f"host-request solve status {inf_h}")
+        Rh = pin[0][0]
         bi = Rh.numel() * Rh.element_size() * 2
-        bo = Dh.numel() * Dh.element_size() + xh.numel() * 8 + 24
+        bo = Rh.numel() * Rh.element_size() + plan.n * 8 + 24
         result["e2e"] = {"value": world * ke / te, "unit": UNIT, "h2d_bytes_per_step": bi,
-                         "d2h_bytes_per_step": bo, "steps": ke}
+                         "d2h_bytes_per_step": bo, "steps": ke, "api": "sfft_submit (host requests)",
+                         "clock": "host wall clock, submit of the first to completion of the last"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -393,6 +460,7 @@ def run_ours(args):
                                             f"with the same fit (n={plan.n}); lag-sum and stencil time scaled "
                                             f"x{smp['scale']:.0f} by pixel count, solve time as measured",
                                   "t_sample_s": round(smp["t_build"] + smp["t_solve"] + smp["t_sub"], 2)}
+    srv.close()
     plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()

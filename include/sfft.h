@@ -129,7 +129,7 @@ int sfft_build_system(sfft_plan_t plan, const void *d_ref, const void *d_sci,
  * Solve M theta = rhs (Eq. 18; the paper names no solver).  FP64 precision:
  * Cholesky in FP64.  Mixed precision: Jacobi scaling, Cholesky in FP32, then
  * iterative refinement with FP64 residuals r = rhs - M theta until
- * ||r|| / ||rhs|| <= 1e-12 or 30 iterations.
+ * ||r|| / ||rhs|| <= 1e-12, at most 12 iterations (else SFFT_ERR_NOT_CONVERGED).
  *   d_M, d_rhs : as written by sfft_build_system (read only).
  *   d_x        : n doubles, the coefficients theta in the unknown order above.
  *   d_info     : device sfft_solve_info, or NULL.
@@ -196,6 +196,80 @@ int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci,
                        const uint8_t *h_mask, double *h_x, sfft_solve_info *h_info,
                        void *h_diff, sfft_stream_t stream);
 
+/* ---- serving: several pairs in flight ------------------------------------ */
+/*
+ * The paper subtracts pair after pair (Sec. 3); a server keeps up to `depth`
+ * pairs of one configuration in flight and solves their systems `batch` at a
+ * time in one launch.  The solve is a latency-bound chain of small steps, so
+ * a batch of systems costs little more than one.  Each pair runs the kernels
+ * of sfft_run_pair on its own workspace, and the batched solve performs, for
+ * each system, the operations of the single solve in the same order, so the
+ * results equal sfft_run_pair's.  Requests complete in submission order.
+ */
+typedef struct sfft_server_s *sfft_server_t;
+
+typedef enum { SFFT_REQ_DEVICE = 0, SFFT_REQ_HOST = 1 } sfft_request_memory;
+
+typedef struct {
+    int32_t memory;         /* sfft_request_memory: where all six buffers below live */
+    const void *ref;        /* n0*n1 image of cfg.dtype */
+    const void *sci;        /* n0*n1 image of cfg.dtype */
+    const uint8_t *mask;    /* n0*n1 bytes or NULL (as sfft_build_system) */
+    double *x;              /* n doubles or NULL */
+    sfft_solve_info *info;  /* or NULL */
+    void *diff;             /* n0*n1 output image; may not alias ref or sci */
+    sfft_stream_t stream;   /* SFFT_REQ_DEVICE: ref, sci and mask are ready in this
+                               stream's order (NULL: the legacy default stream).
+                               Ignored for SFFT_REQ_HOST. */
+} sfft_request;
+
+typedef struct {
+    uint64_t seq; /* submission number, from 0 */
+} sfft_ticket;
+
+/*
+ * Create a server with `depth` (1..8) slots, each a full plan workspace plus
+ * staging buffers for host requests (sfft_server_workspace_bytes), and its
+ * own streams; systems are solved `batch` (1..depth) at a time.
+ * Synchronises once its tables are ready.
+ */
+int sfft_server_create(const sfft_config *cfg, int32_t depth, int32_t batch, sfft_server_t *out);
+
+/* Waits for all submitted requests, then frees everything.  NULL is a no-op. */
+int sfft_server_destroy(sfft_server_t server);
+
+/* Device bytes held by the server. */
+int sfft_server_workspace_bytes(sfft_server_t server, uint64_t *bytes);
+
+/*
+ * Enqueue one pair and return at once with its ticket.  Its build starts at
+ * once; its solve and subtraction are enqueued when its batch is complete, on
+ * sfft_flush, or when the caller polls or waits for it.  The caller keeps
+ * every buffer of the request valid and unchanged (outputs unread) until the
+ * ticket completes; host buffers should be pinned for the copies to overlap.
+ * Blocks only while 64 requests are already pending.  Thread-safe.
+ */
+int sfft_submit(sfft_server_t server, const sfft_request *req, sfft_ticket *ticket);
+
+/* Enqueue the solves and subtractions of an incomplete batch now. */
+int sfft_flush(sfft_server_t server);
+
+/* SFFT_OK if the ticket's request has completed, SFFT_ERR_BUSY if not yet. */
+int sfft_poll(sfft_server_t server, const sfft_ticket *ticket);
+
+/*
+ * Wait until the ticket's request has completed: SFFT_OK, or
+ * SFFT_ERR_TIMEOUT after timeout_us microseconds (timeout_us < 0: no limit).
+ * Numerical failures are reported in the request's info, as for sfft_solve.
+ */
+int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_us);
+
+/*
+ * Make `stream` wait (on the device, without blocking the host) until the
+ * ticket's request has completed, e.g. before a kernel that reads its diff.
+ */
+int sfft_stream_wait_ticket(sfft_server_t server, const sfft_ticket *ticket, sfft_stream_t stream);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Stages of one pair, as re-enqueued by sfft_replay_stage. */
@@ -211,6 +285,9 @@ typedef enum {
 
 /* Number of kernels this plan has enqueued since it was created. */
 int sfft_plan_launch_count(sfft_plan_t plan, uint64_t *count);
+
+/* Number of kernels a server's slots have enqueued since it was created. */
+int sfft_server_launch_count(sfft_server_t server, uint64_t *count);
 
 /*
  * Enqueue one stage of the most recent sfft_run_pair on this plan again, on

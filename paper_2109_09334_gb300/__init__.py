@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 
 from . import binding
+from .binding import make_request  # noqa: F401
 from .binding import (  # noqa: F401
     SfftError,
     make_config,
@@ -24,7 +25,15 @@ from .binding import (  # noqa: F401
     sfft_plan_workspace_bytes,
     sfft_run_pair,
     sfft_run_pair_host,
+    sfft_server_create,
+    sfft_server_destroy,
+    sfft_server_workspace_bytes,
+    sfft_poll,
     sfft_solve,
+    sfft_solve_static,
+    sfft_stream_wait_ticket,
+    sfft_submit,
+    sfft_wait,
     sfft_solve_info,
     sfft_subtract,
     status_string,
@@ -123,3 +132,92 @@ class SfftPlan:
         sfft_run_pair_host(self.handle, ref, sci, mask, x, info, D, self.stream)
         return D, x, {"status": info.status, "iters": info.iters, "rel_residual": info.rel_residual,
                       "min_pivot": info.min_pivot}
+
+
+class SfftServer:
+    """Several pairs of one configuration in flight (sfft_submit / sfft_poll / sfft_wait).
+
+    Tensors on the GPU make device requests (inputs ready in ``stream``'s
+    order, by default torch's current stream); CPU tensors (pinned for
+    overlap) make host requests.  The server keeps every tensor of a request
+    alive until its ticket has been waited for.
+    """
+
+    def __init__(self, n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed", depth=2,
+                 batch=1):
+        torch = _torch()
+        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        self.n = sfft_num_unknowns(self.cfg)
+        self.shape = (n0, n1)
+        self.dtype = {"float32": torch.float32, "f32": torch.float32,
+                      "float64": torch.float64, "f64": torch.float64}[str(dtype)]
+        self.handle = sfft_server_create(self.cfg, depth, batch)
+        self._pending = {}
+
+    @property
+    def workspace_bytes(self):
+        return sfft_server_workspace_bytes(self.handle)
+
+    def submit(self, ref, sci, mask=None, diff=None, x=None, info=None, stream=None):
+        """Enqueue one pair; returns (ticket, diff, x, info) with the outputs still being written."""
+        torch = _torch()
+        host = not ref.is_cuda
+        dev = "cpu" if host else ref.device
+        for t in (ref, sci):
+            assert t.dtype == self.dtype and tuple(t.shape) == self.shape and t.is_contiguous()
+            assert t.is_cuda != host
+        pin = dict(pin_memory=True) if host else {}
+        if diff is None:
+            diff = torch.empty(self.shape, dtype=self.dtype, device=dev, **pin)
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=dev, **pin)
+        if info is None:
+            info = torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=dev, **pin)
+        if stream is None and not host:
+            stream = torch.cuda.current_stream()
+        req = make_request(ref, sci, diff, mask=mask, x=x, info=info, stream=stream, host=host)
+        ticket = sfft_submit(self.handle, req)
+        self._pending[ticket.seq] = (req, ref, sci, mask, diff, x, info)
+        return ticket, diff, x, info
+
+    def _release(self, seq):
+        # requests complete in submission order
+        for k in [k for k in self._pending if k <= seq]:
+            del self._pending[k]
+
+    def poll(self, ticket):
+        done = sfft_poll(self.handle, ticket)
+        if done:
+            self._release(ticket.seq)
+        return done
+
+    def wait(self, ticket, timeout_us=-1):
+        done = sfft_wait(self.handle, ticket, timeout_us)
+        if done:
+            self._release(ticket.seq)
+        return done
+
+    @property
+    def launch_count(self):
+        return binding.sfft_server_launch_count(self.handle)
+
+    def flush(self):
+        binding.sfft_flush(self.handle)
+
+    def stream_wait(self, ticket, stream=None):
+        """Order `stream` (default: torch's current stream) after the ticket's request."""
+        if stream is None:
+            stream = _torch().cuda.current_stream()
+        sfft_stream_wait_ticket(self.handle, ticket, stream)
+
+    def close(self):
+        if self.handle:
+            sfft_server_destroy(self.handle)
+            self.handle = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,6 +28,7 @@ SFFT_STAGE_ROWS, SFFT_STAGE_COLS, SFFT_STAGE_GATHER, SFFT_STAGE_LAGS, SFFT_STAGE
 STAGE_NAMES = ["rows", "cols", "gather", "lags", "solve", "subtract"]
 SFFT_PREC_FP64, SFFT_PREC_MIXED = 0, 1
 SFFT_SOLVE_STATIC_MAX_N = 1024
+SFFT_REQ_DEVICE, SFFT_REQ_HOST = 0, 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sfft.h")
 
@@ -40,6 +41,16 @@ class sfft_config(ctypes.Structure):
 class sfft_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("min_pivot", ctypes.c_double)]
+
+
+class sfft_request(ctypes.Structure):
+    _fields_ = [("memory", ctypes.c_int32), ("ref", ctypes.c_void_p), ("sci", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("x", ctypes.c_void_p), ("info", ctypes.c_void_p),
+                ("diff", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+class sfft_ticket(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_uint64)]
 
 
 class SfftError(RuntimeError):
@@ -71,6 +82,16 @@ def library():
         lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        reqp, tkp = ctypes.POINTER(sfft_request), ctypes.POINTER(sfft_ticket)
+        lib.sfft_server_create.argtypes = [cfgp, i32, i32, ctypes.POINTER(vp)]
+        lib.sfft_flush.argtypes = [vp]
+        lib.sfft_server_destroy.argtypes = [vp]
+        lib.sfft_server_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sfft_submit.argtypes = [vp, reqp, tkp]
+        lib.sfft_poll.argtypes = [vp, tkp]
+        lib.sfft_wait.argtypes = [vp, tkp, ctypes.c_int64]
+        lib.sfft_stream_wait_ticket.argtypes = [vp, tkp, vp]
+        lib.sfft_server_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
         _lib = lib
@@ -173,6 +194,66 @@ def sfft_run_pair(plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, s
 def sfft_run_pair_host(plan, h_ref, h_sci, h_mask, h_x, h_info, h_diff, stream=None):
     _check(library().sfft_run_pair_host(plan, _p(h_ref), _p(h_sci), _p(h_mask), _p(h_x), _p(h_info),
                                         _p(h_diff), _s(stream)), "sfft_run_pair_host")
+
+
+def sfft_server_create(cfg, depth=2, batch=1):
+    h = ctypes.c_void_p()
+    _check(library().sfft_server_create(ctypes.byref(cfg), int(depth), int(batch), ctypes.byref(h)),
+           "sfft_server_create")
+    return h.value
+
+
+def sfft_flush(server):
+    _check(library().sfft_flush(server), "sfft_flush")
+
+
+def sfft_server_destroy(server):
+    _check(library().sfft_server_destroy(server), "sfft_server_destroy")
+
+
+def sfft_server_workspace_bytes(server):
+    b = ctypes.c_uint64()
+    _check(library().sfft_server_workspace_bytes(server, ctypes.byref(b)), "sfft_server_workspace_bytes")
+    return b.value
+
+
+def make_request(ref, sci, diff, mask=None, x=None, info=None, stream=None, host=False):
+    return sfft_request(SFFT_REQ_HOST if host else SFFT_REQ_DEVICE, _p(ref), _p(sci), _p(mask), _p(x), _p(info),
+                        _p(diff), None if host else _s(stream))
+
+
+def sfft_submit(server, req):
+    t = sfft_ticket()
+    _check(library().sfft_submit(server, ctypes.byref(req), ctypes.byref(t)), "sfft_submit")
+    return t
+
+
+def sfft_poll(server, ticket):
+    """True if the ticket's request has completed."""
+    rc = library().sfft_poll(server, ctypes.byref(ticket))
+    if rc == SFFT_ERR_BUSY:
+        return False
+    _check(rc, "sfft_poll")
+    return True
+
+
+def sfft_wait(server, ticket, timeout_us=-1):
+    """True once completed; False on timeout."""
+    rc = library().sfft_wait(server, ctypes.byref(ticket), int(timeout_us))
+    if rc == SFFT_ERR_TIMEOUT:
+        return False
+    _check(rc, "sfft_wait")
+    return True
+
+
+def sfft_stream_wait_ticket(server, ticket, stream=None):
+    _check(library().sfft_stream_wait_ticket(server, ctypes.byref(ticket), _s(stream)), "sfft_stream_wait_ticket")
+
+
+def sfft_server_launch_count(server):
+    c = ctypes.c_uint64()
+    _check(library().sfft_server_launch_count(server, ctypes.byref(c)), "sfft_server_launch_count")
+    return c.value
 
 
 def sfft_plan_launch_count(plan):

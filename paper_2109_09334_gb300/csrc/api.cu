@@ -49,7 +49,7 @@ __global__ void k_poly_dft(int n, int nout, int pmax, const cpx<double> *tw, int
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-static int validate(const sfft_config *c) {
+int plan_validate(const sfft_config *c) {
     if (!c) return SFFT_ERR_INVALID;
     if (!is_pow2(c->n0) || !is_pow2(c->n1)) return SFFT_ERR_UNSUPPORTED;
     if (c->n0 < 16 || c->n1 < 16 || c->n0 > 4096 || c->n1 > 4096) return SFFT_ERR_UNSUPPORTED;
@@ -68,9 +68,9 @@ static int unknowns(const sfft_config *c) {
     return c->const_phot_ratio ? nk * (L - 1) + 1 + nb : nk * L + nb;
 }
 
-static void free_plan(Plan *p) {
+void plan_free(Plan *p) {
     void *bufs[] = {p->tw0, p->tw1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
-                    p->lag, p->A, p->Wm, p->Tm, p->dscale, p->r, p->xw, p->yv, p->zv, p->flag, p->M_own, p->rhs_own,
+                    p->lag, p->A, p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own,
                     p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -81,13 +81,13 @@ static void free_plan(Plan *p) {
     do {                                                              \
         if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {    \
             cudaGetLastError();                                       \
-            free_plan(p);                                             \
+            plan_free(p);                                             \
             return SFFT_ERR_OOM;                                      \
         }                                                             \
         p->ws_bytes += (bytes);                                       \
     } while (0)
 
-static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
+int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     Plan *p = new (std::nothrow) Plan();
     if (!p) return SFFT_ERR_OOM;
     memset((void *)p, 0, sizeof(Plan));
@@ -154,16 +154,14 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->lag, nlag * sizeof(double));
     SFFT_ALLOC(p->A, n * n * rsz);
     SFFT_ALLOC(p->Wm, n * n * rsz);
-    SFFT_ALLOC(p->Tm, n * n * rsz);
     p->solve_grid = solve_grid_size(p->fp64);
-    if (p->solve_grid <= 0 || p->solve_grid > 256) {
-        free_plan(p);
+    if (p->solve_grid <= 0 || p->solve_grid > kMaxSolveGrid) {
+        plan_free(p);
         return SFFT_ERR_CUDA;
     }
     SFFT_ALLOC(p->dscale, n * sizeof(double));
     SFFT_ALLOC(p->r, n * sizeof(double));
-    SFFT_ALLOC(p->xw, (n + 800) * sizeof(double));  // x, stats, per-block partials, kernel sums
-    SFFT_ALLOC(p->yv, (size_t)((n + 31) / 32) * 32 * 32 * rsz);  // diagonal-block inverses
+    SFFT_ALLOC(p->xw, (n + kSolveTail + 64) * sizeof(double));  // x, stats, per-block partials, kernel sums
     SFFT_ALLOC(p->zv, solve_vec_elems((int)n) * rsz);
     SFFT_ALLOC(p->flag, 4 * sizeof(int));
     SFFT_ALLOC(p->M_own, n * n * sizeof(double));
@@ -175,7 +173,7 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     // constant tables
     cudaError_t err;
     if ((err = cudaMemcpyAsync(p->pairs, p->host_pairs, np * sizeof(PairDesc), cudaMemcpyHostToDevice, s))) {
-        free_plan(p);
+        plan_free(p);
         return SFFT_ERR_CUDA;
     }
     double csum[16];
@@ -188,7 +186,7 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     }
     // csum is copied from a host stack array: make the copy synchronous
     if ((err = cudaMemcpy(p->mom + 24 * 7, csum, sizeof(csum), cudaMemcpyHostToDevice))) {
-        free_plan(p);
+        plan_free(p);
         return SFFT_ERR_CUDA;
     }
     cpx<double> *t64a = nullptr, *t64b = nullptr;
@@ -196,7 +194,7 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         cudaMalloc((void **)&t64b, p->n1 * sizeof(cpx<double>)) != cudaSuccess) {
         cudaGetLastError();
         if (t64a) cudaFree(t64a);
-        free_plan(p);
+        plan_free(p);
         return SFFT_ERR_OOM;
     }
     k_twiddle64<<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a);
@@ -218,14 +216,14 @@ static int create(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     cudaFree(t64a);
     cudaFree(t64b);
     if (err != cudaSuccess) {
-        free_plan(p);
+        plan_free(p);
         return SFFT_ERR_CUDA;
     }
     *out = p;
     return SFFT_OK;
 }
 
-static int status_of(cudaError_t e) {
+int status_of(cudaError_t e) {
     if (e == cudaSuccess) return SFFT_OK;
     if (e == cudaErrorMemoryAllocation) return SFFT_ERR_OOM;
     return SFFT_ERR_CUDA;
@@ -288,10 +286,10 @@ int sfft_num_unknowns(const sfft_config *cfg, int32_t *n) {
 int sfft_plan_create(const sfft_config *cfg, sfft_stream_t stream, sfft_plan_t *out) {
     if (!out) return SFFT_ERR_INVALID;
     *out = nullptr;
-    int v = validate(cfg);
+    int v = plan_validate(cfg);
     if (v) return v;
     Plan *p = nullptr;
-    int rc = create(cfg, (cudaStream_t)stream, &p);
+    int rc = plan_new(cfg, (cudaStream_t)stream, &p);
     if (rc == SFFT_OK) *out = (sfft_plan_t)p;
     return rc;
 }
@@ -300,7 +298,7 @@ int sfft_plan_destroy(sfft_plan_t plan) {
     if (!plan) return SFFT_OK;
     Plan *p = (Plan *)plan;
     cudaStreamSynchronize(p->last_stream);
-    free_plan(p);
+    plan_free(p);
     return SFFT_OK;
 }
 

@@ -12,6 +12,12 @@ namespace sfft {
 // r in [0, NA)): min(64, n0).
 constexpr int kMaxNA = 64;
 
+// Cooperative solve grid: at most kMaxSolveGrid blocks.  The plan's vector
+// xw holds x (n), then the solve's statistics (8) and per-block partial sums
+// (2 per block), then the subtraction's kernel sums.
+constexpr int kMaxSolveGrid = 512;
+constexpr int kSolveTail = 8 + 2 * kMaxSolveGrid;
+
 enum PairKind { PK_OMEGA = 0, PK_LAMBDA = 1, PK_THETA = 2 };
 
 // One spectrum product transformed in the gather: conj(U_a) * V_b where V_b
@@ -48,11 +54,10 @@ struct Plan {
     int lag_om, lag_la, lag_th;  // offsets into lag
     // solve workspace
     void *A;               // n*n factor (compute type)
-    void *Wm, *Tm;         // n*n: W = L^-1 and a GEMM temporary (compute type)
+    void *Wm;              // n*n: W = L^-1 (compute type)
     int solve_grid;        // blocks of the cooperative solve kernel (one per SM)
     double *dscale;        // n Jacobi scales
     double *r, *xw;        // n residual, n iterate
-    void *yv;              // [n/32][32][32] inverses of the diagonal Cholesky blocks (compute type)
     void *zv;              // n vector (compute type)
     int *flag;             // device status word for the solve
     // owned buffers for run_pair(_host)
@@ -73,6 +78,12 @@ struct Plan {
     PairDesc host_pairs[256];
 };
 
+// plans (api.cu): validation, allocation + tables, release
+int plan_validate(const sfft_config *c);
+int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out);  // cfg already validated
+void plan_free(Plan *p);
+int status_of(cudaError_t e);
+
 // launchers (return cudaError_t of the last launch)
 cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M,
                          double *rhs, cudaStream_t s);
@@ -81,6 +92,10 @@ cudaError_t row_transform(Plan *p, const void *ref, const void *sci, const uint8
 cudaError_t build_stage(Plan *p, int stage, double *M, double *rhs, cudaStream_t s);
 cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
                          sfft_solve_info *info, cudaStream_t s);
+// Solve the systems of `count` (1..8) plans of the same size together in
+// one cooperative launch (on the grid of plans[0]).
+cudaError_t solve_batch(Plan *const *plans, int count, const double *const *M, const double *const *rhs,
+                        double *const *x, sfft_solve_info *const *info, cudaStream_t s);
 int solve_grid_size(bool fp64);
 size_t solve_vec_elems(int n);
 // Solve workspace given by the caller instead of a plan (sizes for n

@@ -1,0 +1,381 @@
+// server.cu -- sfft_submit / sfft_poll / sfft_wait: several pairs in flight.
+//
+// A server holds `depth` slots, each a full plan (its own spectra, lag
+// tables, M, rhs and solve workspace) plus staging buffers for requests in
+// host memory, and three streams:
+//   sc  copies of host requests' inputs to the slot's staging buffers;
+//   sb  the build of each pair (row/column FFTs, gather, lag sums, assembly);
+//   ss  (highest priority) the solves, the subtractions and the copies of
+//       the results back to host requests.
+// Request s uses slot s mod depth.  Its build is enqueued at once; the
+// requests are grouped `batch` at a time (batch <= depth), and when a group
+// is complete (or on sfft_flush, or when a caller waits for one of its
+// requests) one cooperative launch solves all of its systems together and
+// the group's subtractions follow.  The solve is a latency-bound chain of
+// grid-wide steps, so solving several systems in one launch costs little
+// more than solving one.  Events order the streams:
+//   built[i]: sb -> ss (M, rhs of the slot ready);
+//   done[i]:  ss -> sb, sc (the slot's previous pair is finished, so its
+//             workspace and staging buffers may be overwritten).
+// A slot is reused only by a request of a later group, whose predecessor's
+// group is complete and therefore flushed, so `done` is always recorded
+// before anything waits on it.  Every pair runs the kernels of
+// sfft_run_pair on its own slot, so its results are the same.
+//
+// Completion: every request records an event on ss after its last
+// operation.  ss is in order, so requests complete in submission order and
+// a watermark (all requests below it are complete) answers sfft_poll.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <thread>
+
+#include "internal.h"
+
+namespace sfft {
+namespace {
+
+constexpr int kMaxDepth = 8;
+constexpr int kRing = 64;  // completion events kept; submit waits beyond this
+
+struct Slot {
+    Plan *plan = nullptr;
+    void *ref = nullptr, *sci = nullptr, *diff = nullptr;  // staging for host requests
+    uint8_t *mask = nullptr;
+    cudaEvent_t built = nullptr, done = nullptr, copied = nullptr;
+    // the request built in this slot and not yet flushed
+    bool host = false;
+    const void *in_ref = nullptr, *in_sci = nullptr;  // device images the build read
+    const uint8_t *in_mask = nullptr;
+    double *x = nullptr;
+    sfft_solve_info *info = nullptr;
+    void *diff_out = nullptr;  // device difference image
+    sfft_request req;          // the caller's request (host destinations)
+};
+
+}  // namespace
+
+struct Server {
+    sfft_config cfg;
+    int depth = 0, batch = 1;
+    size_t img_bytes = 0, pixels = 0;
+    Slot slots[kMaxDepth];
+    cudaStream_t sc = nullptr, sb = nullptr, ss = nullptr;
+    cudaEvent_t input_ready = nullptr;
+    cudaEvent_t ring[kRing] = {};
+    uint64_t next_seq = 0;   // sequence number of the next request
+    uint64_t flushed = 0;    // every request below it has its solve and subtraction enqueued
+    uint64_t watermark = 0;  // every request below it has completed
+    std::mutex mu;
+};
+
+namespace {
+
+void server_free(Server *v) {
+    for (int i = 0; i < kMaxDepth; ++i) {
+        Slot &s = v->slots[i];
+        if (s.plan) plan_free(s.plan);
+        void *bufs[] = {s.ref, s.sci, s.diff, s.mask};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        cudaEvent_t evs[] = {s.built, s.done, s.copied};
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+    }
+    for (cudaEvent_t e : v->ring)
+        if (e) cudaEventDestroy(e);
+    if (v->input_ready) cudaEventDestroy(v->input_ready);
+    cudaStream_t sts[] = {v->sc, v->sb, v->ss};
+    for (cudaStream_t s : sts)
+        if (s) cudaStreamDestroy(s);
+    delete v;
+}
+
+// Advance the watermark over completed requests (caller holds mu).  Only
+// flushed requests have their completion event recorded.
+void advance(Server *v) {
+    while (v->watermark < v->flushed) {
+        const cudaError_t e = cudaEventQuery(v->ring[v->watermark % kRing]);
+        if (e == cudaErrorNotReady) return;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        ++v->watermark;
+    }
+}
+
+int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
+    Server *v = new (std::nothrow) Server();
+    if (!v) return SFFT_ERR_OOM;
+    v->cfg = *cfg;
+    v->depth = depth;
+    v->batch = batch;
+    v->pixels = (size_t)cfg->n0 * cfg->n1;
+    v->img_bytes = v->pixels * (cfg->dtype == SFFT_F64 ? sizeof(double) : sizeof(float));
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->sc, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->sb, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->ss, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->input_ready, cudaEventDisableTiming);
+    for (int k = 0; k < kRing && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&v->ring[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        server_free(v);
+        return status_of(e);
+    }
+    for (int i = 0; i < depth; ++i) {
+        Slot &s = v->slots[i];
+        const int rc = plan_new(cfg, v->sb, &s.plan);
+        if (rc != SFFT_OK) {
+            s.plan = nullptr;
+            server_free(v);
+            return rc;
+        }
+        e = cudaMalloc(&s.ref, v->img_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&s.sci, v->img_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&s.diff, v->img_bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s.mask, v->pixels);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.built, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
+        // a fresh slot is free: let the first waits on `done` pass at once
+        if (e == cudaSuccess) e = cudaEventRecord(s.done, v->ss);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            server_free(v);
+            return status_of(e);
+        }
+    }
+    e = cudaStreamSynchronize(v->sb);  // plan tables are ready
+    if (e != cudaSuccess) {
+        server_free(v);
+        return status_of(e);
+    }
+    *out = v;
+    return SFFT_OK;
+}
+
+// Enqueue the solve (one batched launch) and the subtraction of every
+// request built but not yet flushed (caller holds mu).
+int flush(Server *v) {
+    const uint64_t first = v->flushed, end = v->next_seq;
+    const int cnt = (int)(end - first);
+    if (cnt == 0) return SFFT_OK;
+    Plan *plans[kMaxDepth];
+    const double *M[kMaxDepth], *rhs[kMaxDepth];
+    double *x[kMaxDepth];
+    sfft_solve_info *info[kMaxDepth];
+    for (int k = 0; k < cnt; ++k) {
+        Slot &s = v->slots[(first + k) % v->depth];
+        plans[k] = s.plan;
+        M[k] = s.plan->M_own;
+        rhs[k] = s.plan->rhs_own;
+        x[k] = s.x;
+        info[k] = s.info;
+    }
+    // sb is in order: the last build's event covers the earlier ones
+    cudaError_t e = cudaStreamWaitEvent(v->ss, v->slots[(end - 1) % v->depth].built, 0);
+    if (e == cudaSuccess) e = solve_batch(plans, cnt, M, rhs, x, info, v->ss);
+    for (int k = 0; k < cnt && e == cudaSuccess; ++k) {
+        const uint64_t seq = first + k;
+        Slot &s = v->slots[seq % v->depth];
+        Plan *p = s.plan;
+        if (s.in_mask) e = row_transform(p, s.in_ref, s.in_sci, nullptr, false, v->ss);
+        if (e == cudaSuccess) e = subtract_from_rows(p, s.x, s.diff_out, v->ss);
+        if (s.host) {
+            const sfft_request &r = s.req;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.diff, s.diff, v->img_bytes, cudaMemcpyDeviceToHost, v->ss);
+            if (e == cudaSuccess && r.x)
+                e = cudaMemcpyAsync(r.x, p->x_own, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost, v->ss);
+            if (e == cudaSuccess && r.info)
+                e = cudaMemcpyAsync(r.info, p->info_own, sizeof(sfft_solve_info), cudaMemcpyDeviceToHost, v->ss);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(s.done, v->ss);
+        if (e == cudaSuccess) e = cudaEventRecord(v->ring[seq % kRing], v->ss);
+    }
+    if (e != cudaSuccess) return status_of(e);
+    v->flushed = end;
+    return SFFT_OK;
+}
+
+int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
+    const bool host = r->memory == SFFT_REQ_HOST;
+    // keep at most kRing requests in flight: the ring slot must be free
+    while (v->next_seq - v->watermark >= (uint64_t)kRing) {
+        if (v->watermark >= v->flushed) {
+            const int rc = flush(v);
+            if (rc != SFFT_OK) return rc;
+        }
+        const cudaError_t e = cudaEventSynchronize(v->ring[v->watermark % kRing]);
+        if (e != cudaSuccess) return status_of(e);
+        advance(v);
+    }
+    const uint64_t seq = v->next_seq;
+    // the request that used this slot before belongs to an earlier, full,
+    // hence flushed batch (depth >= batch), so its `done` event is recorded
+    Slot &s = v->slots[seq % v->depth];
+    Plan *p = s.plan;
+    const void *ref = r->ref, *sci = r->sci;
+    const uint8_t *mask = r->mask;
+    cudaError_t e = cudaSuccess;
+    if (host) {
+        e = cudaStreamWaitEvent(v->sc, s.done, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.ref, r->ref, v->img_bytes, cudaMemcpyHostToDevice, v->sc);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.sci, r->sci, v->img_bytes, cudaMemcpyHostToDevice, v->sc);
+        if (e == cudaSuccess && r->mask) e = cudaMemcpyAsync(s.mask, r->mask, v->pixels, cudaMemcpyHostToDevice, v->sc);
+        if (e == cudaSuccess) e = cudaEventRecord(s.copied, v->sc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, s.copied, 0);
+        ref = s.ref;
+        sci = s.sci;
+        mask = r->mask ? s.mask : nullptr;
+    } else {
+        // the inputs are ready in the caller's stream order
+        e = cudaEventRecord(v->input_ready, (cudaStream_t)r->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, v->input_ready, 0);
+    }
+    // the slot's previous pair has finished with its workspace
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, s.done, 0);
+    if (e == cudaSuccess) e = build_system(p, ref, sci, mask, p->M_own, p->rhs_own, v->sb);
+    if (e == cudaSuccess) e = cudaEventRecord(s.built, v->sb);
+    if (e != cudaSuccess) return status_of(e);
+    s.host = host;
+    s.in_ref = ref;
+    s.in_sci = sci;
+    s.in_mask = mask;
+    s.x = (!host && r->x) ? r->x : p->x_own;
+    s.info = (!host && r->info) ? r->info : p->info_own;
+    s.diff_out = host ? s.diff : r->diff;
+    s.req = *r;
+    v->next_seq = seq + 1;
+    *seq_out = seq;
+    if (v->next_seq - v->flushed >= (uint64_t)v->batch) return flush(v);
+    return SFFT_OK;
+}
+
+}  // namespace
+}  // namespace sfft
+
+using namespace sfft;
+
+extern "C" {
+
+int sfft_server_create(const sfft_config *cfg, int32_t depth, int32_t batch, sfft_server_t *out) {
+    if (!out) return SFFT_ERR_INVALID;
+    *out = nullptr;
+    if (!cfg || depth < 1 || depth > kMaxDepth || batch < 1 || batch > depth) return SFFT_ERR_INVALID;
+    const int v = plan_validate(cfg);
+    if (v) return v;
+    Server *s = nullptr;
+    const int rc = create_server(cfg, depth, batch, &s);
+    if (rc == SFFT_OK) *out = (sfft_server_t)s;
+    return rc;
+}
+
+int sfft_server_destroy(sfft_server_t server) {
+    if (!server) return SFFT_OK;
+    Server *v = (Server *)server;
+    {
+        std::lock_guard<std::mutex> lock(v->mu);
+        flush(v);
+    }
+    cudaStreamSynchronize(v->sc);
+    cudaStreamSynchronize(v->sb);
+    cudaStreamSynchronize(v->ss);
+    server_free(v);
+    return SFFT_OK;
+}
+
+int sfft_submit(sfft_server_t server, const sfft_request *req, sfft_ticket *ticket) {
+    if (!server || !req || !ticket) return SFFT_ERR_INVALID;
+    if (!req->ref || !req->sci || !req->diff) return SFFT_ERR_INVALID;
+    if (req->memory != SFFT_REQ_DEVICE && req->memory != SFFT_REQ_HOST) return SFFT_ERR_INVALID;
+    if (req->diff == req->ref || req->diff == req->sci) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    uint64_t seq = 0;
+    const int rc = submit(v, req, &seq);
+    if (rc == SFFT_OK) ticket->seq = seq;
+    return rc;
+}
+
+int sfft_poll(sfft_server_t server, const sfft_ticket *ticket) {
+    if (!server || !ticket) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    if (ticket->seq >= v->next_seq) return SFFT_ERR_INVALID;
+    if (ticket->seq >= v->flushed) {
+        const int rc = flush(v);
+        if (rc != SFFT_OK) return rc;
+    }
+    advance(v);
+    return ticket->seq < v->watermark ? SFFT_OK : SFFT_ERR_BUSY;
+}
+
+int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_us) {
+    if (!server || !ticket) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lock(v->mu);
+            if (ticket->seq >= v->next_seq) return SFFT_ERR_INVALID;
+            if (ticket->seq >= v->flushed) {
+                const int rc = flush(v);
+                if (rc != SFFT_OK) return rc;
+            }
+            advance(v);
+            if (ticket->seq < v->watermark) return SFFT_OK;
+        }
+        if (timeout_us >= 0) {
+            const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (us >= timeout_us) return SFFT_ERR_TIMEOUT;
+        }
+        std::this_thread::yield();
+    }
+}
+
+int sfft_stream_wait_ticket(sfft_server_t server, const sfft_ticket *ticket, sfft_stream_t stream) {
+    if (!server || !ticket) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    if (ticket->seq >= v->next_seq) return SFFT_ERR_INVALID;
+    if (ticket->seq >= v->flushed) {
+        const int rc = flush(v);
+        if (rc != SFFT_OK) return rc;
+    }
+    // a ring event is reused only after the host has seen it complete
+    if (ticket->seq + kRing < v->next_seq) return SFFT_OK;
+    return status_of(cudaStreamWaitEvent((cudaStream_t)stream, v->ring[ticket->seq % kRing], 0));
+}
+
+int sfft_flush(sfft_server_t server) {
+    if (!server) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    return flush(v);
+}
+
+int sfft_server_launch_count(sfft_server_t server, uint64_t *count) {
+    if (!server || !count) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    uint64_t c = 0;
+    for (int i = 0; i < v->depth; ++i) c += v->slots[i].plan->launches;
+    *count = c;
+    return SFFT_OK;
+}
+
+int sfft_server_workspace_bytes(sfft_server_t server, uint64_t *bytes) {
+    if (!server || !bytes) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    uint64_t b = 0;
+    for (int i = 0; i < v->depth; ++i) b += v->slots[i].plan->ws_bytes + 3 * v->img_bytes + v->pixels;
+    *bytes = b;
+    return SFFT_OK;
+}
+
+}  // extern "C"

@@ -7,17 +7,20 @@
 //     r = rhs - M x (FP64),  x += D W^T W D r,
 // until ||r|| / ||rhs|| <= 1e-12.
 //
-// Everything runs in one cooperative (grid-synchronised) kernel with one
-// block per SM, so the ~n/32 dependent block steps cost a grid barrier each
+// Everything runs in one cooperative (grid-synchronised) kernel with two
+// blocks per SM, so the ~n/32 dependent block steps cost a grid barrier each
 // instead of a kernel launch:
-//   * Cholesky, right-looking with 32-wide panels: phase P solves for the
-//     panel L_ik = A_ik L_kk^-T, one thread per row; phase U applies
-//     A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64 tiles.  The
-//     block that updates the tile holding the next diagonal block factors it
-//     right away (one warp, registers and shuffles).
-//   * W = L^-1 is formed in the same sweep (forward elimination applied to
-//     the identity): phase P also sets W_k = L_kk^-1 W_k for block row k (one
-//     thread per column) and phase U applies W_i -= L_ik W_k below.
+//   * Cholesky, right-looking with 32-wide panels.  The block that updates
+//     the tile holding the next diagonal block factors it right away and
+//     inverts the factor in the same sweep (rolled loops in shared memory,
+//     so the short serial chain stays in the instruction cache).  Phase P
+//     then forms the panel L_ik = A_ik L_kk^-T as 64x32 GEMM tiles; phase U
+//     applies A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64
+//     tiles.
+//   * W = L^-1 is formed in the same sweep (block forward elimination applied
+//     to the identity): W_kk = L_kk^-1 from the diagonal factorisation, phase
+//     P sets W_k[:, 0:k0] = L_kk^-1 W_k[:, 0:k0] and phase U applies
+//     W_i -= L_ik W_k below.
 //   * refinement: residual GEMV in FP64 and two GEMVs with W.
 // Every control decision after a barrier uses values written before it, so
 // all blocks execute the same sequence of barriers.
@@ -37,13 +40,15 @@ constexpr int kTile = 64;       // trailing-update and GEMM output tile
 constexpr int kMaxIters = 12;   // refinement iterations
 constexpr double kTol = 1e-12;  // ||r|| / ||rhs||
 constexpr int kThreads = 256;
+constexpr int kBlocksPerSM = 2;  // resident FP32 solve blocks per SM (more loads in flight); FP64 takes 1
 constexpr int kSeg = 8;         // row segments of the W^T y product
+constexpr int kMaxBatch = 8;    // systems solved together by one launch
 
 template <typename T>
 struct SolveArgs {
     int n, nblk;
     const double *M, *rhs;
-    double *dsc, *x, *r, *part, *stats;  // part: 2 * gridDim doubles; stats[0..3]
+    double *dsc, *x, *r, *stats;  // stats[0..3]
     T *A, *W, *z, *y, *wseg;
     int *flag;  // [0] status (0 running, 1 converged, <0 failure), [1] iterations
     double *xout;
@@ -99,91 +104,212 @@ __device__ void tile_gemm(T (&acc)[4][4], TileSmem<T> &sm, const T *Ag, int lda,
     }
 }
 
-// One warp factors the 32x32 diagonal block kb (already fully updated) in
-// registers: lane t holds row t; column steps broadcast by shuffles.  Writes
-// L_kk into A (zeros above the diagonal) and flags a non-positive pivot.
+// Shared memory of the diagonal-block factorisation (aliases the GEMM tiles):
+// four columns of S (by row) and four rows of Y (by column) per step,
+// double-buffered by step parity.
 template <typename T>
-__device__ __noinline__ void factor_diag(const SolveArgs<T> &s, int kb) {
-    const int t = threadIdx.x & 31;
+struct __align__(16) FactorSmem {
+    T col[2][kNB][4];
+    T row[2][kNB][4];
+};
+
+template <typename T>
+union SolveSmem {
+    TileSmem<T> tile;
+    FactorSmem<T> fac;
+};
+
+template <typename T>
+__device__ __forceinline__ T pick4(const T (&v)[4], int q) {
+    return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
+}
+
+// four consecutive values of shared memory (16-byte aligned)
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
+// 1 / sqrt(d): the FP32 factor only seeds the FP64 refinement, so the
+// hardware approximation serves; FP64 takes the correctly rounded path.
+__device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
+__device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
+
+// The whole block factors the 32x32 diagonal block kb (already fully
+// updated) and inverts its factor in the same sweep, four columns per step:
+// every thread factors the 4x4 pivot block itself, forms the L entries of the
+// rows it needs by forward substitution, and applies the rank-4 update to S
+// and the matching block forward elimination to Y (L Y = I, so Y ends as
+// L^-1).  Thread (t, u) = (tid / 8, tid % 8) keeps row t, columns u, u+8,
+// u+16, u+24 of S and Y in registers; each step publishes the next four
+// columns of S and rows of Y through shared memory (one barrier per step).
+// Writes L_kk into A and L_kk^-1 into W (zeros above the diagonal) and flags
+// a non-positive pivot.
+template <typename T>
+__device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb) {
+    const int tid = threadIdx.x;
     const int n = s.n, k0 = kb * kNB;
     const int nb = min(kNB, n - k0);
-    T a[kNB];
+    const int t = tid >> 3, u = tid & 7;
+    T sv[4], yv[4];
 #pragma unroll
-    for (int c = 0; c < kNB; ++c) {
+    for (int q = 0; q < 4; ++q) {
+        const int c = u + 8 * q;
         T v = (T)0;
         if (t < nb && c < nb) v = s.A[(size_t)(k0 + t) * n + k0 + c];
-        if (t >= nb && c == t) v = (T)1;  // identity beyond the matrix edge
-        a[c] = v;
+        else if (t == c) v = (T)1;  // identity beyond the matrix edge
+        sv[q] = v;
+        yv[q] = (t == c) ? (T)1 : (T)0;
+    }
+    if (u < 4) f.col[0][t][u] = sv[0];
+    if (t < 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f.row[0][u + 8 * q][t] = yv[q];
     }
     bool bad = false;
     T minpiv = (T)1e30;
+#pragma unroll 1
+    for (int jb = 0; jb < kNB; jb += 4) {
+        __syncthreads();  // columns jb..jb+3 of S and rows jb..jb+3 of Y are published
+        const int b = (jb >> 2) & 1;
+        T p0[4], p1[4], p2[4], p3[4], st[4], sc[4][4], yc[4][4];
+        ld4(f.col[b][jb], p0);
+        ld4(f.col[b][jb + 1], p1);
+        ld4(f.col[b][jb + 2], p2);
+        ld4(f.col[b][jb + 3], p3);
+        ld4(f.col[b][t], st);
 #pragma unroll
-    for (int j = 0; j < kNB; ++j) {
-        const T d = __shfl_sync(0xffffffffu, a[j], j);
-        if (!(d > (T)0)) bad = true;
-        const T l = sqrt(d > (T)0 ? d : (T)1);
-        if (j < nb && d < minpiv) minpiv = d;
-        if (t == j) a[j] = l;
-        if (t > j) a[j] = a[j] / l;
+        for (int q = 0; q < 4; ++q) {
+            ld4(f.col[b][u + 8 * q], sc[q]);
+            ld4(f.row[b][u + 8 * q], yc[q]);
+        }
+        // 4x4 Cholesky of the pivot block
+        const T d0 = p0[0];
+        const T i0 = inv_sqrt(d0 > (T)0 ? d0 : (T)1);
+        const T l10 = p1[0] * i0, l20 = p2[0] * i0, l30 = p3[0] * i0;
+        const T d1 = p1[1] - l10 * l10;
+        const T i1 = inv_sqrt(d1 > (T)0 ? d1 : (T)1);
+        const T l21 = (p2[1] - l20 * l10) * i1, l31 = (p3[1] - l30 * l10) * i1;
+        const T d2 = p2[2] - l20 * l20 - l21 * l21;
+        const T i2 = inv_sqrt(d2 > (T)0 ? d2 : (T)1);
+        const T l32 = (p3[2] - l30 * l20 - l31 * l21) * i2;
+        const T d3 = p3[3] - l30 * l30 - l31 * l31 - l32 * l32;
+        const T i3 = inv_sqrt(d3 > (T)0 ? d3 : (T)1);
+        const T dp[4] = {d0, d1, d2, d3};
 #pragma unroll
-        for (int c = j + 1; c < kNB; ++c) {
-            const T lcj = __shfl_sync(0xffffffffu, a[j], c);
-            if (t >= c) a[c] -= a[j] * lcj;
+        for (int p = 0; p < 4; ++p) {
+            if (!(dp[p] > (T)0)) bad = true;
+            if (jb + p < nb && dp[p] < minpiv) minpiv = dp[p];
+        }
+        // L entries in columns jb..jb+3 of a row from its S entries there
+        auto lrow = [&](const T (&r)[4], T (&l)[4]) {
+            l[0] = r[0] * i0;
+            l[1] = (r[1] - l[0] * l10) * i1;
+            l[2] = (r[2] - l[0] * l20 - l[1] * l21) * i2;
+            l[3] = (r[3] - l[0] * l30 - l[1] * l31 - l[2] * l32) * i3;
+        };
+        T lt[4];
+        lrow(st, lt);  // row t of L (entries right of the diagonal are not used)
+        if (u < 4 && t < nb && jb + u < nb)
+            s.A[(size_t)(k0 + t) * n + k0 + jb + u] = (t >= jb + u) ? pick4(lt, u) : (T)0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = u + 8 * q;
+            // rows jb..jb+3 of X = L^-1 in column c: block forward substitution
+            T x[4];
+            lrow(yc[q], x);
+            if (t >= jb && t < jb + 4 && c <= t && t < nb && c < nb)
+                s.W[(size_t)(k0 + t) * n + k0 + c] = pick4(x, t - jb);
+            if (t > jb + 3) {
+                if (c > jb + 3 && c <= t) {
+                    T lc[4];
+                    lrow(sc[q], lc);
+                    sv[q] -= lt[0] * lc[0] + lt[1] * lc[1] + lt[2] * lc[2] + lt[3] * lc[3];
+                }
+                if (c <= jb + 3) yv[q] -= lt[0] * x[0] + lt[1] * x[1] + lt[2] * x[2] + lt[3] * x[3];
+            }
+        }
+        // publish columns jn..jn+3 of S and rows jn..jn+3 of Y (the other buffer)
+        const int jn = jb + 4;
+        if (jn < kNB) {
+            const int u0 = jn & 7;
+            if (u >= u0 && u < u0 + 4) f.col[b ^ 1][t][u - u0] = pick4(sv, jn >> 3);
+            if (t >= jn && t < jn + 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) f.row[b ^ 1][u + 8 * q][t - jn] = yv[q];
+            }
         }
     }
-    if (bad) {
-        if (t == 0) s.flag[0] = SFFT_ERR_SINGULAR;
-        return;
-    }
-    if (t == 0 && (double)minpiv < s.stats[0]) s.stats[0] = (double)minpiv;
-    if (t < nb) {
+    // zeros above the diagonal of both blocks
 #pragma unroll
-        for (int c = 0; c < kNB; ++c)
-            if (c < nb) s.A[(size_t)(k0 + t) * n + k0 + c] = (c <= t) ? a[c] : (T)0;
+    for (int q = 0; q < 4; ++q) {
+        const int c = u + 8 * q;
+        if (c > t && t < nb && c < nb) {
+            s.A[(size_t)(k0 + t) * n + k0 + c] = (T)0;
+            s.W[(size_t)(k0 + t) * n + k0 + c] = (T)0;
+        }
     }
+    if (tid == 0) {
+        if (bad) s.flag[0] = SFFT_ERR_SINGULAR;
+        else if ((double)minpiv < s.stats[0]) s.stats[0] = (double)minpiv;
+    }
+    __syncthreads();
 }
 
-// Forward substitution L_kk y = b for one right-hand side held in registers
-// (L_kk in shared memory, lower triangular, padded rows).
-template <typename T>
-__device__ __forceinline__ void trsv_lower(T (&b)[kNB], const T (*L)[kNB + 1]) {
+// sum_{j < len} a[j] b[j] by one warp (lane = this thread's lane), with
+// eight independent loads of each operand in flight; the result is
+// reduced across the warp (every lane returns it).
+template <typename T, typename V>
+__device__ __forceinline__ T dot_warp(const T *a, const V *b, int lane, int len) {
+    T acc[8];
 #pragma unroll
-    for (int c = 0; c < kNB; ++c) {
-        T v = b[c];
+    for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+    int j = lane;
+    for (; j + 7 * 32 < len; j += 8 * 32) {
+        T av[8], bv[8];
 #pragma unroll
-        for (int p = 0; p < c; ++p) v -= L[c][p] * b[p];
-        b[c] = v / L[c][c];
+        for (int q = 0; q < 8; ++q) {
+            av[q] = a[j + 32 * q];
+            bv[q] = (T)b[j + 32 * q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += av[q] * bv[q];
     }
+    for (; j < len; j += 32) acc[0] += a[j] * (T)b[j];
+    T r = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
 }
 
-// Panel row i: L[i, k0:k0+kn] = solution of L_kk x = A[i, k0:k0+kn]^T
+// sum_{k0 <= k < k1} W[k][i] y[k] by one thread, eight rows in flight
 template <typename T>
-__device__ __noinline__ void panel_row(T *Ai, int kn, const T (*L)[kNB + 1]) {
-    T b[kNB];
+__device__ __forceinline__ T col_dot(const T *W, const T *y, int n, int i, int k0, int k1) {
+    T acc[8];
 #pragma unroll
-    for (int c = 0; c < kNB; ++c) b[c] = (c < kn) ? Ai[c] : (T)0;
-    trsv_lower(b, L);
+    for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+    int k = k0;
+    for (; k + 7 < k1; k += 8) {
+        T wv[8], yv[8];
 #pragma unroll
-    for (int c = 0; c < kNB; ++c)
-        if (c < kn) Ai[c] = b[c];
-}
-
-// Column c of W's block row k: W[k0:k0+kn, c] = L_kk^-1 W[k0:k0+kn, c] for
-// c < k0, or column c - k0 of L_kk^-1 for c >= k0.
-template <typename T>
-__device__ __noinline__ void wcol(T *W, int n, int k0, int kn, int c, const T (*L)[kNB + 1]) {
-    T b[kNB];
+        for (int q = 0; q < 8; ++q) {
+            wv[q] = W[(size_t)(k + q) * n + i];
+            yv[q] = y[k + q];
+        }
 #pragma unroll
-    for (int r = 0; r < kNB; ++r) {
-        T v;
-        if (c < k0) v = (r < kn) ? W[(size_t)(k0 + r) * n + c] : (T)0;
-        else v = (r == c - k0) ? (T)1 : (T)0;
-        b[r] = v;
+        for (int q = 0; q < 8; ++q) acc[q] += wv[q] * yv[q];
     }
-    trsv_lower(b, L);
-#pragma unroll
-    for (int r = 0; r < kNB; ++r)
-        if (r < kn) W[(size_t)(k0 + r) * n + c] = b[r];
+    for (; k < k1; ++k) acc[0] += W[(size_t)k * n + i] * y[k];
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // trailing-update tile tt -> (ti, tj), ti >= tj
@@ -197,107 +323,201 @@ __device__ __forceinline__ void lower_tile(int tt, int *ti, int *tj) {
     *tj = t;
 }
 
+// Phase P task `task` of one system at panel k0: a 64-row tile of the panel
+// L_ik = A_ik L_kk^-T (task < npt) or a 64-column tile of block row k of W,
+// W_k[:, 0:k0] = L_kk^-1 W_k[:, 0:k0].  L_kk^-1 is held in W_kk.  Each tile
+// reads its inputs into shared memory before it overwrites them.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1) k_solve_coop(SolveArgs<T> s) {
+__device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int kn, int base, int npt, int task) {
+    const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    const T *Linv = s.W + (size_t)k0 * n + k0;
+    T acc[4][4] = {};
+    if (task < npt) {
+        const int i0 = base + task * kTile, ni = min(kTile, n - i0);
+        // a(i, p) = A[i0 + i][k0 + p], b(p, c) = Linv[c][p]
+        tile_gemm(acc, sm, s.A + k0, n, i0, ni, Linv, n, 0, kn, true, 0, kn);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int i = tr * 4 + u, j = tc + 16 * v;
+                if (i < ni && j < kn) s.A[(size_t)(i0 + i) * n + k0 + j] = acc[u][v];
+            }
+    } else {
+        const int j0 = (task - npt) * kTile, nj = min(kTile, k0 - j0);
+        // a(r, p) = Linv[r][p], b(p, c) = W[k0 + p][j0 + c]
+        tile_gemm(acc, sm, s.W + k0, n, k0, kn, s.W + (size_t)k0 * n, n, j0, nj, false, 0, kn);
+        if (tr < kNB / 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = tr * 4 + u, c = tc + 16 * v;
+                    if (r < kn && c < nj) s.W[(size_t)(k0 + r) * n + j0 + c] = acc[u][v];
+                }
+        }
+    }
+}
+
+// Phase U task `task` of one system at panel k0: a 64x64 tile of the
+// trailing lower triangle, A_ij -= L_ik L_jk^T (task < ntiles; task 0 holds
+// the next diagonal block), or a 64x64 tile of the block rows of W below,
+// W_i[:, 0:k0+32] -= L_ik W_k.  The old values are loaded before the GEMM so
+// that the latencies overlap.
+template <typename T>
+__device__ void update_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int base, int ntiles, int ncw, int task) {
+    const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    T acc[4][4] = {};
+    T old[4][4];
+    if (task < ntiles) {
+        int ti, tj;
+        lower_tile(task, &ti, &tj);
+        const int i0 = base + ti * kTile, j0 = base + tj * kTile;
+        const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
+                old[u][v] = (i < n && j < n && j <= i) ? s.A[(size_t)i * n + j] : (T)0;
+            }
+        tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.A + k0, n, j0, nj, true, 0, kNB);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
+                if (i < n && j < n && j <= i) s.A[(size_t)i * n + j] = old[u][v] - acc[u][v];
+            }
+    } else {
+        const int q = task - ntiles, ti = q / ncw, tj = q % ncw;
+        const int i0 = base + ti * kTile, j0 = tj * kTile;
+        const int ni = min(kTile, n - i0), nj = min(kTile, k0 + kNB - j0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
+                old[u][v] = (i < n && j < k0 + kNB) ? s.W[(size_t)i * n + j] : (T)0;
+            }
+        // a(i, p) = L[i0 + i][k0 + p], b(p, j) = W[k0 + p][j0 + j]
+        tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.W + (size_t)k0 * n, n, j0, nj, false, 0, kNB);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
+                if (i < n && j < k0 + kNB) s.W[(size_t)i * n + j] = old[u][v] - acc[u][v];
+            }
+    }
+}
+
+// Up to kMaxBatch systems of the same size, solved together: every phase
+// spreads the tasks of all systems over the grid, and block b factors the
+// diagonal blocks of system b, so the serial chains of the systems run side
+// by side.
+template <typename T>
+struct BatchArgs {
+    int nsys;
+    SolveArgs<T> sys[kMaxBatch];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k_solve_coop(BatchArgs<T> ba) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ TileSmem<T> sm;
-    __shared__ T Ls[kNB][kNB + 1];
-    __shared__ double red[2][kThreads / 32];
+    __shared__ SolveSmem<T> sm;
+    __shared__ double sums[kMaxBatch][2];
     const int tid = threadIdx.x, bid = blockIdx.x, nbk = gridDim.x;
     const int gtid = bid * kThreads + tid, gthreads = nbk * kThreads;
-    const int n = s.n, nblk = s.nblk;
-    const int tr = tid / 16, tc = tid % 16;
     const int warp = tid >> 5, lane = tid & 31, nw = kThreads / 32;
+    const int nsys = ba.nsys;
+    const int n = ba.sys[0].n, nblk = ba.sys[0].nblk;  // the same for every system
 
-    // ---- Jacobi scaling, zero W and x --------------------------------------
-    for (int i = gtid; i < n; i += gthreads) {
-        const double d = s.M[(size_t)i * n + i];
-        if (!(d > 0.0)) s.flag[0] = SFFT_ERR_SINGULAR;
-        s.dsc[i] = (d > 0.0) ? 1.0 / sqrt(d) : 0.0;
-        s.x[i] = 0.0;
+    // ---- status reset; Jacobi scaling, zero W and x -------------------------
+    if (bid == 0 && tid < nsys) {
+        const SolveArgs<T> &s = ba.sys[tid];
+        s.flag[0] = s.flag[1] = s.flag[2] = s.flag[3] = 0;
+        s.stats[0] = 1e300;
+        s.stats[1] = s.stats[2] = s.stats[3] = 0.0;
     }
-    for (size_t e = gtid; e < (size_t)n * n; e += gthreads) s.W[e] = (T)0;
     grid.sync();
-    for (int i = bid; i < n; i += nbk) {
+    for (int b = 0; b < nsys; ++b) {
+        const SolveArgs<T> &s = ba.sys[b];
+        for (int i = gtid; i < n; i += gthreads) {
+            const double d = s.M[(size_t)i * n + i];
+            if (!(d > 0.0)) s.flag[0] = SFFT_ERR_SINGULAR;
+            s.dsc[i] = (d > 0.0) ? 1.0 / sqrt(d) : 0.0;
+            s.x[i] = 0.0;
+        }
+        for (size_t e = gtid; e < (size_t)n * n; e += gthreads) s.W[e] = (T)0;
+    }
+    grid.sync();
+    for (int row = bid; row < nsys * n; row += nbk) {
+        const int b = row / n, i = row - b * n;
+        const SolveArgs<T> &s = ba.sys[b];
         const double di = s.dsc[i];
         const double *Mi = s.M + (size_t)i * n;
         T *Ai = s.A + (size_t)i * n;
-        for (int j = tid; j < n; j += kThreads) Ai[j] = (T)(Mi[j] * di * s.dsc[j]);
+        // four independent loads in flight before the stores
+        for (int j0 = tid; j0 < n; j0 += 4 * kThreads) {
+            double m[4], d[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q * kThreads;
+                m[q] = j < n ? Mi[j] : 0.0;
+                d[q] = j < n ? s.dsc[j] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = j0 + q * kThreads;
+                if (j < n) Ai[j] = (T)(m[q] * di * d[q]);
+            }
+        }
     }
     grid.sync();
 
     // ---- Cholesky and W = L^-1 ----------------------------------------------
-    if (s.flag[0] == 0 && bid == 0 && warp == 0) factor_diag(s, 0);
+    // A system whose status turned negative (written before a barrier, so
+    // read alike by every block) is skipped from then on.
+    if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_inv(ba.sys[bid], sm.fac, 0);
     grid.sync();
     for (int kb = 0; kb < nblk; ++kb) {
-        if (s.flag[0] < 0) break;  // written before the last barrier: same value everywhere
         const int k0 = kb * kNB;
         const int kn = min(kNB, n - k0);
         const int base = k0 + kNB;  // first trailing row
         const int rows = n - base;  // may be <= 0 on the last block
-        // phase P: L_kk to shared memory; then, one thread per right-hand side,
-        // the panel rows L[i, k0:k0+32] = A[i, k0:k0+32] L_kk^-T (i >= k0+32)
-        // and the block row k of W: W_k[:, c] = L_kk^-1 W_k[:, c] for c < k0,
-        // W_kk = L_kk^-1 (identity right-hand sides)
         {
-            for (int e = tid; e < kNB * kNB; e += kThreads) {
-                const int i = e / kNB, c = e % kNB;
-                Ls[i][c] = (i < kn && c < kn) ? s.A[(size_t)(k0 + i) * n + k0 + c] : (i == c ? (T)1 : (T)0);
-            }
-            __syncthreads();
-            const int nrow = rows > 0 ? rows : 0;
-            const int ncol = k0 + kn;
-            for (int task = gtid; task < nrow + ncol; task += gthreads) {
-                if (task < nrow) panel_row(s.A + (size_t)(base + task) * n + k0, kn, Ls);
-                else wcol(s.W, n, k0, kn, task - nrow, Ls);
+            const int npt = rows > 0 ? (rows + kTile - 1) / kTile : 0;
+            const int nwt = (k0 + kTile - 1) / kTile;
+            const int per = npt + nwt;
+            for (int task = bid; task < nsys * per; task += nbk) {
+                const int b = task / per;
+                if (ba.sys[b].flag[0] < 0) continue;
+                panel_task(ba.sys[b], sm.tile, k0, kn, base, npt, task - b * per);
             }
         }
         grid.sync();
         if (rows <= 0) break;  // last block: nothing below (same in every block)
-        // phase U: the trailing lower triangle of A in 64x64 tiles, and the
-        // block rows of W below: W_i[:, 0:k0+32] -= L_ik W_k.  Block 0 takes
-        // tile 0 (it holds the next diagonal block) and factors that block at
-        // once; all other tasks go to the other blocks.
+        // Block b takes task 0 of system b (the tile holding its next diagonal
+        // block) and factors that block at once; the other blocks share the
+        // remaining tasks of all systems.
         {
             const int nt = (rows + kTile - 1) / kTile;
             const int ntiles = nt * (nt + 1) / 2;
             const int ncw = (k0 + kNB + kTile - 1) / kTile;
-            const int ntask = ntiles + nt * ncw;
-            const int first = (nbk == 1) ? 0 : (bid == 0 ? 0 : bid);
-            const int step = (nbk == 1) ? 1 : (bid == 0 ? ntask : nbk - 1);
-            for (int task = first; task < ntask; task += step) {
-                T acc[4][4] = {};
-                if (task < ntiles) {
-                    int ti, tj;
-                    lower_tile(task, &ti, &tj);
-                    const int i0 = base + ti * kTile, j0 = base + tj * kTile;
-                    const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
-                    tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.A + k0, n, j0, nj, true, 0, kNB);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                            if (i < n && j < n && j <= i) s.A[(size_t)i * n + j] -= acc[u][v];
-                        }
-                    if (task == 0) {
-                        __syncthreads();  // the tile's writes are visible to the block
-                        if (warp == 0) factor_diag(s, kb + 1);
-                        __syncthreads();
-                    }
-                } else {
-                    const int q = task - ntiles, ti = q / ncw, tj = q % ncw;
-                    const int i0 = base + ti * kTile, j0 = tj * kTile;
-                    const int ni = min(kTile, n - i0), nj = min(kTile, k0 + kNB - j0);
-                    // a(i, p) = L[i0 + i][k0 + p], b(p, j) = W[k0 + p][j0 + j]
-                    tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.W + (size_t)k0 * n, n, j0, nj, false, 0, kNB);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                            if (i < n && j < k0 + kNB) s.W[(size_t)i * n + j] -= acc[u][v];
-                        }
+            const int per = ntiles + nt * ncw - 1;  // tasks besides task 0
+            if (bid < nsys) {
+                const SolveArgs<T> &s = ba.sys[bid];
+                if (s.flag[0] == 0) {
+                    update_task(s, sm.tile, k0, base, ntiles, ncw, 0);
+                    __syncthreads();  // the tile's writes are visible to the block
+                    factor_inv(s, sm.fac, kb + 1);
+                }
+            } else {
+                for (int task = bid - nsys; task < nsys * per; task += nbk - nsys) {
+                    const int b = task / per;
+                    if (ba.sys[b].flag[0] < 0) continue;
+                    update_task(ba.sys[b], sm.tile, k0, base, ntiles, ncw, 1 + task - b * per);
                 }
             }
         }
@@ -305,63 +525,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_coop(SolveArgs<T> s) {
     }
 
     // ---- refinement ---------------------------------------------------------
-    for (int it = 0; it <= kMaxIters; ++it) {
-        if (s.flag[0] != 0) break;  // same value in every block
-        // r = rhs - M x (FP64); z = D r; per-block partial norms
-        double pr = 0.0, pb = 0.0;
-        for (int i = bid * nw + warp; i < n; i += nbk * nw) {
-            const double *Mi = s.M + (size_t)i * n;
-            double a = 0.0;
-            for (int j = lane; j < n; j += 32) a += Mi[j] * s.x[j];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    // done: bit b set once system b has converged, failed or run out of
+    // iterations; every block derives it from the same values.  The norms
+    // are sums over the rows in one fixed order (warp b of every block sums
+    // system b), so the decisions do not depend on the grid or the batch.
+    unsigned done = 0;
+    for (int b = 0; b < nsys; ++b)
+        if (ba.sys[b].flag[0] != 0) done |= 1u << b;
+    const unsigned all = (1u << nsys) - 1u;
+    if (warp < nsys) {
+        const SolveArgs<T> &s = ba.sys[warp];
+        const double bb = dot_warp<double>(s.rhs, s.rhs, lane, n);
+        if (lane == 0) sums[warp][1] = bb;
+    }
+    __syncthreads();
+    for (int it = 0; it <= kMaxIters && done != all; ++it) {
+        // r = rhs - M x (FP64); z = D r
+        for (int row = bid * nw + warp; row < nsys * n; row += nbk * nw) {
+            const int b = row / n, i = row - b * n;
+            if (done & (1u << b)) continue;
+            const SolveArgs<T> &s = ba.sys[b];
+            const double a = dot_warp<double>(s.M + (size_t)i * n, s.x, lane, n);
             const double ri = s.rhs[i] - a;
             if (lane == 0) {
                 s.r[i] = ri;
                 s.z[i] = (T)(s.dsc[i] * ri);
-                pr += ri * ri;
-                pb += s.rhs[i] * s.rhs[i];
             }
-        }
-        if (lane == 0) {
-            red[0][warp] = pr;
-            red[1][warp] = pb;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < nw; ++w) {
-                a += red[0][w];
-                b += red[1][w];
-            }
-            s.part[2 * bid] = a;
-            s.part[2 * bid + 1] = b;
         }
         grid.sync();
-        // every block sums the partials in the same order: the same decision everywhere
-        double rr = 0.0, bb = 0.0;
-        for (int k = 0; k < nbk; ++k) {
-            rr += s.part[2 * k];
-            bb += s.part[2 * k + 1];
+        if (warp < nsys && !(done & (1u << warp))) {
+            const SolveArgs<T> &s = ba.sys[warp];
+            const double rr = dot_warp<double>(s.r, s.r, lane, n);
+            if (lane == 0) sums[warp][0] = rr;
         }
-        const double rel = (bb > 0.0) ? sqrt(rr / bb) : sqrt(rr);
-        if (bid == 0 && tid == 0) {
-            s.stats[1] = bb;
-            s.stats[2] = rr;
+        __syncthreads();
+        for (int b = 0; b < nsys; ++b) {
+            if (done & (1u << b)) continue;
+            const SolveArgs<T> &s = ba.sys[b];
+            const double rr = sums[b][0], bb = sums[b][1];
+            const double rel = (bb > 0.0) ? sqrt(rr / bb) : sqrt(rr);
+            if (bid == 0 && tid == 0) {
+                s.stats[1] = bb;
+                s.stats[2] = rr;
+            }
+            if (rel <= kTol || rr == 0.0) {
+                if (bid == 0 && tid == 0) s.flag[0] = 1;
+                done |= 1u << b;
+            } else if (it == kMaxIters) {
+                if (bid == 0 && tid == 0) s.flag[0] = SFFT_ERR_NOT_CONVERGED;
+                done |= 1u << b;
+            }
         }
-        if (rel <= kTol || rr == 0.0) {
-            if (bid == 0 && tid == 0) s.flag[0] = 1;
-            break;
-        }
-        if (it == kMaxIters) {
-            if (bid == 0 && tid == 0) s.flag[0] = SFFT_ERR_NOT_CONVERGED;
-            break;
-        }
+        if (done == all) break;
         // y = W z  (W lower triangular)
-        for (int i = bid * nw + warp; i < n; i += nbk * nw) {
-            const T *Wi = s.W + (size_t)i * n;
-            T a = (T)0;
-            for (int j = lane; j <= i; j += 32) a += Wi[j] * s.z[j];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        for (int row = bid * nw + warp; row < nsys * n; row += nbk * nw) {
+            const int b = row / n, i = row - b * n;
+            if (done & (1u << b)) continue;
+            const SolveArgs<T> &s = ba.sys[b];
+            const T a = dot_warp<T>(s.W + (size_t)i * n, s.z, lane, i + 1);
             if (lane == 0) s.y[i] = a;
         }
         grid.sync();
@@ -369,78 +590,109 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_coop(SolveArgs<T> s) {
         {
             const int segrows = (n + kSeg - 1) / kSeg;
             const int nchunk = (n + 31) / 32;
-            for (int task = bid * nw + warp; task < nchunk * kSeg; task += nbk * nw) {
-                const int ch = task / kSeg, sg = task % kSeg;
+            const int per = nchunk * kSeg;
+            for (int task = bid * nw + warp; task < nsys * per; task += nbk * nw) {
+                const int b = task / per, q = task - b * per;
+                if (done & (1u << b)) continue;
+                const SolveArgs<T> &s = ba.sys[b];
+                const int ch = q / kSeg, sg = q % kSeg;
                 const int i = ch * 32 + lane;
                 const int k0 = max(ch * 32, sg * segrows), k1 = min(n, (sg + 1) * segrows);
-                T a = (T)0;
-                if (i < n)
-                    for (int k = k0; k < k1; ++k) a += s.W[(size_t)k * n + i] * s.y[k];
-                if (i < n) s.wseg[(size_t)sg * n + i] = a;
+                if (i < n) s.wseg[(size_t)sg * n + i] = col_dot<T>(s.W, s.y, n, i, k0, k1);
             }
         }
         grid.sync();
-        for (int i = gtid; i < n; i += gthreads) {
+        for (int e = gtid; e < nsys * n; e += gthreads) {
+            const int b = e / n, i = e - b * n;
+            if (done & (1u << b)) continue;
+            const SolveArgs<T> &s = ba.sys[b];
             T a = (T)0;
 #pragma unroll
             for (int sg = 0; sg < kSeg; ++sg) a += s.wseg[(size_t)sg * n + i];
             s.x[i] += s.dsc[i] * (double)a;
         }
-        if (bid == 0 && tid == 0) s.flag[1] += 1;
+        if (bid == 0 && tid < nsys && !(done & (1u << tid))) ba.sys[tid].flag[1] += 1;
         grid.sync();
     }
     // ---- results ------------------------------------------------------------
-    for (int i = gtid; i < n; i += gthreads) s.xout[i] = s.x[i];
-    if (s.info && bid == 0 && tid == 0) {
-        const int f = s.flag[0];
-        s.info->status = (f == 1) ? SFFT_OK : (f == 0 ? SFFT_ERR_NOT_CONVERGED : f);
-        s.info->iters = s.flag[1];
-        s.info->rel_residual = (s.stats[1] > 0.0) ? sqrt(s.stats[2] / s.stats[1]) : sqrt(s.stats[2]);
-        s.info->min_pivot = s.stats[0];
+    for (int e = gtid; e < nsys * n; e += gthreads) {
+        const int b = e / n, i = e - b * n;
+        ba.sys[b].xout[i] = ba.sys[b].x[i];
+    }
+    if (bid == 0 && tid < nsys) {
+        const SolveArgs<T> &s = ba.sys[tid];
+        if (s.info) {
+            const int f = s.flag[0];
+            s.info->status = (f == 1) ? SFFT_OK : (f == 0 ? SFFT_ERR_NOT_CONVERGED : f);
+            s.info->iters = s.flag[1];
+            s.info->rel_residual = (s.stats[1] > 0.0) ? sqrt(s.stats[2] / s.stats[1]) : sqrt(s.stats[2]);
+            s.info->min_pivot = s.stats[0];
+        }
     }
 }
 
-__global__ void k_solve_reset(int *flag, double *stats) {
-    flag[0] = flag[1] = flag[2] = flag[3] = 0;
-    stats[0] = 1e300;
-    stats[1] = stats[2] = stats[3] = 0.0;
-}
+static size_t solve_dyn_smem(bool) { return 0; }
 
-static size_t solve_dyn_smem(bool fp64);
-
+// Arguments of one system: the caller's M, rhs, x, info and the workspace.
 template <typename T>
-static cudaError_t solve_t(Plan *p, const double *M, const double *rhs, double *x, sfft_solve_info *info,
-                           cudaStream_t st) {
+static SolveArgs<T> system_args(int n, const double *M, const double *rhs, double *x, sfft_solve_info *info,
+                                double *dsc, double *xw, double *r, void *A, void *W, void *zv, int *flag) {
     SolveArgs<T> a;
-    a.n = p->n;
-    a.nblk = (p->n + kNB - 1) / kNB;
+    a.n = n;
+    a.nblk = (n + kNB - 1) / kNB;
     a.M = M;
     a.rhs = rhs;
-    a.dsc = p->dscale;
-    a.x = p->xw;
-    a.r = p->r;
-    a.stats = p->xw + p->n;
-    a.part = p->xw + p->n + 8;
-    a.A = (T *)p->A;
-    a.W = (T *)p->Wm;
-    a.z = (T *)p->zv;
-    a.y = (T *)p->zv + p->n;
-    a.wseg = (T *)p->zv + 2 * (size_t)p->n;
-    a.flag = p->flag;
+    a.dsc = dsc;
+    a.x = xw;
+    a.r = r;
+    a.stats = xw + n;
+    a.A = (T *)A;
+    a.W = (T *)W;
+    a.z = (T *)zv;
+    a.y = (T *)zv + n;
+    a.wseg = (T *)zv + 2 * (size_t)n;
+    a.flag = flag;
     a.xout = x;
     a.info = info;
-    k_solve_reset<<<1, 1, 0, st>>>(p->flag, a.stats);
-    cudaError_t err = cudaGetLastError();
-    if (err) return err;
-    void *args[] = {&a};
-    const size_t dsm = solve_dyn_smem(p->fp64);
-    err = cudaLaunchCooperativeKernel(p->fp64 ? (void *)k_solve_coop<double> : (void *)k_solve_coop<float>,
-                                      p->solve_grid, kThreads, args, dsm, st);
-    p->launches += 2;
+    return a;
+}
+
+template <typename T>
+static cudaError_t launch_batch(const BatchArgs<T> &ba, int grid, cudaStream_t st) {
+    if (grid <= ba.nsys) return cudaErrorInvalidConfiguration;  // blocks >= nsys take the shared tasks
+    void *args[] = {(void *)&ba};
+    return cudaLaunchCooperativeKernel((void *)k_solve_coop<T>, grid, kThreads, args, solve_dyn_smem(sizeof(T) == 8),
+                                       st);
+}
+
+template <typename T>
+static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *const *M, const double *const *rhs,
+                                 double *const *x, sfft_solve_info *const *info, cudaStream_t st) {
+    BatchArgs<T> ba;
+    ba.nsys = count;
+    for (int b = 0; b < count; ++b) {
+        Plan *p = plans[b];
+        ba.sys[b] = system_args<T>(p->n, M[b], rhs[b], x[b], info[b], p->dscale, p->xw, p->r, p->A, p->Wm, p->zv,
+                                   p->flag);
+    }
+    const cudaError_t err = launch_batch(ba, plans[0]->solve_grid, st);
+    plans[0]->launches += 1;
     return err;
 }
 
-static size_t solve_dyn_smem(bool) { return 0; }
+cudaError_t solve_batch(Plan *const *plans, int count, const double *const *M, const double *const *rhs,
+                        double *const *x, sfft_solve_info *const *info, cudaStream_t s) {
+    if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
+    for (int b = 1; b < count; ++b)
+        if (plans[b]->n != plans[0]->n || plans[b]->fp64 != plans[0]->fp64) return cudaErrorInvalidValue;
+    return plans[0]->fp64 ? solve_batch_t<double>(plans, count, M, rhs, x, info, s)
+                          : solve_batch_t<float>(plans, count, M, rhs, x, info, s);
+}
+
+cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x, sfft_solve_info *info,
+                         cudaStream_t s) {
+    return solve_batch(&p, 1, &M, &rhs, &x, &info, s);
+}
 
 int solve_grid_size(bool fp64) {
     int dev = 0, sms = 0, per = 0;
@@ -455,42 +707,19 @@ int solve_grid_size(bool fp64) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_coop<float>, kThreads, dsm);
     }
     if (per < 1 || sms < 1) return 0;
-    return sms;  // one block per SM; partial sums sized for at most 256 blocks
+    const int g = sms * (per < kBlocksPerSM ? per : kBlocksPerSM);
+    return g <= kMaxSolveGrid ? g : 0;
 }
 
 size_t solve_vec_elems(int n) { return (size_t)(2 + kSeg) * n; }
 
-cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x, sfft_solve_info *info,
-                         cudaStream_t s) {
-    return p->fp64 ? solve_t<double>(p, M, rhs, x, info, s) : solve_t<float>(p, M, rhs, x, info, s);
-}
-
 template <typename T>
 static cudaError_t solve_buf_t(const SolveBuffers &b, const double *M, const double *rhs, double *x,
                                sfft_solve_info *info, cudaStream_t st) {
-    SolveArgs<T> a;
-    a.n = b.n;
-    a.nblk = (b.n + kNB - 1) / kNB;
-    a.M = M;
-    a.rhs = rhs;
-    a.dsc = b.dsc;
-    a.x = b.xw;
-    a.r = b.r;
-    a.stats = b.xw + b.n;
-    a.part = b.xw + b.n + 8;
-    a.A = (T *)b.A;
-    a.W = (T *)b.W;
-    a.z = (T *)b.zv;
-    a.y = (T *)b.zv + b.n;
-    a.wseg = (T *)b.zv + 2 * (size_t)b.n;
-    a.flag = b.flag;
-    a.xout = x;
-    a.info = info;
-    k_solve_reset<<<1, 1, 0, st>>>(b.flag, a.stats);
-    cudaError_t err = cudaGetLastError();
-    if (err) return err;
-    void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((void *)k_solve_coop<T>, b.grid, kThreads, args, solve_dyn_smem(b.fp64), st);
+    BatchArgs<T> ba;
+    ba.nsys = 1;
+    ba.sys[0] = system_args<T>(b.n, M, rhs, x, info, b.dsc, b.xw, b.r, b.A, b.W, b.zv, b.flag);
+    return launch_batch(ba, b.grid, st);
 }
 
 cudaError_t solve_on_buffers(const SolveBuffers &b, const double *M, const double *rhs, double *x,

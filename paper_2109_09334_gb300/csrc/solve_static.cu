@@ -6,10 +6,9 @@
 // A and W = L^-1) plus 256 KiB for the vectors: 16.25 MiB per device, owned
 // by this translation unit's module and placed by the CUDA driver when the
 // module is loaded.  Each call lays the workspace for its own n out from the
-// start of the array.  Nothing in it has to start at zero: every call first
-// resets the status flags and statistics with a one-thread kernel, and the
-// solve kernel writes every element of A, W and the vectors before it reads
-// them.  Two calls whose executions overlap on one device (different
+// start of the array.  Nothing in it has to start at zero: the solve kernel
+// first resets the status flags and statistics, and it writes every element
+// of A, W and the vectors before it reads them.  Two calls whose executions overlap on one device (different
 // streams, or host threads without ordering) share the array and race.
 #include <cuda_runtime.h>
 
@@ -21,7 +20,7 @@
 namespace {
 
 constexpr size_t kMaxN = SFFT_SOLVE_STATIC_MAX_N;
-constexpr int kMaxGrid = 256;    // per-block partial sums: 2 doubles per block
+constexpr int kMaxGrid = sfft::kMaxSolveGrid;  // per-block partial sums: 2 doubles per block
 constexpr int kMaxDevices = 64;  // devices with their own setup record
 constexpr size_t kAlign = 256;
 constexpr size_t kScratchBytes = 2 * kMaxN * kMaxN * sizeof(double) + 256 * 1024;

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0
 template <typename T>
 static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
     cudaError_t err;
-    double *ksum = p->xw + p->n + 700;  // after the solve's statistics and partial sums
+    double *ksum = p->xw + p->n + kSolveTail;  // after the solve's statistics and partial sums
     p->launches += 4;
     k_kernel_sums<<<p->nk, 256, 0, s>>>(p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x, ksum);
     const size_t tot = (size_t)p->nk * p->L0 * p->h1c;
