@@ -7,6 +7,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "fft16.cuh"
 #include "internal.h"
 
 namespace sfft {
@@ -17,6 +18,31 @@ __global__ void k_twiddle64(int n, cpx<double> *tw) {
         double s, c;
         sincospi(-2.0 * (double)q / (double)n, &s, &c);
         tw[q] = mk(c, s);
+    }
+}
+
+// Pass-ordered twiddles of a length-n transform (fft16.cuh): for the
+// radix-16 pass of stride ns, entry (r - 1) * ns + k holds
+// exp(-2 pi i r k / (16 ns)) = tw64[r k n / (16 ns)] rounded to T.
+template <typename T>
+__global__ void k_pass_table(int n, int ns, const cpx<double> *tw64, cpx<T> *out) {
+    const int cnt = 15 * ns;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+        const int r = 1 + e / ns, k = e % ns;
+        const cpx<double> w = tw64[r * k * (n / (16 * ns))];  // r k < 16 ns, so the index is below n
+        out[e] = mk((T)w.re, (T)w.im);
+    }
+}
+
+template <typename T>
+static void pass_tables(int n, const cpx<double> *tw64, cpx<T> *out, cudaStream_t s) {
+    int e = 0;
+    while ((1 << e) < n) ++e;
+    int off = 0;
+    for (int ns = 1 << (e & 3); ns < n; ns *= 16) {
+        if (ns == 1) continue;
+        k_pass_table<T><<<(15 * ns + 255) / 256, 256, 0, s>>>(n, ns, tw64, out + off);
+        off += 15 * ns;
     }
 }
 
@@ -69,7 +95,7 @@ static int unknowns(const sfft_config *c) {
 }
 
 void plan_free(Plan *p) {
-    void *bufs[] = {p->tw0, p->tw1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
+    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
                     p->lag, p->A, p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own,
                     p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
     for (void *b : bufs)
@@ -143,6 +169,8 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
 
     SFFT_ALLOC(p->tw0, p->n0 * csz);
     SFFT_ALLOC(p->tw1, p->n1 * csz);
+    SFFT_ALLOC(p->twp0, p->n0 * csz);
+    SFFT_ALLOC(p->twp1, p->n1 * csz);
     SFFT_ALLOC(p->xhat, (size_t)(cfg->db + 1) * p->n0 * csz);
     SFFT_ALLOC(p->yhat, (size_t)(cfg->db + 1) * p->h1c * csz);
     SFFT_ALLOC(p->F, (size_t)(cfg->dk + 2) * half * csz);
@@ -203,11 +231,15 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     if (p->fp64) {
         k_round<double><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<double> *)p->tw0);
         k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<double> *)p->tw1);
+        pass_tables<double>(p->n0, t64a, (cpx<double> *)p->twp0, s);
+        pass_tables<double>(p->n1, t64b, (cpx<double> *)p->twp1, s);
         k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<double> *)p->xhat);
         k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<double> *)p->yhat);
     } else {
         k_round<float><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<float> *)p->tw0);
         k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<float> *)p->tw1);
+        pass_tables<float>(p->n0, t64a, (cpx<float> *)p->twp0, s);
+        pass_tables<float>(p->n1, t64b, (cpx<float> *)p->twp1, s);
         k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<float> *)p->xhat);
         k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<float> *)p->yhat);
     }

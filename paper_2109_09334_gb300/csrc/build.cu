@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     const int x0b = (blockIdx.x / nfft) * TR;
     const int sa = 2 * f, sb = 2 * f + 1;
     cpx<T> *zr = Z + (size_t)grp * np;
-    for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
+    const int ntw = pass_table_len(n1);
+    for (int q = tid; q < ntw; q += nthr) tw[q] = tw1g[q];
     {
         // thread gt loads pixels [16 gt, 16 gt + 16) of its row (all loads in flight)
         const size_t rowoff = (size_t)(x0b + grp) * n1;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
         }
     }
     __syncthreads();
-    group_fft(zr, n1, -1, tw, n1, gt, G);
+    group_fft(zr, n1, -1, tw, gt, G);
     // separate the two real transforms and write them transposed
     const int h1c = n1 / 2 + 1;
     const int total = h1c * TR;
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, in
     const int nk = n_terms(dk);
     const int t = blockIdx.y * GI + grp;
     const bool act = t <= nk;
-    for (int q = tid; q < n0; q += nthr) tw[q] = tw0g[q];
+    const int ntw = pass_table_len(n0);
+    for (int q = tid; q < ntw; q += nthr) tw[q] = tw0g[q];
     cpx<T> *zr = Z + (size_t)grp * np;
     if (act) {
         // thread gt loads elements [16 gt, 16 gt + 16) of the column (all in flight)
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, in
     }
     __syncthreads();
     // the last pass stores bin l = lb + NB*r at lb*(NA+1) + r
-    group_fft(zr, n0, -1, tw, n0, gt, G, nbk, na);
+    group_fft(zr, n0, -1, tw, gt, G, nbk, na);
     if (act) {
         cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
         for (int o = gt; o < n0; o += G) {
@@ -617,7 +619,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int nfft = (p->cfg.dk + 3) / 2;
     kern<<<(p->n0 / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, TR, (const I *)ref, (const I *)sci,
-                                                   mask, (cpx<T> *)p->F, (const cpx<T> *)p->tw1);
+                                                   mask, (cpx<T> *)p->F, (const cpx<T> *)p->twp1);
     p->launches++;
     if (moments) {
         k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
@@ -646,7 +648,7 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(p->h1c, (nimg + GI - 1) / GI);
     kern<<<grid, GI * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, GI, (const cpx<T> *)p->F,
-                                    (cpx<T> *)p->U, (const cpx<T> *)p->tw0);
+                                    (cpx<T> *)p->U, (const cpx<T> *)p->twp0);
     p->launches++;
     return cudaGetLastError();
 }

@@ -7,8 +7,10 @@
 // rest is a whole number of radix-16 passes), then radix-16 passes, each
 // thread holding one butterfly's 16 values in registers.  Passes are in
 // place: all loads of a pass complete (block barrier) before its stores.
-// Twiddles exp(sgn 2 pi i q / n_tab) come from a shared table of n_tab
-// entries (tw[q] = exp(-2 pi i q / n_tab); the inverse uses conjugates).
+// Twiddles come from a pass-ordered table (pass_table_*): the radix-16 pass
+// of stride ns > 1 reads exp(-2 pi i r k / (16 ns)) at (r - 1) * ns + k, so
+// the lanes of a warp (consecutive k) read consecutive words; the inverse
+// uses conjugates.
 #pragma once
 
 #include "common.cuh"
@@ -69,10 +71,9 @@ __device__ __forceinline__ int out_pos(int l, int perm_nb, int perm_na) {
 // One Stockham pass of radix R on the padded buffer.  All threads of the
 // block call it (block barriers inside); gtid/gsize index the group.
 template <typename T, int R>
-__device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, const cpx<T> *tw, int tw_n, int gtid,
+__device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, const cpx<T> *twp, int gtid,
                                          int gsize, int perm_nb = 0, int perm_na = 0) {
     const int nb = n / R;  // butterflies
-    const int stride = (tw_n / n) * (n / (R * ns));
     constexpr int kMaxPer = 16 / R;  // butterflies per thread (gsize = n / 16)
     cpx<T> v[kMaxPer][R];
 #pragma unroll
@@ -82,9 +83,9 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
             const int k = j & (ns - 1);
 #pragma unroll
             for (int r = 0; r < R; ++r) v[u][r] = buf[pad16(j + r * nb)];
-            if (ns > 1) {
+            if (ns > 1) {  // only radix-16 passes have ns > 1
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], tw_get(tw, r * k * stride, sgn));
+                for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], tw_get(twp, (r - 1) * ns + k, sgn));
             }
             if constexpr (R == 16) dft16(v[u], sgn);
             else if constexpr (R == 8) dft8(v[u], sgn);
@@ -110,30 +111,44 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
 // buffer; the block must call it with the same n in every group.  With
 // perm_nb > 0 the last pass stores in the residue-class layout (out_pos).
 template <typename T>
-__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *tw, int tw_n, int gtid, int gsize,
-                          int perm_nb = 0, int perm_na = 0) {
+__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize, int perm_nb = 0,
+                          int perm_na = 0) {
     const int e = 31 - __clz(n);
     int ns = 1;
     const bool only_first = (e >> 2) == 0;  // no radix-16 pass follows
     switch (e & 3) {
         case 1:
-            fft_pass<T, 2>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 2>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
             ns = 2;
             break;
         case 2:
-            fft_pass<T, 4>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 4>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
             ns = 4;
             break;
         case 3:
-            fft_pass<T, 8>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 8>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
             ns = 8;
             break;
         default: break;
     }
+    int off = 0;  // this pass's entries in the pass-ordered table
     for (; ns < n; ns *= 16) {
         const bool last = ns * 16 >= n;
-        fft_pass<T, 16>(buf, n, ns, sgn, tw, tw_n, gtid, gsize, last ? perm_nb : 0, perm_na);
+        fft_pass<T, 16>(buf, n, ns, sgn, twp + off, gtid, gsize, last ? perm_nb : 0, perm_na);
+        if (ns > 1) off += 15 * ns;
     }
+}
+
+// Strides ns of the radix-16 passes with twiddles, in execution order, for a
+// transform of length n (power of two): ns = 2^(e mod 4) * 16^m, ns > 1.
+// The pass-ordered table holds 15 ns entries per pass, fewer than n in all.
+__host__ __device__ inline int pass_table_len(int n) {
+    int e = 0;
+    while ((1 << e) < n) ++e;
+    int len = 0;
+    for (int ns = 1 << (e & 3); ns < n; ns *= 16)
+        if (ns > 1) len += 15 * ns;
+    return len;
 }
 
 // 16 consecutive values of type I from global memory into registers as T,

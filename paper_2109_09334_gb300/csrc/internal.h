@@ -42,6 +42,7 @@ struct Plan {
 
     // device workspace
     void *tw0, *tw1;       // twiddle tables exp(-2 pi i q / n), length n0 and n1 (compute type)
+    void *twp0, *twp1;     // the same twiddles in pass order for the FFTs (fft16.cuh)
     void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
     void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
     void *F;               // [(dk+2)][m][x] row transforms (compute type)

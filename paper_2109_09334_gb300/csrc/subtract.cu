@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0
     const int half = n1 / 2;
     const T inv = (T)1 / (T)n1;
     const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
-    for (int q = tid; q < n1; q += nthr) tw[q] = tw1g[q];
+    const int ntw = pass_table_len(n1);
+    for (int q = tid; q < ntw; q += nthr) tw[q] = tw1g[q];
     cpx<T> *zr = Z + (size_t)grp * np;
     {
         // 16 frequencies per thread, all loads in flight
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0
         }
     }
     __syncthreads();
-    group_fft(zr, n1, 1, tw, n1, gt, G);
+    group_fft(zr, n1, 1, tw, gt, G);
     for (int y = gt; y < n1; y += G) {
         const cpx<T> z = zr[pad16(y)];
         D[(size_t)xa * n1 + y] = (I)(z.re * inv);
@@ -236,11 +237,11 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
         if (p->cfg.dtype == SFFT_F64) {
             cudaFuncSetAttribute(k_rows_inv<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_rows_inv<T, double><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, NG, (const cpx<T> *)p->U,
-                                                                (const cpx<T> *)p->tw1, (double *)diff);
+                                                                (const cpx<T> *)p->twp1, (double *)diff);
         } else {
             cudaFuncSetAttribute(k_rows_inv<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_rows_inv<T, float><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, NG, (const cpx<T> *)p->U,
-                                                               (const cpx<T> *)p->tw1, (float *)diff);
+                                                               (const cpx<T> *)p->twp1, (float *)diff);
         }
     }
     return cudaGetLastError();
