@@ -194,12 +194,13 @@ __global__ void k_moments(int n0, int nmom, const double *__restrict__ rowmom, d
 }
 
 // ---------------------------------------------------------------------------
-// Column pass.  Block (m, chunk): GI output images in parallel, one group of
-// G = n0/16 threads each.  Image t < nk is the term (i, j): the row transform
-// of yt^j * Rm weighted by xt^i; t = nk is Sm.  Output layout
-// U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
+// Column pass.  Block (chunk, m): GI output images in parallel, one group of
+// G = n0/16 threads each; the chunks of one column are neighbours in launch
+// order, so the row transforms they share are read from L2.  Image t < nk is
+// the term (i, j): the row transform of yt^j * Rm weighted by xt^i; t = nk
+// is Sm.  Output layout U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
 template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, int n1, int dk, int na, int nbk, int GI,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int n1, int dk, int na, int nbk, int GI,
                                                const cpx<T> *__restrict__ F, cpx<T> *__restrict__ U,
                                                const cpx<T> *__restrict__ tw0g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -209,25 +210,25 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(int n0, in
     cpx<T> *Z = tw + n0;                                 // GI * np
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int grp = tid / G, gt = tid - grp * G;
-    const int m = blockIdx.x;
+    const int m = blockIdx.y;
     const int h1c = n1 / 2 + 1;
     const int nk = n_terms(dk);
-    const int t = blockIdx.y * GI + grp;
+    const int t = blockIdx.x * GI + grp;
     const bool act = t <= nk;
     const int ntw = pass_table_len(n0);
     for (int q = tid; q < ntw; q += nthr) tw[q] = tw0g[q];
     cpx<T> *zr = Z + (size_t)grp * np;
     if (act) {
-        // thread gt loads elements [16 gt, 16 gt + 16) of the column (all in flight)
+        // thread gt loads elements gt + G c, c < 16: coalesced, all in flight
         int i = 0, j = dk + 1;
         if (t < nk) term_ij(t, &i, &j);
-        const cpx<T> *col = F + ((size_t)j * h1c + m) * n0 + 16 * gt;
+        const cpx<T> *col = F + ((size_t)j * h1c + m) * n0 + gt;
         cpx<T> v[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = col[c];
+        for (int c = 0; c < 16; ++c) v[c] = col[G * c];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const int x = 16 * gt + c;
+            const int x = gt + G * c;
             zr[pad16(x)] = scale(v[c], ipow(coord<T>(x, n0), i));
         }
     }
@@ -635,18 +636,20 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
     p->launches++;
     const int G = p->n0 / 16;
-    int GI = (sizeof(T) == 4 ? 1024 : 512) / G;
+    // at most 512 (FP32) / 256 (FP64) threads and about 100 KB of shared
+    // memory per block, so that two blocks share an SM
+    int GI = (sizeof(T) == 4 ? 512 : 256) / G;
     if (GI > 4) GI = 4;
     const int nimg = p->nk + 1;
     if (GI > nimg) GI = nimg;
     size_t smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
-    while (GI > 1 && smem > 200 * 1024) {
+    while (GI > 1 && smem > 110 * 1024) {
         --GI;
         smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
     }
     auto kern = k_cols<T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(p->h1c, (nimg + GI - 1) / GI);
+    dim3 grid((nimg + GI - 1) / GI, p->h1c);
     kern<<<grid, GI * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, GI, (const cpx<T> *)p->F,
                                     (cpx<T> *)p->U, (const cpx<T> *)p->twp0);
     p->launches++;
