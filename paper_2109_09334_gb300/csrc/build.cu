@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     const int total = h1c * TR;
     cpx<T> *Fa = F + (size_t)sa * h1c * n0 + x0b;
     cpx<T> *Fb = F + (size_t)sb * h1c * n0 + x0b;
+    const int ltr = __ffs(TR) - 1;  // TR is a power of two
     for (int idx = tid; idx < total; idx += nthr) {
-        const int m = idx / TR, r = idx - m * TR;
+        const int m = idx >> ltr, r = idx & (TR - 1);
         const cpx<T> *zz = Z + (size_t)r * np;
         const cpx<T> z = zz[pad16(m)];
         const cpx<T> zc = conj(zz[pad16((n1 - m) & (n1 - 1))]);
@@ -233,12 +234,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
         }
     }
     __syncthreads();
-    // the last pass stores bin l = lb + NB*r at lb*(NA+1) + r
-    group_fft(zr, n0, -1, tw, gt, G, nbk, na);
+    // the last pass stores bin l = lb + NB*r at lb*(NA+1) + r (NA, NB powers of two)
+    const int lna = __ffs(na) - 1, lnb = __ffs(nbk) - 1;
+    group_fft(zr, n0, -1, tw, gt, G, lnb, na);
     if (act) {
         cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
         for (int o = gt; o < n0; o += G) {
-            const int lb = o / na, r = o - lb * na;
+            const int lb = o >> lna, r = o & (na - 1);
             out[o] = zr[lb * (na + 1) + r];
         }
     }

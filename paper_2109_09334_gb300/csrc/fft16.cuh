@@ -61,18 +61,18 @@ __device__ __forceinline__ void dft16(cpx<T> (&v)[16], int sgn) {
 // register slot of output X[r] after dft16
 __device__ __forceinline__ constexpr int slot16(int r) { return (r & 3) * 4 + (r >> 2); }
 
-// Store position of output l: the padded natural layout, or (perm_nb > 0)
-// the residue-class layout [l mod perm_nb][l / perm_nb] with rows of
+// Store position of output l: the padded natural layout, or (perm_lnb >= 0)
+// the residue-class layout [l mod nb][l / nb], nb = 2^perm_lnb, with rows of
 // perm_na + 1 elements.
-__device__ __forceinline__ int out_pos(int l, int perm_nb, int perm_na) {
-    return perm_nb > 0 ? (l % perm_nb) * (perm_na + 1) + l / perm_nb : pad16(l);
+__device__ __forceinline__ int out_pos(int l, int perm_lnb, int perm_na) {
+    return perm_lnb >= 0 ? (l & ((1 << perm_lnb) - 1)) * (perm_na + 1) + (l >> perm_lnb) : pad16(l);
 }
 
 // One Stockham pass of radix R on the padded buffer.  All threads of the
 // block call it (block barriers inside); gtid/gsize index the group.
 template <typename T, int R>
 __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, const cpx<T> *twp, int gtid,
-                                         int gsize, int perm_nb = 0, int perm_na = 0) {
+                                         int gsize, int perm_lnb = -1, int perm_na = 0) {
     const int nb = n / R;  // butterflies
     constexpr int kMaxPer = 16 / R;  // butterflies per thread (gsize = n / 16)
     cpx<T> v[kMaxPer][R];
@@ -101,7 +101,7 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
             const int k = j & (ns - 1);
             const int o = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[out_pos(o + r * ns, perm_nb, perm_na)] = v[u][(R == 16) ? slot16(r) : r];
+            for (int r = 0; r < R; ++r) buf[out_pos(o + r * ns, perm_lnb, perm_na)] = v[u][(R == 16) ? slot16(r) : r];
         }
     }
     __syncthreads();
@@ -109,24 +109,24 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
 
 // Whole transform of length n (power of two, 16 <= n <= 4096) on the padded
 // buffer; the block must call it with the same n in every group.  With
-// perm_nb > 0 the last pass stores in the residue-class layout (out_pos).
+// perm_lnb >= 0 the last pass stores in the residue-class layout (out_pos).
 template <typename T>
-__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize, int perm_nb = 0,
+__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize, int perm_lnb = -1,
                           int perm_na = 0) {
     const int e = 31 - __clz(n);
     int ns = 1;
     const bool only_first = (e >> 2) == 0;  // no radix-16 pass follows
     switch (e & 3) {
         case 1:
-            fft_pass<T, 2>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 2>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_lnb : -1, perm_na);
             ns = 2;
             break;
         case 2:
-            fft_pass<T, 4>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 4>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_lnb : -1, perm_na);
             ns = 4;
             break;
         case 3:
-            fft_pass<T, 8>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_nb : 0, perm_na);
+            fft_pass<T, 8>(buf, n, ns, sgn, twp, gtid, gsize, only_first ? perm_lnb : -1, perm_na);
             ns = 8;
             break;
         default: break;
@@ -134,7 +134,7 @@ __device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gt
     int off = 0;  // this pass's entries in the pass-ordered table
     for (; ns < n; ns *= 16) {
         const bool last = ns * 16 >= n;
-        fft_pass<T, 16>(buf, n, ns, sgn, twp + off, gtid, gsize, last ? perm_nb : 0, perm_na);
+        fft_pass<T, 16>(buf, n, ns, sgn, twp + off, gtid, gsize, last ? perm_lnb : -1, perm_na);
         if (ns > 1) off += 15 * ns;
     }
 }

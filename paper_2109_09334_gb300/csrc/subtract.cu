@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
 // group transforms two rows at once (real and imaginary part of one complex
 // FFT of the Hermitian-extended row spectra).
 template <typename T, typename I>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv(int n0, int n1, int NG, const cpx<T> *__restrict__ Dt,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_rows_inv(int n0, int n1, int NG, const cpx<T> *__restrict__ Dt,
                                                    const cpx<T> *__restrict__ tw1g, I *__restrict__ D) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
@@ -225,11 +225,14 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
     }
     {
         const int G = p->n1 / 16;
-        int NG = (sizeof(T) == 4 ? 1024 : 512) / G;
+        // at most 512 (FP32) / 256 (FP64) threads and about 100 KB of shared
+        // memory per block, so that two blocks share an SM
+        int NG = (sizeof(T) == 4 ? 512 : 256) / G;
+        if (NG < 1) NG = 1;
         if (NG > 4) NG = 4;
         if (NG > p->n0 / 2) NG = p->n0 / 2;
         size_t smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
-        while (NG > 1 && smem > 200 * 1024) {
+        while (NG > 1 && smem > 110 * 1024) {
             NG /= 2;
             smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
         }
