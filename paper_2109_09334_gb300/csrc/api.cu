@@ -46,6 +46,35 @@ static void pass_tables(int n, const cpx<double> *tw64, cpx<T> *out, cudaStream_
     }
 }
 
+// Bluestein chirp c_t = exp(-i pi t^2 / n), t < n, in FP64; t^2 is reduced
+// mod 2n exactly in integers first.
+__global__ void k_chirp64(int n, cpx<double> *c) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const long long q = ((long long)t * t) % (2LL * n);
+        double sn, cs;
+        sincospi(-(double)q / (double)n, &sn, &cs);
+        c[t] = mk(cs, sn);
+    }
+}
+
+// Bluestein filter: the length-m FFT of b_t = conj(c_|t|), |t| < n, placed at
+// t mod m, by direct FP64 summation with the FP64 twiddles of length m.
+template <typename T>
+__global__ void k_bfilt(int n, int m, const cpx<double> *twm, const cpx<double> *c, cpx<T> *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int t = -(n - 1); t < n; ++t) {
+            const cpx<double> ct = c[t < 0 ? -t : t];
+            const int tm = t < 0 ? t + m : t;
+            const cpx<double> w = twm[(int)(((long long)tm * k) & (m - 1))];
+            // conj(ct) * w
+            re += ct.re * w.re + ct.im * w.im;
+            im += ct.re * w.im - ct.im * w.re;
+        }
+        out[k] = mk((T)re, (T)im);
+    }
+}
+
 template <typename T>
 __global__ void k_round(int n, const cpx<double> *src, cpx<T> *dst) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
@@ -77,11 +106,12 @@ static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int plan_validate(const sfft_config *c) {
     if (!c) return SFFT_ERR_INVALID;
-    if (!is_pow2(c->n0) || !is_pow2(c->n1)) return SFFT_ERR_UNSUPPORTED;
     if (c->n0 < 16 || c->n1 < 16 || c->n0 > 4096 || c->n1 > 4096) return SFFT_ERR_UNSUPPORTED;
     if (c->w0 < 0 || c->w1 < 0 || c->dk < 0 || c->db < 0) return SFFT_ERR_INVALID;
     if (c->dk > 3 || c->db > 3) return SFFT_ERR_UNSUPPORTED;
-    const int na = c->n0 < kMaxNA ? c->n0 : kMaxNA;
+    // lag ranges: |rho| <= 2w must stay inside one period; along x the split
+    // pruned transform of power-of-two n0 further needs 4 w0 + 1 <= NA
+    const int na = !is_pow2(c->n0) ? c->n0 : (c->n0 < kMaxNA ? c->n0 : kMaxNA);
     if (4 * c->w0 + 1 > na || 4 * c->w1 + 1 > c->n1) return SFFT_ERR_UNSUPPORTED;
     if (c->dtype != SFFT_F32 && c->dtype != SFFT_F64) return SFFT_ERR_INVALID;
     if (c->precision != SFFT_PREC_FP64 && c->precision != SFFT_PREC_MIXED) return SFFT_ERR_INVALID;
@@ -95,7 +125,7 @@ static int unknowns(const sfft_config *c) {
 }
 
 void plan_free(Plan *p) {
-    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
+    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->chirp1, p->bfilt1, p->twpm1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
                     p->lag, p->A, p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own,
                     p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
     for (void *b : bufs)
@@ -126,7 +156,10 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     p->n = unknowns(cfg);
     p->L0 = 2 * cfg->w0 + 1;
     p->L1 = 2 * cfg->w1 + 1;
-    p->na = cfg->n0 < kMaxNA ? cfg->n0 : kMaxNA;
+    p->gen0 = !is_pow2(cfg->n0);
+    p->gen1 = !is_pow2(cfg->n1);
+    p->m1 = p->gen1 ? bluestein_len(cfg->n1) : cfg->n1;
+    p->na = p->gen0 ? cfg->n0 : (cfg->n0 < kMaxNA ? cfg->n0 : kMaxNA);
     p->nbk = cfg->n0 / p->na;
     p->nimg = p->nk + 1;
     p->fp64 = cfg->precision == SFFT_PREC_FP64;
@@ -174,7 +207,13 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->xhat, (size_t)(cfg->db + 1) * p->n0 * csz);
     SFFT_ALLOC(p->yhat, (size_t)(cfg->db + 1) * p->h1c * csz);
     SFFT_ALLOC(p->F, (size_t)(cfg->dk + 2) * half * csz);
-    SFFT_ALLOC(p->U, (size_t)p->nimg * half * csz);
+    // the column spectra (power-of-two n0); the subtraction reuses U for D~
+    SFFT_ALLOC(p->U, (size_t)(p->gen0 ? 1 : p->nimg) * half * csz);
+    if (p->gen1) {
+        SFFT_ALLOC(p->chirp1, (size_t)p->n1 * csz);
+        SFFT_ALLOC(p->bfilt1, (size_t)p->m1 * csz);
+        SFFT_ALLOC(p->twpm1, (size_t)p->m1 * csz);
+    }
     SFFT_ALLOC(p->Q, (size_t)p->nrows * p->h1c * csz);
     SFFT_ALLOC(p->pairs, (size_t)np * sizeof(PairDesc));
     SFFT_ALLOC(p->rowmom, (size_t)p->n0 * p->nmom * sizeof(double));
@@ -231,17 +270,43 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     if (p->fp64) {
         k_round<double><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<double> *)p->tw0);
         k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<double> *)p->tw1);
-        pass_tables<double>(p->n0, t64a, (cpx<double> *)p->twp0, s);
-        pass_tables<double>(p->n1, t64b, (cpx<double> *)p->twp1, s);
+        if (!p->gen0) pass_tables<double>(p->n0, t64a, (cpx<double> *)p->twp0, s);
+        if (!p->gen1) pass_tables<double>(p->n1, t64b, (cpx<double> *)p->twp1, s);
         k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<double> *)p->xhat);
         k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<double> *)p->yhat);
     } else {
         k_round<float><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<float> *)p->tw0);
         k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<float> *)p->tw1);
-        pass_tables<float>(p->n0, t64a, (cpx<float> *)p->twp0, s);
-        pass_tables<float>(p->n1, t64b, (cpx<float> *)p->twp1, s);
+        if (!p->gen0) pass_tables<float>(p->n0, t64a, (cpx<float> *)p->twp0, s);
+        if (!p->gen1) pass_tables<float>(p->n1, t64b, (cpx<float> *)p->twp1, s);
         k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<float> *)p->xhat);
         k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<float> *)p->yhat);
+    }
+    if (p->gen1) {
+        cpx<double> *tm64 = nullptr, *c64 = nullptr;
+        if (cudaMalloc((void **)&tm64, p->m1 * sizeof(cpx<double>)) != cudaSuccess ||
+            cudaMalloc((void **)&c64, p->n1 * sizeof(cpx<double>)) != cudaSuccess) {
+            cudaGetLastError();
+            if (tm64) cudaFree(tm64);
+            cudaFree(t64a);
+            cudaFree(t64b);
+            plan_free(p);
+            return SFFT_ERR_OOM;
+        }
+        k_twiddle64<<<(p->m1 + 255) / 256, 256, 0, s>>>(p->m1, tm64);
+        k_chirp64<<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64);
+        if (p->fp64) {
+            k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64, (cpx<double> *)p->chirp1);
+            k_bfilt<double><<<(p->m1 + 127) / 128, 128, 0, s>>>(p->n1, p->m1, tm64, c64, (cpx<double> *)p->bfilt1);
+            pass_tables<double>(p->m1, tm64, (cpx<double> *)p->twpm1, s);
+        } else {
+            k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64, (cpx<float> *)p->chirp1);
+            k_bfilt<float><<<(p->m1 + 127) / 128, 128, 0, s>>>(p->n1, p->m1, tm64, c64, (cpx<float> *)p->bfilt1);
+            pass_tables<float>(p->m1, tm64, (cpx<float> *)p->twpm1, s);
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(tm64);
+        cudaFree(c64);
     }
     err = cudaGetLastError();
     cudaStreamSynchronize(s);

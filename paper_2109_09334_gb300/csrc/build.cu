@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     cpx<T> *zr = Z + (size_t)grp * np;
     const int ntw = pass_table_len(n1);
     for (int q = tid; q < ntw; q += nthr) tw[q] = tw1g[q];
-    {
+    if (x0b + grp < n0) {
         // thread gt loads pixels [16 gt, 16 gt + 16) of its row (all loads in flight)
         const size_t rowoff = (size_t)(x0b + grp) * n1;
         const int y0 = 16 * gt;
@@ -106,9 +106,63 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     const int ltr = __ffs(TR) - 1;  // TR is a power of two
     for (int idx = tid; idx < total; idx += nthr) {
         const int m = idx >> ltr, r = idx & (TR - 1);
+        if (x0b + r >= n0) continue;  // rows past the end (n0 not a multiple of TR)
         const cpx<T> *zz = Z + (size_t)r * np;
         const cpx<T> z = zz[pad16(m)];
         const cpx<T> zc = conj(zz[pad16((n1 - m) & (n1 - 1))]);
+        const size_t o = (size_t)m * n0 + r;
+        Fa[o] = scale(z + zc, (T)0.5);
+        if (sb < nseq) Fb[o] = mul_i(scale(z - zc, (T)0.5), -1);
+    }
+}
+
+// Row pass for a row length n1 that is not a power of two: Bluestein DFTs of
+// length n1 through FFTs of length m1 (fft16.cuh); one group of m1/16
+// threads per row, TR rows per block, otherwise as k_rows (two real
+// sequences per complex transform, transposed output).
+template <typename T, typename I>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0, int n1, int m1, int dk, int TR,
+                                               const I *__restrict__ R, const I *__restrict__ S,
+                                               const uint8_t *__restrict__ mask, cpx<T> *__restrict__ F,
+                                               const cpx<T> *__restrict__ chirp, const cpx<T> *__restrict__ bfilt,
+                                               const cpx<T> *__restrict__ twpm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = m1 / 16;
+    const int np = padded_len(m1) + 4;
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // TR * np
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int grp = tid / G, gt = tid - grp * G;
+    const int nseq = dk + 2;
+    const int nfft = (nseq + 1) / 2;
+    const int f = blockIdx.x % nfft;
+    const int x0b = (blockIdx.x / nfft) * TR;
+    const int sa = 2 * f, sb = 2 * f + 1;
+    cpx<T> *zr = Z + (size_t)grp * np;
+    if (x0b + grp < n0) {
+        const size_t rowoff = (size_t)(x0b + grp) * n1;
+        for (int y = gt; y < n1; y += G) {
+            const bool keep = mask == nullptr || mask[rowoff + y] != 0;
+            const T rv = keep ? (T)R[rowoff + y] : (T)0;
+            const T sv = keep ? (T)S[rowoff + y] : (T)0;
+            const T yt = coord<T>(y, n1);
+            const T va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
+            const T vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
+            zr[pad16(y)] = mk(va, vb);
+        }
+    }
+    __syncthreads();
+    bluestein(zr, n1, m1, -1, chirp, bfilt, twpm, gt, G);
+    // separate the two real transforms and write them transposed
+    const int h1c = n1 / 2 + 1;
+    const int total = h1c * TR;
+    cpx<T> *Fa = F + (size_t)sa * h1c * n0 + x0b;
+    cpx<T> *Fb = F + (size_t)sb * h1c * n0 + x0b;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int m = idx / TR, r = idx - m * TR;
+        if (x0b + r >= n0) continue;
+        const cpx<T> *zz = Z + (size_t)r * np;
+        const cpx<T> z = zz[pad16(m)];
+        const cpx<T> zc = conj(zz[pad16(m == 0 ? 0 : n1 - m)]);
         const size_t o = (size_t)m * n0 + r;
         Fa[o] = scale(z + zc, (T)0.5);
         if (sb < nseq) Fb[o] = mul_i(scale(z - zc, (T)0.5), -1);
@@ -436,6 +490,155 @@ __global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_ga
 }
 
 // ---------------------------------------------------------------------------
+// Gather for a column count n0 that is not a power of two: no column FFT; the
+// lag sums along x are evaluated directly as circular cross-correlations in
+// the (x, frequency-y) domain, only at the needed lags |rho| <= h0:
+//     Q(rho, m) = n0 * sum_x conj(Ga(x, m)) Gb(x + rho mod n0, m),
+// which equals the frequency-domain sum of k_gather (correlation theorem).
+// Ga, Gb are xt^i F_j (image (i, j)), S, or xt^p for Lambda.  The DC bin of
+// column m = 0 is removed there by centring both sequences (their means come
+// from an FP64 reduction).  Each term is rounded once in FP32; plain FP32
+// partials over kXcFold steps are folded into two-sum accumulators.
+// Block per column m; per product, Ga and Gb (with a wrapped halo) are staged
+// in shared memory; warp w takes kXcLags lags, each lane 4 consecutive x per
+// step, so that one step is 4 + 4 + kXcLags - 1 loads for 4 kXcLags products.
+constexpr int kXcLags = 5;
+constexpr int kXcFold = 4;
+constexpr int kXcThreads = 256;
+
+// Element x of a sequence at column m: idx < 0 is image t = -idx - 1 (t = nk
+// is S), idx >= 0 the monomial xt^idx; `centre` subtracts its mean.
+template <typename T>
+__device__ __forceinline__ cpx<T> xc_seq(int idx, int dk, int m, bool centre, int x, int h1c, int n0,
+                                         const cpx<T> *__restrict__ F, const T *xt, const double *mu_re,
+                                         const double *mu_im, const double *mu_p) {
+    if (idx >= 0) {
+        const T v = ipow(xt[x], idx) - (centre ? (T)mu_p[idx] : (T)0);
+        return mk(v, (T)0);
+    }
+    const int t = -idx - 1;
+    const int nk = n_terms(dk);
+    int i = 0, j = dk + 1;
+    if (t < nk) term_ij(t, &i, &j);
+    const cpx<T> v = scale(F[((size_t)j * h1c + m) * n0 + x], ipow(xt[x], i));
+    return centre ? v - mk((T)mu_re[t], (T)mu_im[t]) : v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, int db, int npairs, int hmax,
+                                                      const PairDesc *__restrict__ pairs,
+                                                      const cpx<T> *__restrict__ F, cpx<T> *__restrict__ Q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int hB = hmax + 8;                                     // halo of B on each side
+    cpx<T> *A = reinterpret_cast<cpx<T> *>(smem_raw);            // n0 + 8
+    cpx<T> *B = A + n0 + 8;                                      // n0 + 2 hB + 8
+    T *xt = reinterpret_cast<T *>(B + n0 + 2 * hB + 8);          // n0
+    __shared__ double mu_re[12], mu_im[12], mu_p[4];
+    __shared__ double red[kXcThreads / 32][2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = blockIdx.x, h1c = n1 / 2 + 1;
+    const int nk = n_terms(dk);
+    for (int x = tid; x < n0; x += kXcThreads) xt[x] = coord<T>(x, n0);
+    __syncthreads();
+    if (m == 0) {
+        // means of every sequence at m = 0 (the DC bin is removed there)
+        for (int q = 0; q < nk + 1 + db + 1; ++q) {
+            const int idx = q <= nk ? -q - 1 : q - nk - 1;
+            double sr = 0.0, si = 0.0;
+            for (int x = tid; x < n0; x += kXcThreads) {
+                const cpx<T> v = xc_seq<T>(idx, dk, 0, false, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
+                sr += (double)v.re;
+                si += (double)v.im;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) {
+                red[warp][0] = sr;
+                red[warp][1] = si;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0.0, b = 0.0;
+                for (int w = 0; w < kXcThreads / 32; ++w) {
+                    a += red[w][0];
+                    b += red[w][1];
+                }
+                if (q <= nk) {
+                    mu_re[q] = a / n0;
+                    mu_im[q] = b / n0;
+                } else {
+                    mu_p[q - nk - 1] = a / n0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int pi = 0; pi < npairs; ++pi) {
+        const PairDesc pd = pairs[pi];
+        const int h0 = pd.h0;
+        const int ia = -pd.a - 1;
+        const int ib = pd.kind == PK_LAMBDA ? pd.b : -pd.b - 1;  // Theta: b = nk (S)
+        for (int x = tid; x < n0 + 8; x += kXcThreads)
+            A[x] = x < n0 ? conj(xc_seq<T>(ia, dk, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p)) : mk((T)0, (T)0);
+        for (int e = tid; e < n0 + 2 * hB + 8; e += kXcThreads) {
+            int x = (e - hB) % n0;
+            if (x < 0) x += n0;
+            B[e] = xc_seq<T>(ib, dk, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
+        }
+        __syncthreads();
+        const int nlag = 2 * h0 + 1;
+        for (int c0 = warp * kXcLags; c0 < nlag; c0 += (kXcThreads / 32) * kXcLags) {
+            CAcc<T> acc[kXcLags];
+            cpx<T> part[kXcLags];
+#pragma unroll
+            for (int k = 0; k < kXcLags; ++k) {
+                acc[k].zero();
+                part[k] = mk((T)0, (T)0);
+            }
+            int step = 0;
+            for (int x0 = 4 * lane; x0 < n0; x0 += 128) {
+                cpx<T> a[4], bw[4 + kXcLags - 1];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a[q] = A[x0 + q];
+                const int base = x0 - h0 + c0 + hB;  // B index of x0 + rho_0
+#pragma unroll
+                for (int e = 0; e < 4 + kXcLags - 1; ++e) bw[e] = B[base + e];
+#pragma unroll
+                for (int k = 0; k < kXcLags; ++k)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) part[k] = part[k] + cmul(a[q], bw[q + k]);
+                if (++step == kXcFold) {
+#pragma unroll
+                    for (int k = 0; k < kXcLags; ++k) {
+                        acc[k].add(part[k]);
+                        part[k] = mk((T)0, (T)0);
+                    }
+                    step = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kXcLags; ++k) {
+                acc[k].add(part[k]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    shfl_add(acc[k].re, o);
+                    shfl_add(acc[k].im, o);
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < kXcLags; ++k)
+                    if (c0 + k < nlag)
+                        Q[(size_t)(pd.row0 + c0 + k) * h1c + m] =
+                            mk((T)((double)n0 * acc[k].re.wide()), (T)((double)n0 * acc[k].im.wide()));
+            }
+        }
+        __syncthreads();  // A and B are refilled for the next product
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stage 2: sum over m.  One block per stage-1 row.
 template <typename T>
 __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npairs,
@@ -611,6 +814,21 @@ __global__ void k_assemble(int n, int w0, int w1, int dk, int db, int cpr, LagVi
 template <typename T, typename I>
 static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
                                bool moments, cudaStream_t s) {
+    const int nfft = (p->cfg.dk + 3) / 2;
+    if (p->gen1) {
+        const int G = p->m1 / 16;
+        int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
+        if (TR < 1) TR = 1;
+        if (TR > 16) TR = 16;
+        auto smem_of = [&](int tr) { return (size_t)tr * (padded_len(p->m1) + 4) * sizeof(cpx<T>); };
+        while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
+        const size_t smem = smem_of(TR);
+        auto kern = k_rows_blu<T, I>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(
+            p->n0, p->n1, p->m1, p->cfg.dk, TR, (const I *)ref, (const I *)sci, mask, (cpx<T> *)p->F,
+            (const cpx<T> *)p->chirp1, (const cpx<T> *)p->bfilt1, (const cpx<T> *)p->twpm1);
+    } else {
     const int G = p->n1 / 16;
     int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
     if (TR > 16) TR = 16;
@@ -620,9 +838,10 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int nfft = (p->cfg.dk + 3) / 2;
-    kern<<<(p->n0 / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, TR, (const I *)ref, (const I *)sci,
-                                                   mask, (cpx<T> *)p->F, (const cpx<T> *)p->twp1);
+    kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, TR, (const I *)ref,
+                                                              (const I *)sci, mask, (cpx<T> *)p->F,
+                                                              (const cpx<T> *)p->twp1);
+    }
     p->launches++;
     if (moments) {
         k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
@@ -637,6 +856,7 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     const MomLayout ml = mom_layout(p->cfg.dk, p->cfg.db);
     k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
     p->launches++;
+    if (p->gen0) return cudaGetLastError();  // the lag sums along x need no column spectra
     const int G = p->n0 / 16;
     // at most 512 (FP32) / 256 (FP64) threads and about 100 KB of shared
     // memory per block, so that two blocks share an SM
@@ -660,6 +880,15 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
+    if (p->gen0) {
+        const int hmax = 2 * p->cfg.w0;
+        const size_t smem = (size_t)(2 * p->n0 + 2 * (hmax + 8) + 16) * sizeof(cpx<T>) + (size_t)p->n0 * sizeof(T);
+        cudaFuncSetAttribute(k_xcorr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_xcorr<T><<<p->h1c, kXcThreads, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->npairs, hmax, p->pairs,
+                                                    (const cpx<T> *)p->F, (cpx<T> *)p->Q);
+        p->launches++;
+        return cudaGetLastError();
+    }
     const int G = p->na / 8;
     const int nimg = p->nimg, nxp = p->cfg.db + 1;
     // one group of G lanes per product, whole warps, at most 384 threads per

@@ -151,6 +151,53 @@ __host__ __device__ inline int pass_table_len(int n) {
     return len;
 }
 
+// Bluestein (chirp-z) DFT of any length n through power-of-two FFTs of
+// length m >= 2n - 1 (L. Bluestein, 1970): with c_t = exp(-i pi t^2 / n),
+// jk = (j^2 + k^2 - (k - j)^2) / 2 gives
+//     X_k = sum_j x_j exp(-2 pi i jk / n) = c_k sum_j (x_j c_j) conj(c_(k-j)),
+// a convolution of a_j = x_j c_j with b_t = conj(c_t), |t| < n, evaluated by
+// FFTs of length m.  The inverse direction (sgn > 0) conjugates the chirps.
+//   buf   : padded buffer of m entries; x_j at pad16(j) for j < n on entry,
+//           X_k at pad16(k) for k < n on exit (unnormalised);
+//   chirp : c_t, t < n;  bfilt : FFT_m of b (forward chirps);
+//   twpm  : the pass-ordered twiddles of length m.
+// All threads of the block call it (block barriers); gtid/gsize index the
+// group of m/16 threads that owns buf.
+template <typename T>
+__device__ void bluestein(cpx<T> *buf, int n, int m, int sgn, const cpx<T> *__restrict__ chirp,
+                          const cpx<T> *__restrict__ bfilt, const cpx<T> *__restrict__ twpm, int gtid, int gsize) {
+    for (int j = gtid; j < m; j += gsize) {
+        cpx<T> v = mk((T)0, (T)0);
+        if (j < n) {
+            const cpx<T> c = chirp[j];
+            v = cmul(buf[pad16(j)], sgn < 0 ? c : conj(c));
+        }
+        buf[pad16(j)] = v;
+    }
+    __syncthreads();
+    group_fft(buf, m, -1, twpm, gtid, gsize);
+    // the filter of the conjugated chirps is conj(B(-k))
+    for (int k = gtid; k < m; k += gsize) {
+        const cpx<T> b = sgn < 0 ? bfilt[k] : conj(bfilt[(m - k) & (m - 1)]);
+        buf[pad16(k)] = cmul(buf[pad16(k)], b);
+    }
+    __syncthreads();
+    group_fft(buf, m, 1, twpm, gtid, gsize);
+    const T inv = (T)1 / (T)m;
+    for (int k = gtid; k < n; k += gsize) {
+        const cpx<T> c = chirp[k];
+        buf[pad16(k)] = scale(cmul(buf[pad16(k)], sgn < 0 ? c : conj(c)), inv);
+    }
+    __syncthreads();
+}
+
+// Bluestein transform length for n: the least power of two >= 2n - 1.
+__host__ __device__ inline int bluestein_len(int n) {
+    int m = 1;
+    while (m < 2 * n - 1) m *= 2;
+    return m;
+}
+
 // 16 consecutive values of type I from global memory into registers as T,
 // with 16-byte vector loads (p must be 16-byte aligned).
 template <typename T, typename I>

@@ -43,6 +43,11 @@ struct Plan {
     // device workspace
     void *tw0, *tw1;       // twiddle tables exp(-2 pi i q / n), length n0 and n1 (compute type)
     void *twp0, *twp1;     // the same twiddles in pass order for the FFTs (fft16.cuh)
+    // Sizes that are not powers of two.  gen1: the row transforms are
+    // Bluestein DFTs of length n1 through FFTs of length m1; gen0: the lag
+    // sums along x are direct circular correlations (k_xcorr), no column FFT.
+    int gen0, gen1, m1;
+    void *chirp1, *bfilt1, *twpm1;  // Bluestein tables for n1 (compute type)
     void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
     void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
     void *F;               // [(dk+2)][m][x] row transforms (compute type)

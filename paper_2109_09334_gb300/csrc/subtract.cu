@@ -89,7 +89,7 @@ __global__ void k_kernel_table(int n1, int nk, int w0, int w1, int cpr, const do
 template <typename T>
 __host__ __device__ constexpr int sub_q() { return sizeof(T) == 4 ? 4 : 8; }
 
-template <typename T>
+template <typename T, bool P2>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0, int n1, int dk, int db, int w0,
                                                                          int nbkg_off, const cpx<T> *__restrict__ F,
                                                                          const cpx<T> *__restrict__ kap,
@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
     auto padq = [](int v) { return v + v / Q; };
     const int m = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
     const int h1c = n1 / 2 + 1;
-    const int msk = n0 - 1;  // n0 is a power of two
-    const int x0 = Q * tid;
+    const int msk = n0 - 1;
+    // index mod n0 for -n0 <= v < 2 n0 (P2: n0 is a power of two)
+    auto wrapx = [&](int v) { return P2 ? (v & msk) : (v < 0 ? v + n0 : (v >= n0 ? v - n0 : v)); };
+    const int x0 = Q * tid;  // outputs x0 .. x0 + Q - 1 below n0
     for (int e = tid; e < nk * L0; e += nthr) kp[e] = kap[(size_t)e * h1c + m];
     T xt[Q];
 #pragma unroll
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
     {
         const cpx<T> *Sc = F + ((size_t)(dk + 1) * h1c + m) * n0 + x0;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) acc[q] = Sc[q];
+        for (int q = 0; q < Q; ++q) acc[q] = (P2 || x0 + q < n0) ? Sc[q] : mk((T)0, (T)0);
         for (int s = 0; s < nbt; ++s) {
             int p, qq;
             term_ij(s, &p, &qq);
@@ -130,29 +132,31 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
         cpx<T> f[Q];
         const cpx<T> *Fj = F + ((size_t)j * h1c + m) * n0 + x0;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) f[q] = Fj[q];
+        for (int q = 0; q < Q; ++q) f[q] = (P2 || x0 + q < n0) ? Fj[q] : mk((T)0, (T)0);
         for (int i = 0; i + j <= dk; ++i) {
             __syncthreads();  // previous term's window reads are done
 #pragma unroll
-            for (int q = 0; q < Q; ++q) W[padq(x0 + q)] = scale(f[q], ipow(xt[q], i));
+            for (int q = 0; q < Q; ++q)
+                if (P2 || x0 + q < n0) W[padq(x0 + q)] = scale(f[q], ipow(xt[q], i));
             __syncthreads();
             const cpx<T> *kt = kp + term_index(i, j) * L0;
             cpx<T> win[Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) win[q] = W[padq((x0 - w0 + q) & msk)];
+            for (int q = 0; q < Q; ++q) win[q] = W[padq(wrapx(x0 - w0 + q))];
             for (int a = w0; a >= -w0; --a) {
                 const cpx<T> kv = kt[a + w0];
 #pragma unroll
                 for (int q = 0; q < Q; ++q) acc[q] = acc[q] - cmul(kv, win[q]);
 #pragma unroll
                 for (int q = 0; q + 1 < Q; ++q) win[q] = win[q + 1];
-                win[Q - 1] = W[padq((x0 + Q - a) & msk)];
+                win[Q - 1] = W[padq(wrapx(x0 + Q - a))];
             }
         }
     }
     cpx<T> *out = Dt + (size_t)m * n0 + x0;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) out[q] = acc[q];
+    for (int q = 0; q < Q; ++q)
+        if (P2 || x0 + q < n0) out[q] = acc[q];
 }
 
 // Inverse real FFT of rows: NG groups of G = n1/16 threads per block, each
@@ -181,8 +185,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_rows_inv(int n0,
         for (int c = 0; c < 16; ++c) {
             const int mm = gt + c * G;
             const int mr = (mm <= half) ? mm : n1 - mm;
-            A[c] = Dt[(size_t)mr * n0 + xa];
-            B[c] = Dt[(size_t)mr * n0 + xb];
+            A[c] = xa < n0 ? Dt[(size_t)mr * n0 + xa] : mk((T)0, (T)0);
+            B[c] = xb < n0 ? Dt[(size_t)mr * n0 + xb] : mk((T)0, (T)0);
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -196,8 +200,45 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_rows_inv(int n0,
     group_fft(zr, n1, 1, tw, gt, G);
     for (int y = gt; y < n1; y += G) {
         const cpx<T> z = zr[pad16(y)];
-        D[(size_t)xa * n1 + y] = (I)(z.re * inv);
-        D[(size_t)xb * n1 + y] = (I)(z.im * inv);
+        if (xa < n0) D[(size_t)xa * n1 + y] = (I)(z.re * inv);
+        if (xb < n0) D[(size_t)xb * n1 + y] = (I)(z.im * inv);
+    }
+}
+
+// Inverse real transform of rows for a row length n1 that is not a power of
+// two: as k_rows_inv, with Bluestein DFTs of length n1 (FFTs of length m1).
+template <typename T, typename I>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv_blu(int n0, int n1, int m1, int NG,
+                                                       const cpx<T> *__restrict__ Dt,
+                                                       const cpx<T> *__restrict__ chirp,
+                                                       const cpx<T> *__restrict__ bfilt,
+                                                       const cpx<T> *__restrict__ twpm, I *__restrict__ D) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = m1 / 16;
+    const int np = padded_len(m1);
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // NG * np
+    const int tid = threadIdx.x;
+    const int grp = tid / G, gt = tid - grp * G;
+    const int half = n1 / 2;
+    const T inv = (T)1 / (T)n1;
+    const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
+    cpx<T> *zr = Z + (size_t)grp * np;
+    for (int mm = gt; mm < n1; mm += G) {
+        const int mr = (mm <= half) ? mm : n1 - mm;
+        cpx<T> a = xa < n0 ? Dt[(size_t)mr * n0 + xa] : mk((T)0, (T)0);
+        cpx<T> b = xb < n0 ? Dt[(size_t)mr * n0 + xb] : mk((T)0, (T)0);
+        if (mm > half) {
+            a = conj(a);
+            b = conj(b);
+        }
+        zr[pad16(mm)] = a + mul_i(b, 1);
+    }
+    __syncthreads();
+    bluestein(zr, n1, m1, 1, chirp, bfilt, twpm, gt, G);
+    for (int y = gt; y < n1; y += G) {
+        const cpx<T> z = zr[pad16(y)];
+        if (xa < n0) D[(size_t)xa * n1 + y] = (I)(z.re * inv);
+        if (xb < n0) D[(size_t)xb * n1 + y] = (I)(z.im * inv);
     }
 }
 
@@ -214,29 +255,52 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
                                              ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
     if ((err = cudaGetLastError())) return err;
     {
-        const int nthr = p->n0 / sub_q<T>();
+        const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
         const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
-        cudaFuncSetAttribute(k_sub_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int nbkg_off = p->n - p->nb;
-        k_sub_cols<T><<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
-                                                 (const cpx<T> *)p->F, (const cpx<T> *)p->kap,
-                                                 (const cpx<T> *)p->yhat, x, (cpx<T> *)p->U);
+        auto kern = p->gen0 ? k_sub_cols<T, false> : k_sub_cols<T, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
+                                        (const cpx<T> *)p->F, (const cpx<T> *)p->kap, (const cpx<T> *)p->yhat, x,
+                                        (cpx<T> *)p->U);
         if ((err = cudaGetLastError())) return err;
     }
-    {
+    if (p->gen1) {
+        const int G = p->m1 / 16;
+        int NG = (sizeof(T) == 4 ? 1024 : 512) / G;
+        if (NG < 1) NG = 1;
+        if (NG > 4) NG = 4;
+        if (NG > (p->n0 + 1) / 2) NG = (p->n0 + 1) / 2;
+        size_t smem = (size_t)NG * padded_len(p->m1) * sizeof(cpx<T>);
+        while (NG > 1 && smem > 200 * 1024) {
+            NG /= 2;
+            smem = (size_t)NG * padded_len(p->m1) * sizeof(cpx<T>);
+        }
+        const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
+        const cpx<T> *ch = (const cpx<T> *)p->chirp1, *bf = (const cpx<T> *)p->bfilt1, *tw = (const cpx<T> *)p->twpm1;
+        if (p->cfg.dtype == SFFT_F64) {
+            cudaFuncSetAttribute(k_rows_inv_blu<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_rows_inv_blu<T, double><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, p->m1, NG, (const cpx<T> *)p->U,
+                                                                    ch, bf, tw, (double *)diff);
+        } else {
+            cudaFuncSetAttribute(k_rows_inv_blu<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_rows_inv_blu<T, float><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, p->m1, NG, (const cpx<T> *)p->U,
+                                                                   ch, bf, tw, (float *)diff);
+        }
+    } else {
         const int G = p->n1 / 16;
         // at most 512 (FP32) / 256 (FP64) threads and about 100 KB of shared
         // memory per block, so that two blocks share an SM
         int NG = (sizeof(T) == 4 ? 512 : 256) / G;
         if (NG < 1) NG = 1;
         if (NG > 4) NG = 4;
-        if (NG > p->n0 / 2) NG = p->n0 / 2;
+        if (NG > (p->n0 + 1) / 2) NG = (p->n0 + 1) / 2;
         size_t smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
         while (NG > 1 && smem > 110 * 1024) {
             NG /= 2;
             smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
         }
-        const int blocks = p->n0 / (2 * NG);
+        const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
         if (p->cfg.dtype == SFFT_F64) {
             cudaFuncSetAttribute(k_rows_inv<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_rows_inv<T, double><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, NG, (const cpx<T> *)p->U,

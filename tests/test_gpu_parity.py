@@ -64,6 +64,14 @@ SMALL = [
     (128, 64, 4, 2, 3, 3, 1, False),
     (64, 128, 5, 6, 0, 3, 1, True),
     (256, 64, 0, 0, 2, 2, 1, False),
+    # sizes that are not powers of two: Bluestein row transforms (n1) and
+    # direct lag sums along x (n0)
+    (48, 40, 2, 2, 1, 1, 1, False),
+    (40, 64, 3, 2, 2, 1, 0, True),
+    (64, 48, 2, 3, 1, 2, 1, False),
+    (37, 41, 2, 1, 0, 1, 1, True),
+    (17, 19, 1, 1, 1, 0, 0, False),
+    (100, 96, 4, 4, 2, 2, 1, False),
 ]
 
 
@@ -150,7 +158,7 @@ def test_singular_reference_reports_status():
 def test_invalid_configs_rejected():
     from paper_2109_09334_gb300 import SfftError, SfftPlan
     with pytest.raises(SfftError):
-        SfftPlan(100, 64, 2, 2, 0, 0, 1)        # not a power of two
+        SfftPlan(5000, 64, 2, 2, 0, 0, 1)       # beyond the largest supported size
     with pytest.raises(SfftError):
         SfftPlan(64, 64, 16, 2, 0, 0, 1)        # lag range beyond the inner transform
     with pytest.raises(SfftError):
