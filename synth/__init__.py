@@ -81,6 +81,26 @@ PAIR4096 = PairSpec("pair4096", 4096, 4096, "float32", 20000, flux_law="powerlaw
 SPECS = {s.name: s for s in (PAIR256, PAIR1024, PAIR4096)}
 
 
+def sector(n: int, fit: FitParams, name: str | None = None) -> PairSpec:
+    """One sector of the variable-size workloads: an n x n float32 pair with
+    the PSF, sky and noise family of the 4096^2 pair, one source per 500 px^2."""
+    return replace(PAIR4096, name=name or f"sector{n}", n0=n, n1=n, n_src=max(1, (n * n) // 500),
+                   n_transients=max(1, (50 * n * n) // (4096 * 4096)), fit=fit)
+
+
+def draw_sectors(count: int, seed: int, n_range=(512, 2048)):
+    """Sector specs with n uniform over the integers of n_range and w in 4..8,
+    D_K and D_B in 0..2 drawn per sector (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        w = int(rng.integers(4, 9))
+        fit = FitParams(w, w, int(rng.integers(0, 3)), int(rng.integers(0, 3)), True)
+        out.append(sector(n, fit, name=f"sector{k}:{n}"))
+    return out
+
+
 def scaled(spec: PairSpec, n0: int, n1: int | None = None, name: str | None = None) -> PairSpec:
     """Same structure at another size, keeping the source density."""
     n1 = n0 if n1 is None else n1
