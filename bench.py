@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 single-pair comparison")
     ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
     ap.add_argument("--batch", type=int, default=4, help="systems solved per launch in the serving path")
     return ap.parse_args()
@@ -54,6 +55,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(vals, world, device=None):
+    """Element-wise maximum of `vals` over all ranks (the slowest rank sets the
+    time of a replicated run); a no-op for one rank."""
+    if world <= 1:
+        return list(vals)
+    import torch
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def pairs_per_second(world, steps, total_ms):
+    """Whole-job throughput of a replicated run: every rank processes `steps`
+    pairs, and the job takes as long as its slowest rank."""
+    return world * steps / (total_ms / 1e3)
 
 
 def workload_config(spec, precision):
@@ -335,11 +353,8 @@ def run_ours(args):
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     seq_ms = evs[0].elapsed_time(evs[-1])
     total_ms = es0.elapsed_time(es1)
-    if world > 1:
-        t = torch.tensor([total_ms, seq_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, seq_ms = float(t[0].item()), float(t[1].item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, seq_ms = max_over_ranks([total_ms, seq_ms], world, dev)
+    value = pairs_per_second(world, args.steps, total_ms)
     ms_step = total_ms / args.steps
     P = spec.n0 * spec.n1
 
@@ -442,10 +457,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         run_host(ke)
         te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks([te], world, dev)[0]
         inf_h = info_from_bytes(hout[(ke - 1) % len(hout)][2].numpy())
         if inf_h["status"] != 0:
             raise RuntimeError(f"host-request solve status {inf_h}")
@@ -455,6 +467,41 @@ def run_ours(args):
         result["e2e"] = {"value": world * ke / te, "unit": UNIT, "h2d_bytes_per_step": bi,
                          "d2h_bytes_per_step": bo, "steps": ke, "api": "sfft_submit (host requests)",
                          "clock": "host wall clock, submit of the first to completion of the last"}
+
+    # the plain FP64 GPU path (FP64 FFTs, products, sums, Cholesky), one pair
+    # at a time on the same inputs, and how far the headline path's difference
+    # image is from it (in units of the noise sigma)
+    if not args.no_fp64 and args.precision == "mixed":
+        p64 = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
+                       precision="fp64")
+        s64 = p64.stream
+        D64 = torch.empty_like(D)
+        x64 = torch.empty_like(x)
+        i64 = torch.zeros_like(info)
+        for k in range(2):
+            binding.sfft_run_pair(p64.handle, dev_pairs[k & 1][0], dev_pairs[k & 1][1], None, None, None, x64, i64,
+                                  D64, s64)
+        k64 = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s64)
+        for k in range(k64):
+            binding.sfft_run_pair(p64.handle, dev_pairs[k & 1][0], dev_pairs[k & 1][1], None, None, None, x64, i64,
+                                  D64, s64)
+        e1.record(s64)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / k64
+        # both paths on pair 0
+        binding.sfft_run_pair(p64.handle, dev_pairs[0][0], dev_pairs[0][1], None, None, None, x64, i64, D64, s64)
+        step(0)
+        torch.cuda.synchronize()
+        dd = float(torch.sqrt(torch.mean((D.double() - D64.double()) ** 2)).item())
+        result["fp64_single_pair"] = {"value": world * 1e3 / t64, "unit": UNIT, "ms_per_pair": t64, "steps": k64,
+                                      "solve": info_from_bytes(i64.cpu().numpy()),
+                                      "rms_diff_vs_headline_sigma": dd / spec.sigma,
+                                      "note": "plain FP64 path, sfft_run_pair, same inputs; D of the mixed path "
+                                              "compared with it on pair 0"}
+        p64.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
