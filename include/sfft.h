@@ -270,6 +270,46 @@ int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_u
  */
 int sfft_stream_wait_ticket(sfft_server_t server, const sfft_ticket *ticket, sfft_stream_t stream);
 
+/* ---- pool: pairs of many configurations under one memory budget -------- */
+/*
+ * A pool holds one server (lane) per configuration it has seen, each with
+ * `depth` slots and solve batches of `batch`, created on first use and kept
+ * with their plans and spectra on the device.  Lanes of different
+ * configurations run on their own streams, so their work overlaps on the
+ * GPU.  Admission by memory footprint: a new configuration is admitted only
+ * if its lane fits in `budget_bytes` together with the lanes held; idle lanes
+ * (every request completed, nobody waiting) are released, least recently used
+ * first, to make room.  Results equal sfft_run_pair's on the same inputs.
+ */
+typedef struct sfft_pool_s *sfft_pool_t;
+
+typedef struct {
+    uint64_t lane; /* lane id, from 1 */
+    uint64_t seq;  /* submission number within the lane */
+} sfft_pool_ticket;
+
+/* budget_bytes > 0; 1 <= batch <= depth <= 8. */
+int sfft_pool_create(uint64_t budget_bytes, int32_t depth, int32_t batch, sfft_pool_t *out);
+
+/* Waits for every request, then frees all lanes.  NULL is a no-op. */
+int sfft_pool_destroy(sfft_pool_t pool);
+
+/*
+ * Enqueue one pair of configuration *cfg (as sfft_submit, same request
+ * rules).  SFFT_ERR_BUSY: the configuration's lane does not fit the budget
+ * even after releasing the idle lanes; wait for some ticket and retry.
+ * Thread-safe.
+ */
+int sfft_pool_submit(sfft_pool_t pool, const sfft_config *cfg, const sfft_request *req,
+                     sfft_pool_ticket *ticket);
+
+/* As sfft_poll / sfft_wait for a pool ticket. */
+int sfft_pool_poll(sfft_pool_t pool, const sfft_pool_ticket *ticket);
+int sfft_pool_wait(sfft_pool_t pool, const sfft_pool_ticket *ticket, int64_t timeout_us);
+
+/* Device bytes held by the pool's lanes and their number. */
+int sfft_pool_usage(sfft_pool_t pool, uint64_t *bytes, int32_t *lanes);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Stages of one pair, as re-enqueued by sfft_replay_stage. */

@@ -221,3 +221,62 @@ class SfftServer:
             self.close()
         except Exception:
             pass
+
+
+class SfftPool:
+    """Pairs of many configurations under one device-memory budget
+    (sfft_pool_*): one lane per configuration, created on first use,
+    idle lanes released least recently used first to admit new ones."""
+
+    def __init__(self, budget_bytes, depth=2, batch=1):
+        self.handle = binding.sfft_pool_create(budget_bytes, depth, batch)
+        self._keep = {}
+
+    def submit(self, ref, sci, w0, w1, dk, db, const_phot_ratio, precision="mixed", mask=None, diff=None,
+               stream=None):
+        """Enqueue a pair; returns (ticket, diff, x, info), or None if it cannot be admitted now."""
+        torch = _torch()
+        host = not ref.is_cuda
+        dtype = {torch.float32: "float32", torch.float64: "float64"}[ref.dtype]
+        n0, n1 = ref.shape
+        cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        n = sfft_num_unknowns(cfg)
+        dev = "cpu" if host else ref.device
+        pin = dict(pin_memory=True) if host else {}
+        if diff is None:
+            diff = torch.empty((n0, n1), dtype=ref.dtype, device=dev, **pin)
+        x = torch.empty(n, dtype=torch.float64, device=dev, **pin)
+        info = torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=dev, **pin)
+        if stream is None and not host:
+            stream = torch.cuda.current_stream()
+        req = make_request(ref, sci, diff, mask=mask, x=x, info=info, stream=stream, host=host)
+        t = binding.sfft_pool_submit(self.handle, cfg, req)
+        if t is None:
+            return None
+        self._keep[(t.lane, t.seq)] = (req, ref, sci, mask, diff, x, info)
+        return t, diff, x, info
+
+    def wait(self, ticket, timeout_us=-1):
+        done = binding.sfft_pool_wait(self.handle, ticket, timeout_us)
+        if done:
+            self._keep.pop((ticket.lane, ticket.seq), None)
+        return done
+
+    def poll(self, ticket):
+        return binding.sfft_pool_poll(self.handle, ticket)
+
+    @property
+    def usage(self):
+        return binding.sfft_pool_usage(self.handle)
+
+    def close(self):
+        if self.handle:
+            binding.sfft_pool_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -53,6 +53,10 @@ class sfft_ticket(ctypes.Structure):
     _fields_ = [("seq", ctypes.c_uint64)]
 
 
+class sfft_pool_ticket(ctypes.Structure):
+    _fields_ = [("lane", ctypes.c_uint64), ("seq", ctypes.c_uint64)]
+
+
 class SfftError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -92,6 +96,13 @@ def library():
         lib.sfft_wait.argtypes = [vp, tkp, ctypes.c_int64]
         lib.sfft_stream_wait_ticket.argtypes = [vp, tkp, vp]
         lib.sfft_server_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        ptk = ctypes.POINTER(sfft_pool_ticket)
+        lib.sfft_pool_create.argtypes = [ctypes.c_uint64, i32, i32, ctypes.POINTER(vp)]
+        lib.sfft_pool_destroy.argtypes = [vp]
+        lib.sfft_pool_submit.argtypes = [vp, cfgp, reqp, ptk]
+        lib.sfft_pool_poll.argtypes = [vp, ptk]
+        lib.sfft_pool_wait.argtypes = [vp, ptk, ctypes.c_int64]
+        lib.sfft_pool_usage.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
         _lib = lib
@@ -254,6 +265,48 @@ def sfft_server_launch_count(server):
     c = ctypes.c_uint64()
     _check(library().sfft_server_launch_count(server, ctypes.byref(c)), "sfft_server_launch_count")
     return c.value
+
+
+def sfft_pool_create(budget_bytes, depth=2, batch=1):
+    h = ctypes.c_void_p()
+    _check(library().sfft_pool_create(int(budget_bytes), int(depth), int(batch), ctypes.byref(h)), "sfft_pool_create")
+    return h.value
+
+
+def sfft_pool_destroy(pool):
+    _check(library().sfft_pool_destroy(pool), "sfft_pool_destroy")
+
+
+def sfft_pool_submit(pool, cfg, req):
+    """Ticket, or None if the configuration cannot be admitted now (SFFT_ERR_BUSY)."""
+    t = sfft_pool_ticket()
+    rc = library().sfft_pool_submit(pool, ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(t))
+    if rc == SFFT_ERR_BUSY:
+        return None
+    _check(rc, "sfft_pool_submit")
+    return t
+
+
+def sfft_pool_poll(pool, ticket):
+    rc = library().sfft_pool_poll(pool, ctypes.byref(ticket))
+    if rc == SFFT_ERR_BUSY:
+        return False
+    _check(rc, "sfft_pool_poll")
+    return True
+
+
+def sfft_pool_wait(pool, ticket, timeout_us=-1):
+    rc = library().sfft_pool_wait(pool, ctypes.byref(ticket), int(timeout_us))
+    if rc == SFFT_ERR_TIMEOUT:
+        return False
+    _check(rc, "sfft_pool_wait")
+    return True
+
+
+def sfft_pool_usage(pool):
+    b, n = ctypes.c_uint64(), ctypes.c_int32()
+    _check(library().sfft_pool_usage(pool, ctypes.byref(b), ctypes.byref(n)), "sfft_pool_usage")
+    return b.value, n.value
 
 
 def sfft_plan_launch_count(plan):

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -39,6 +40,7 @@ namespace {
 
 constexpr int kMaxDepth = 8;
 constexpr int kRing = 64;  // completion events kept; submit waits beyond this
+constexpr int kMaxPoolLanes = 64;  // configurations a pool holds at once
 
 struct Slot {
     Plan *plan = nullptr;
@@ -69,6 +71,7 @@ struct Server {
     uint64_t flushed = 0;    // every request below it has its solve and subtraction enqueued
     uint64_t watermark = 0;  // every request below it has completed
     std::mutex mu;
+    int refs = 0;  // callers waiting on it through a pool (guarded by the pool's lock)
 };
 
 namespace {
@@ -256,6 +259,79 @@ int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
 }
 
 }  // namespace
+
+// ---- pool: servers of several configurations under one byte budget --------
+
+namespace {
+
+struct Lane {
+    uint64_t id = 0;
+    sfft_config cfg{};
+    Server *srv = nullptr;
+    uint64_t bytes = 0;
+    uint64_t last_use = 0;
+};
+
+bool same_config(const sfft_config &a, const sfft_config &b) { return memcmp(&a, &b, sizeof(sfft_config)) == 0; }
+
+// every request of the lane has completed (caller holds the pool's lock)
+bool lane_idle(Lane &l) {
+    std::lock_guard<std::mutex> lock(l.srv->mu);
+    advance(l.srv);
+    return l.srv->flushed == l.srv->next_seq && l.srv->watermark == l.srv->next_seq;
+}
+
+uint64_t server_bytes(const Server *v) {
+    uint64_t b = 0;
+    for (int i = 0; i < v->depth; ++i) b += v->slots[i].plan->ws_bytes + 3 * v->img_bytes + v->pixels;
+    return b;
+}
+
+}  // namespace
+
+struct Pool {
+    uint64_t budget = 0, used = 0, next_id = 1, clock = 0;
+    int depth = 1, batch = 1;
+    Lane lanes[kMaxPoolLanes];
+    int nlanes = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+Lane *find_lane(Pool *pl, uint64_t id) {
+    for (int k = 0; k < pl->nlanes; ++k)
+        if (pl->lanes[k].id == id) return &pl->lanes[k];
+    return nullptr;
+}
+
+void drop_lane(Pool *pl, int k) {
+    Lane &l = pl->lanes[k];
+    sfft_server_destroy((sfft_server_t)l.srv);
+    pl->used -= l.bytes;
+    pl->lanes[k] = pl->lanes[pl->nlanes - 1];
+    --pl->nlanes;
+}
+
+// release idle lanes, least recently used first, until `need` more bytes fit
+// (or a lane slot is needed); returns whether they fit
+bool make_room(Pool *pl, uint64_t need, bool want_slot, uint64_t keep_id) {
+    for (;;) {
+        const bool fits = pl->used + need <= pl->budget && (!want_slot || pl->nlanes < kMaxPoolLanes);
+        if (fits) return true;
+        int victim = -1;
+        for (int k = 0; k < pl->nlanes; ++k) {
+            Lane &l = pl->lanes[k];
+            if (l.id == keep_id || l.srv->refs > 0 || !lane_idle(l)) continue;
+            if (victim < 0 || l.last_use < pl->lanes[victim].last_use) victim = k;
+        }
+        if (victim < 0) return false;
+        drop_lane(pl, victim);
+    }
+}
+
+}  // namespace
+
 }  // namespace sfft
 
 using namespace sfft;
@@ -375,6 +451,112 @@ int sfft_server_workspace_bytes(sfft_server_t server, uint64_t *bytes) {
     uint64_t b = 0;
     for (int i = 0; i < v->depth; ++i) b += v->slots[i].plan->ws_bytes + 3 * v->img_bytes + v->pixels;
     *bytes = b;
+    return SFFT_OK;
+}
+
+
+int sfft_pool_create(uint64_t budget_bytes, int32_t depth, int32_t batch, sfft_pool_t *out) {
+    if (!out) return SFFT_ERR_INVALID;
+    *out = nullptr;
+    if (budget_bytes == 0 || depth < 1 || depth > kMaxDepth || batch < 1 || batch > depth) return SFFT_ERR_INVALID;
+    Pool *pl = new (std::nothrow) Pool();
+    if (!pl) return SFFT_ERR_OOM;
+    pl->budget = budget_bytes;
+    pl->depth = depth;
+    pl->batch = batch;
+    *out = (sfft_pool_t)pl;
+    return SFFT_OK;
+}
+
+int sfft_pool_destroy(sfft_pool_t pool) {
+    if (!pool) return SFFT_OK;
+    Pool *pl = (Pool *)pool;
+    {
+        std::lock_guard<std::mutex> lock(pl->mu);
+        while (pl->nlanes > 0) drop_lane(pl, pl->nlanes - 1);
+    }
+    delete pl;
+    return SFFT_OK;
+}
+
+int sfft_pool_submit(sfft_pool_t pool, const sfft_config *cfg, const sfft_request *req, sfft_pool_ticket *ticket) {
+    if (!pool || !cfg || !req || !ticket) return SFFT_ERR_INVALID;
+    if (!req->ref || !req->sci || !req->diff) return SFFT_ERR_INVALID;
+    if (req->memory != SFFT_REQ_DEVICE && req->memory != SFFT_REQ_HOST) return SFFT_ERR_INVALID;
+    const int v = plan_validate(cfg);
+    if (v) return v;
+    Pool *pl = (Pool *)pool;
+    std::lock_guard<std::mutex> lock(pl->mu);
+    Lane *lane = nullptr;
+    for (int k = 0; k < pl->nlanes; ++k)
+        if (same_config(pl->lanes[k].cfg, *cfg)) lane = &pl->lanes[k];
+    if (!lane) {
+        // admission: the new lane's workspace must fit the budget
+        if (!make_room(pl, 0, true, 0)) return SFFT_ERR_BUSY;
+        Server *srv = nullptr;
+        int rc = create_server(cfg, pl->depth, pl->batch, &srv);
+        if (rc == SFFT_ERR_OOM) {  // the device itself is full: release idle lanes and retry once
+            if (!make_room(pl, pl->budget, true, 0)) return SFFT_ERR_BUSY;
+            rc = create_server(cfg, pl->depth, pl->batch, &srv);
+        }
+        if (rc != SFFT_OK) return rc;
+        const uint64_t bytes = server_bytes(srv);
+        if (!make_room(pl, bytes, true, 0)) {
+            sfft_server_destroy((sfft_server_t)srv);
+            return SFFT_ERR_BUSY;
+        }
+        lane = &pl->lanes[pl->nlanes++];
+        lane->id = pl->next_id++;
+        lane->cfg = *cfg;
+        lane->srv = srv;
+        lane->bytes = bytes;
+        pl->used += bytes;
+    }
+    lane->last_use = ++pl->clock;
+    sfft_ticket t;
+    const int rc = sfft_submit((sfft_server_t)lane->srv, req, &t);
+    if (rc != SFFT_OK) return rc;
+    ticket->lane = lane->id;
+    ticket->seq = t.seq;
+    return SFFT_OK;
+}
+
+int sfft_pool_wait(sfft_pool_t pool, const sfft_pool_ticket *ticket, int64_t timeout_us) {
+    if (!pool || !ticket) return SFFT_ERR_INVALID;
+    Pool *pl = (Pool *)pool;
+    Server *srv = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(pl->mu);
+        if (ticket->lane == 0 || ticket->lane >= pl->next_id) return SFFT_ERR_INVALID;
+        Lane *l = find_lane(pl, ticket->lane);
+        if (!l) return SFFT_OK;  // a lane is released only once all its requests have completed
+        srv = l->srv;
+        ++srv->refs;  // the lane is not released while this wait uses it
+    }
+    sfft_ticket t{ticket->seq};
+    const int rc = sfft_wait((sfft_server_t)srv, &t, timeout_us);
+    std::lock_guard<std::mutex> lock(pl->mu);
+    --srv->refs;
+    return rc;
+}
+
+int sfft_pool_poll(sfft_pool_t pool, const sfft_pool_ticket *ticket) {
+    if (!pool || !ticket) return SFFT_ERR_INVALID;
+    Pool *pl = (Pool *)pool;
+    std::lock_guard<std::mutex> lock(pl->mu);
+    if (ticket->lane == 0 || ticket->lane >= pl->next_id) return SFFT_ERR_INVALID;
+    Lane *l = find_lane(pl, ticket->lane);
+    if (!l) return SFFT_OK;
+    sfft_ticket t{ticket->seq};
+    return sfft_poll((sfft_server_t)l->srv, &t);
+}
+
+int sfft_pool_usage(sfft_pool_t pool, uint64_t *bytes, int32_t *lanes) {
+    if (!pool || !bytes || !lanes) return SFFT_ERR_INVALID;
+    Pool *pl = (Pool *)pool;
+    std::lock_guard<std::mutex> lock(pl->mu);
+    *bytes = pl->used;
+    *lanes = pl->nlanes;
     return SFFT_OK;
 }
 
