@@ -394,6 +394,16 @@ __global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_ga
         part[o] = mk((T)0, (T)0);
     }
     cpx<T> *tg = sT + (size_t)grp * NAP;
+    // NS = 5 (G = 8, lags <= 16): validity and lag of each output slot
+    bool o_ok[NS];
+    int o_rho[NS];
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+        const int s1 = o < 3 ? o : o + 3;
+        const int rp = lane + 8 * s1;
+        o_ok[o] = rp <= h0 || rp >= NA - h0;
+        o_rho[o] = rp <= h0 ? rp : rp - NA;
+    }
     constexpr int kPer16 = 16 / (int)sizeof(cpx<T>);
     constexpr int kChunksPerImg = NA / kPer16;
     const int chunks = (nimg + nxp) * kChunksPerImg;
@@ -439,7 +449,18 @@ __global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_ga
             }
         }
         __syncwarp();
-        if (act) {
+        if (act && NS == 5) {
+            // G = 8: this lane's s2 = lane; outputs s1 in {0, 1, 2, 6, 7} with
+            // their lags precomputed (they do not depend on lb)
+            const cpx<T> *wrow_lb = sW + (size_t)lb * wrow + hmax;
+            cpx<T> u[G];
+#pragma unroll
+            for (int r1 = 0; r1 < G; ++r1) u[r1] = tg[lane * 8 + (r1 ^ lane)];
+            dftG<T, G>(u, 1);
+#pragma unroll
+            for (int o = 0; o < NS; ++o)
+                if (o_ok[o]) part[o] = part[o] + cmul(u[o < 3 ? o : o + 3], wrow_lb[o_rho[o]]);
+        } else if (act) {
             const cpx<T> *wrow_lb = sW + (size_t)lb * wrow + hmax;
             // lane handles s2 = lane + G*c for c < 8/G; G-point DFT over r1
 #pragma unroll
@@ -460,12 +481,12 @@ __global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_ga
                     if (o >= 0) part[o] = part[o] + cmul(u[s1], wrow_lb[rho]);
                 }
             }
-            if ((lb % kFold) == kFold - 1 || lb == nbk - 1) {
+        }
+        if (act && ((lb % kFold) == kFold - 1 || lb == nbk - 1)) {
 #pragma unroll
-                for (int o = 0; o < NS; ++o) {
-                    acc[o].add(part[o]);
-                    part[o] = mk((T)0, (T)0);
-                }
+            for (int o = 0; o < NS; ++o) {
+                acc[o].add(part[o]);
+                part[o] = mk((T)0, (T)0);
             }
         }
         __syncthreads();  // the buffer of this step is refilled two steps later
