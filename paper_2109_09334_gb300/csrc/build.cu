@@ -186,10 +186,11 @@ __global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, c
     for (int v = 0; v < 7; ++v) pRR[v] = pR[v] = (T)0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) pRS[v] = pS[v] = (T)0;
+#pragma unroll 4
     for (int y = tid; y < n1; y += nthr) {
         const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
-        const T rv = (T)load_img(R, rowoff + y) * keep;
-        const T sv = (T)load_img(S, rowoff + y) * keep;
+        const T rv = (T)R[rowoff + y] * keep;
+        const T sv = (T)S[rowoff + y] * keep;
         const T yt = coord<T>(y, n1);
         T p = (T)1;
 #pragma unroll

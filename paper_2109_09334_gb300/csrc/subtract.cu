@@ -89,7 +89,9 @@ __global__ void k_kernel_table(int n1, int nk, int w0, int w1, int cpr, const do
 template <typename T>
 __host__ __device__ constexpr int sub_q() { return sizeof(T) == 4 ? 4 : 8; }
 
-template <typename T, bool P2>
+// W0 >= 0: the kernel half-width is the compile-time W0 (the tap loop unrolls
+// completely, so the window shifts are register renames); W0 < 0: w0 at run time.
+template <typename T, bool P2, int W0>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0, int n1, int dk, int db, int w0,
                                                                          int nbkg_off, const cpx<T> *__restrict__ F,
                                                                          const cpx<T> *__restrict__ kap,
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
                                                                          cpx<T> *__restrict__ Dt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = n_terms(dk), nbt = n_terms(db);
+    if (W0 >= 0) w0 = W0;
     const int L0 = 2 * w0 + 1;
     cpx<T> *kp = reinterpret_cast<cpx<T> *>(smem_raw);  // nk * L0
     constexpr int Q = sub_q<T>();
@@ -143,7 +146,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
             cpx<T> win[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) win[q] = W[padq(wrapx(x0 - w0 + q))];
-            for (int a = w0; a >= -w0; --a) {
+#pragma unroll
+            for (int a = (W0 >= 0 ? W0 : w0); a >= -(W0 >= 0 ? W0 : w0); --a) {
                 const cpx<T> kv = kt[a + w0];
 #pragma unroll
                 for (int q = 0; q < Q; ++q) acc[q] = acc[q] - cmul(kv, win[q]);
@@ -258,7 +262,15 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
         const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
         const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
         const int nbkg_off = p->n - p->nb;
-        auto kern = p->gen0 ? k_sub_cols<T, false> : k_sub_cols<T, true>;
+        auto kern = p->gen0 ? k_sub_cols<T, false, -1> : k_sub_cols<T, true, -1>;
+        switch (p->cfg.w0) {  // the half-widths of the workloads, unrolled
+            case 4: kern = p->gen0 ? k_sub_cols<T, false, 4> : k_sub_cols<T, true, 4>; break;
+            case 5: kern = p->gen0 ? k_sub_cols<T, false, 5> : k_sub_cols<T, true, 5>; break;
+            case 6: kern = p->gen0 ? k_sub_cols<T, false, 6> : k_sub_cols<T, true, 6>; break;
+            case 7: kern = p->gen0 ? k_sub_cols<T, false, 7> : k_sub_cols<T, true, 7>; break;
+            case 8: kern = p->gen0 ? k_sub_cols<T, false, 8> : k_sub_cols<T, true, 8>; break;
+            default: break;
+        }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
                                         (const cpx<T> *)p->F, (const cpx<T> *)p->kap, (const cpx<T> *)p->yhat, x,
