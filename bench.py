@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 single-pair comparison")
+    ap.add_argument("--mode", default="full", choices=["full", "pair"],
+                    help="pair: only warmup + steps pairs through sfft_run_pair (for profiler captures)")
     ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
     ap.add_argument("--batch", type=int, default=4, help="systems solved per launch in the serving path")
     return ap.parse_args()
@@ -223,26 +225,43 @@ def survey_alg_bytes(spec):
 
 
 def load_traffic(kernel):
-    """DRAM bytes per launch from a committed ncu capture, if its source hash matches."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch of `kernel` from its committed ncu
+    summary profiles/<kernel>_pair4096_mixed.md, used only while the hash of
+    the kernel's source recorded there matches the source as it is now."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel}_pair4096_mixed.md")
     try:
         with open(path) as fh:
-            d = json.load(fh)
-    except (OSError, ValueError):
+            text = fh.read()
+    except OSError:
         return None
-    ent = d.get(kernel)
-    if not ent:
+    m_hash = re.search(r"kernel source hash: `([0-9a-f]+)`", text)
+    m_rd = re.search(r"\| DRAM bytes read \| ([0-9.]+) Mbyte", text)
+    m_wr = re.search(r"\| DRAM bytes written \| ([0-9.]+) Mbyte", text)
+    if not (m_hash and m_rd and m_wr) or m_hash.group(1) != kernel_source_hash(kernel):
         return None
-    if ent.get("source_sha") != source_hash():
-        return None
-    return ent.get("bytes_per_launch")
+    return int(round((float(m_rd.group(1)) + float(m_wr.group(1))) * 1e6))
 
 
-def source_hash():
-    h = hashlib.sha256()
+def kernel_source_hash(kernel):
+    """Hash of a kernel's own text in csrc (from its template line to the
+    closing brace at column 0) plus the headers it includes."""
     csrc = os.path.join(ROOT, "paper_2109_09334_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if not name.endswith(".cu"):
+            continue
+        with open(os.path.join(csrc, name)) as fh:
+            text = fh.read()
+        i = text.find(f" {kernel}(")
+        if i < 0:
+            continue
+        start = text.rfind("\ntemplate", 0, i)
+        start = start + 1 if start >= 0 else text.rfind("\n", 0, i) + 1
+        end = text.find("\n}\n", i)
+        h.update(text[start:end].encode())
+    for name in ("common.cuh", "fft.cuh", "fft16.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -414,13 +433,13 @@ def run_ours(args):
         if t_hbm >= t_alu:
             ach = sb[top] / t_s / 1e9
             result["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                  "frac": ach / peak, "traffic": load_traffic(kern), "kernel": kern,
+                                  "frac": ach / peak, "traffic": load_traffic(kern) if kern.startswith("k_") and " " not in kern else None, "kernel": kern,
                                   "stage": top, "alg_bytes_per_launch": sb[top],
                                   "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"}
         else:
             ach = sf[top] / t_s / 1e12
             result["roofline"] = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                                  "frac": ach / alu_peak, "traffic": load_traffic(kern), "kernel": kern,
+                                  "frac": ach / alu_peak, "traffic": load_traffic(kern) if kern.startswith("k_") and " " not in kern else None, "kernel": kern,
                                   "stage": top, "alg_flops_per_launch": sf[top], "alg_bytes_per_launch": sb[top],
                                   "peak_source": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {clk:.0f} MHz"}
         ba = survey_alg_bytes(spec)
@@ -726,9 +745,31 @@ def run_stream(args):
         print(json.dumps(out), flush=True)
 
 
+def run_pairs_only(args):
+    """warmup + steps pairs of the workload through sfft_run_pair on one plan
+    and one stream, nothing else (the command the ncu captures profile)."""
+    import torch
+    import synth
+    from paper_2109_09334_gb300 import SfftPlan, info_from_bytes
+    spec = synth.SPECS[args.workload]
+    f = spec.fit
+    R, S = synth.make_pair(spec, seed=100)
+    plan = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
+                    precision=args.precision)
+    Rt, St = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    for _ in range(args.warmup + args.steps):
+        D, x, info, _, _ = plan.run_pair(Rt, St)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "pair", "workload": spec.name, "pairs": args.warmup + args.steps,
+                      "solve": info_from_bytes(info.cpu().numpy())}), flush=True)
+    plan.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.mode == "pair":
+        run_pairs_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "sectors64":
         run_sectors(args)
