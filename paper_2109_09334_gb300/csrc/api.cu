@@ -90,11 +90,14 @@ __global__ void k_poly_dft(int n, int nout, int pmax, const cpx<double> *tw, int
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int p = e / nout, l = e % nout;
         double re = 0.0, im = 0.0;
+        int q = 0;  // l x mod n, stepped by l
         for (int x = 0; x < n; ++x) {
             const double v = ipow(coord<double>(x, n), p);
-            const cpx<double> w = tw[(int)(((long long)l * x) % n)];
+            const cpx<double> w = tw[q];
             re += v * w.re;
             im += v * w.im;
+            q += l;
+            if (q >= n) q -= n;
         }
         int o = l;
         if (permute) o = (l % nbk) * na + l / nbk;
