@@ -12,6 +12,8 @@ Three independent tiers:
 * :mod:`oracle.bruteforce`: the least-squares definition written out -- an
   explicit design matrix ``C`` (one column per unknown, Eq. 11-12), ``M = C^T C``,
   ``rhs = C^T S`` and a library least-squares solve.  Tiny images only.
+* :mod:`oracle.decorr`: the noise decorrelation filter of App. C (Eq. 24) for one
+  pair, with numpy's FFT as the DFT primitive.
 * :mod:`oracle.fourier`: Eq. 19-24 evaluated literally as frequency sums of
   spectrum products with the basis spectra of Eq. 14 (numpy FFT as the DFT
   primitive).  Tiny images only.

@@ -1,0 +1,60 @@
+"""Noise decorrelation of the difference image (App. C, Eq. 21-24), FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package header): imported by the tests.
+
+For one pair with no co-addition (M = N = 1 and G = H = delta in Eq. 21),
+Eq. 23-24 give the real decorrelation filter
+
+    Q0(p) = sqrt( sigma_D^2 / (sigma_S^2 + sigma_R^2 |K(p)|^2) ),
+
+where K(p) is the DFT of the matching kernel.  App. C ignores the spatial
+variation of the kernel, so K is the kernel of Eq. 6 evaluated at one
+normalised position (xt0, yt0).  The filter is normalised to unit kernel
+sum (the flux-preserving choice App. C names), i.e. Q(0) = 1, which sets
+sigma_D^2 = sigma_S^2 + sigma_R^2 K(0)^2.  The decorrelated image is the
+circular convolution D_dc = D (*) Q.  numpy's FFT serves as the DFT primitive.
+"""
+import numpy as np
+
+from . import bruteforce
+
+
+def kernel_image(x, w0, w1, dk, db, const_phot_ratio, xt0, yt0):
+    """Matching kernel at (xt0, yt0) as an image k[alpha + w0, beta + w1].
+
+    With the delta basis of Eq. 3-4, K_ab = delta(a, b) - delta(0, 0) for
+    (a, b) != 0 and K_00 = delta(0, 0), so a coefficient of offset (a, b) != 0
+    adds at the offset and subtracts at the centre; Eq. 6 weights the
+    coefficients of term (i, j) by xt0^i yt0^j.
+    """
+    k = np.zeros((2 * w0 + 1, 2 * w1 + 1))
+    for u, unk in enumerate(bruteforce.unknown_list(w0, w1, dk, db, const_phot_ratio)):
+        if unk[0] != "k":
+            continue
+        (i, j), (a, b) = unk[1], unk[2]
+        c = x[u] * xt0 ** i * yt0 ** j
+        if (a, b) == (0, 0):
+            k[w0, w1] += c
+        else:
+            k[a + w0, b + w1] += c
+            k[w0, w1] -= c
+    return k
+
+
+def filter_spectrum(k, n0, n1, sigma_ref, sigma_sci):
+    """Q(l, m) of Eq. 24, normalised to Q(0, 0) = 1, for the kernel image k."""
+    w0, w1 = k.shape[0] // 2, k.shape[1] // 2
+    full = np.zeros((n0, n1))
+    for a in range(-w0, w0 + 1):
+        for b in range(-w1, w1 + 1):
+            full[a % n0, b % n1] += k[a + w0, b + w1]
+    kh = np.fft.fft2(full)
+    sd2 = sigma_sci ** 2 + sigma_ref ** 2 * abs(kh[0, 0]) ** 2
+    return np.sqrt(sd2 / (sigma_sci ** 2 + sigma_ref ** 2 * np.abs(kh) ** 2))
+
+
+def decorrelate(D, k, sigma_ref, sigma_sci):
+    """D (*) Q, circular, with Q from filter_spectrum."""
+    D = np.asarray(D, np.float64)
+    q = filter_spectrum(k, D.shape[0], D.shape[1], sigma_ref, sigma_sci)
+    return np.real(np.fft.ifft2(np.fft.fft2(D) * q))

@@ -1,0 +1,73 @@
+"""Pins of the decorrelation oracle (App. C, Eq. 21-24) against what the
+mathematics fixes, on the CPU."""
+import numpy as np
+import pytest
+
+from oracle import bruteforce, decorr
+from synth import random_field
+
+
+def test_kernel_image_reproduces_the_model_convolution():
+    """For D_K = 0 the kernel part of the model, sum_u x_u C_u (the design
+    matrix of Eq. 12), is the circular convolution of R with the kernel image."""
+    rng = np.random.default_rng(3)
+    n0, n1, w0, w1 = 12, 10, 2, 1
+    R = random_field(n0, n1, 5)
+    for cpr in (True, False):
+        unk = bruteforce.unknown_list(w0, w1, 0, 1, cpr)
+        x = rng.standard_normal(len(unk))
+        C = bruteforce.design_matrix(R, w0, w1, 0, 1, cpr)
+        kcols = [u for u, e in enumerate(unk) if e[0] == "k"]
+        model = (C[:, kcols] @ x[kcols]).reshape(n0, n1)
+        k = decorr.kernel_image(x, w0, w1, 0, 1, cpr, 0.3, -0.7)
+        conv = np.zeros((n0, n1))
+        for a in range(-w0, w0 + 1):
+            for b in range(-w1, w1 + 1):
+                conv += k[a + w0, b + w1] * np.roll(np.roll(R, a, axis=0), b, axis=1)
+        assert np.allclose(conv, model, rtol=0, atol=1e-10 * np.abs(model).max())
+
+
+def test_delta_kernel_leaves_the_image_unchanged():
+    k = np.zeros((5, 3))
+    k[2, 1] = 1.3  # a scaled delta: |K^| is constant, so Q = 1
+    D = random_field(16, 12, 9)
+    assert np.allclose(decorr.decorrelate(D, k, 4.0, 6.0), D, rtol=0, atol=1e-10 * np.abs(D).max())
+
+
+def test_mean_is_preserved():
+    rng = np.random.default_rng(1)
+    k = rng.standard_normal((5, 5)) * 0.1
+    k[2, 2] += 1.0
+    D = random_field(20, 24, 2)
+    assert np.isclose(decorr.decorrelate(D, k, 5.0, 3.0).mean(), D.mean(), rtol=1e-12)
+
+
+def test_whitens_the_difference_noise():
+    """White noise in R and S (sigma_R, sigma_S) through D = S - K (*) R has
+    the power spectrum sigma_S^2 + sigma_R^2 |K^|^2; after decorrelation it is
+    flat at sigma_S^2 + sigma_R^2 K^(0)^2.  Averaged over many realisations."""
+    rng = np.random.default_rng(7)
+    n0, n1, sr, ss = 24, 20, 3.0, 2.0
+    k = np.zeros((5, 5))
+    k[2, 2], k[1, 2], k[3, 2], k[2, 1], k[2, 3] = 0.6, 0.15, 0.1, 0.1, 0.05  # a blur
+    full = np.zeros((n0, n1))
+    for a in range(-2, 3):
+        for b in range(-2, 3):
+            full[a % n0, b % n1] = k[a + 2, b + 2]
+    kh = np.fft.fft2(full)
+    raw = np.zeros((n0, n1))
+    dec = np.zeros((n0, n1))
+    trials = 400
+    for _ in range(trials):
+        R = rng.normal(0, sr, (n0, n1))
+        S = rng.normal(0, ss, (n0, n1))
+        D = S - np.real(np.fft.ifft2(np.fft.fft2(R) * kh))
+        raw += np.abs(np.fft.fft2(D)) ** 2
+        dec += np.abs(np.fft.fft2(decorr.decorrelate(D, k, sr, ss))) ** 2
+    raw /= trials * n0 * n1
+    dec /= trials * n0 * n1
+    flat = ss ** 2 + sr ** 2 * kh[0, 0].real ** 2
+    assert raw.max() / raw.min() > 2.0  # the difference's noise is correlated
+    # each averaged bin has a relative error of about 1/sqrt(trials) = 5 %
+    assert np.abs(dec / flat - 1).max() < 0.3
+    assert abs(dec.mean() / flat - 1) < 0.02
