@@ -177,6 +177,24 @@ int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
                   void *d_diff, sfft_stream_t stream);
 
 /*
+ * Noise decorrelation of a difference image (App. C, Eq. 21-24) for one
+ * pair: D_dc = D (*) Q with the real filter of Eq. 24,
+ *     Q^(p) = sqrt(sigma_D^2 / (sigma_sci^2 + sigma_ref^2 |K^(p)|^2)),
+ * normalised to unit kernel sum (sigma_D^2 = sigma_sci^2 + sigma_ref^2 K^(0)^2,
+ * the flux-preserving choice), as a circular convolution.  App. C ignores the
+ * spatial variation of the kernel: K is the matching kernel of Eq. 6 at the
+ * normalised position (xt0, yt0) in [-1, 1]^2, built from the coefficients
+ * d_x of sfft_solve (the delta basis of Eq. 3-4).
+ *   sigma_ref >= 0, sigma_sci > 0 : noise of R and S (their ratio matters).
+ *   d_diff : n0*n1 image of cfg.dtype (read);  d_out : n0*n1 image of
+ *            cfg.dtype (written; may equal d_diff).
+ * Uses the plan's workspace: it overwrites the row transforms of the last
+ * build, so call it after sfft_subtract / sfft_run_pair of that pair.
+ */
+int sfft_decorrelate(sfft_plan_t plan, const double *d_x, double xt0, double yt0, double sigma_ref,
+                     double sigma_sci, const void *d_diff, void *d_out, sfft_stream_t stream);
+
+/*
  * One whole pair on device buffers: build, solve and subtract.  d_M, d_rhs,
  * d_x and d_info may be NULL, in which case plan-owned buffers are used.
  */

@@ -110,6 +110,14 @@ class SfftPlan:
         sfft_subtract(self.handle, ref, sci, x, D, self.stream)
         return D
 
+    def decorrelate(self, x, diff, sigma_ref, sigma_sci, xt0=0.0, yt0=0.0, out=None):
+        """Noise decorrelation of a difference image (App. C); see sfft_decorrelate."""
+        torch = _torch()
+        self._check_img(diff)
+        out = out if out is not None else torch.empty_like(diff)
+        binding.sfft_decorrelate(self.handle, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, self.stream)
+        return out
+
     def run_pair(self, ref, sci, mask=None, out=None, keep_system=False):
         torch = _torch()
         self._check_img(ref), self._check_img(sci)

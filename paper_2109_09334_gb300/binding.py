@@ -83,6 +83,8 @@ def library():
         lib.sfft_build_system.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_solve_static.argtypes = [vp, vp, i32, i32, vp, vp, vp]
+        dbl = ctypes.c_double
+        lib.sfft_decorrelate.argtypes = [vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]
         lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -191,6 +193,11 @@ def sfft_solve_static(d_M, d_rhs, n, precision, d_x, d_info=None, stream=None):
     if rc == SFFT_ERR_UNSUPPORTED and int(n) > SFFT_SOLVE_STATIC_MAX_N:
         raise SfftError(rc, f"sfft_solve_static: n={int(n)} exceeds SFFT_SOLVE_STATIC_MAX_N={SFFT_SOLVE_STATIC_MAX_N}")
     _check(rc, "sfft_solve_static")
+
+
+def sfft_decorrelate(plan, d_x, xt0, yt0, sigma_ref, sigma_sci, d_diff, d_out, stream=None):
+    _check(library().sfft_decorrelate(plan, _p(d_x), float(xt0), float(yt0), float(sigma_ref), float(sigma_sci),
+                                      _p(d_diff), _p(d_out), _s(stream)), "sfft_decorrelate")
 
 
 def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):

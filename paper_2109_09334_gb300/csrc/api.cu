@@ -128,7 +128,7 @@ static int unknowns(const sfft_config *c) {
 }
 
 void plan_free(Plan *p) {
-    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->chirp1, p->bfilt1, p->twpm1, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
+    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->chirp1, p->bfilt1, p->twpm1, p->chirp0, p->bfilt0, p->twpm0, p->kimg, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
                     p->lag, p->A, p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own,
                     p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
     for (void *b : bufs)
@@ -162,6 +162,7 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     p->gen0 = !is_pow2(cfg->n0);
     p->gen1 = !is_pow2(cfg->n1);
     p->m1 = p->gen1 ? bluestein_len(cfg->n1) : cfg->n1;
+    p->m0 = p->gen0 ? bluestein_len(cfg->n0) : cfg->n0;
     p->na = p->gen0 ? cfg->n0 : (cfg->n0 < kMaxNA ? cfg->n0 : kMaxNA);
     p->nbk = cfg->n0 / p->na;
     p->nimg = p->nk + 1;
@@ -212,6 +213,12 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->F, (size_t)(cfg->dk + 2) * half * csz);
     // the column spectra (power-of-two n0); the subtraction reuses U for D~
     SFFT_ALLOC(p->U, (size_t)(p->gen0 ? 1 : p->nimg) * half * csz);
+    SFFT_ALLOC(p->kimg, (size_t)p->L0 * p->L1 * sizeof(double));
+    if (p->gen0) {
+        SFFT_ALLOC(p->chirp0, (size_t)p->n0 * csz);
+        SFFT_ALLOC(p->bfilt0, (size_t)p->m0 * csz);
+        SFFT_ALLOC(p->twpm0, (size_t)p->m0 * csz);
+    }
     if (p->gen1) {
         SFFT_ALLOC(p->chirp1, (size_t)p->n1 * csz);
         SFFT_ALLOC(p->bfilt1, (size_t)p->m1 * csz);
@@ -285,10 +292,15 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<float> *)p->xhat);
         k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<float> *)p->yhat);
     }
-    if (p->gen1) {
+    for (int ax = 0; ax < 2; ++ax) {  // Bluestein tables of the axes that are not powers of two
+        const bool gen = ax == 0 ? p->gen0 : p->gen1;
+        if (!gen) continue;
+        const int nn = ax == 0 ? p->n0 : p->n1, mm = ax == 0 ? p->m0 : p->m1;
+        void *chirp = ax == 0 ? p->chirp0 : p->chirp1, *bfilt = ax == 0 ? p->bfilt0 : p->bfilt1;
+        void *twpm = ax == 0 ? p->twpm0 : p->twpm1;
         cpx<double> *tm64 = nullptr, *c64 = nullptr;
-        if (cudaMalloc((void **)&tm64, p->m1 * sizeof(cpx<double>)) != cudaSuccess ||
-            cudaMalloc((void **)&c64, p->n1 * sizeof(cpx<double>)) != cudaSuccess) {
+        if (cudaMalloc((void **)&tm64, mm * sizeof(cpx<double>)) != cudaSuccess ||
+            cudaMalloc((void **)&c64, nn * sizeof(cpx<double>)) != cudaSuccess) {
             cudaGetLastError();
             if (tm64) cudaFree(tm64);
             cudaFree(t64a);
@@ -296,16 +308,16 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
             plan_free(p);
             return SFFT_ERR_OOM;
         }
-        k_twiddle64<<<(p->m1 + 255) / 256, 256, 0, s>>>(p->m1, tm64);
-        k_chirp64<<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64);
+        k_twiddle64<<<(mm + 255) / 256, 256, 0, s>>>(mm, tm64);
+        k_chirp64<<<(nn + 255) / 256, 256, 0, s>>>(nn, c64);
         if (p->fp64) {
-            k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64, (cpx<double> *)p->chirp1);
-            k_bfilt<double><<<(p->m1 + 127) / 128, 128, 0, s>>>(p->n1, p->m1, tm64, c64, (cpx<double> *)p->bfilt1);
-            pass_tables<double>(p->m1, tm64, (cpx<double> *)p->twpm1, s);
+            k_round<double><<<(nn + 255) / 256, 256, 0, s>>>(nn, c64, (cpx<double> *)chirp);
+            k_bfilt<double><<<(mm + 127) / 128, 128, 0, s>>>(nn, mm, tm64, c64, (cpx<double> *)bfilt);
+            pass_tables<double>(mm, tm64, (cpx<double> *)twpm, s);
         } else {
-            k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, c64, (cpx<float> *)p->chirp1);
-            k_bfilt<float><<<(p->m1 + 127) / 128, 128, 0, s>>>(p->n1, p->m1, tm64, c64, (cpx<float> *)p->bfilt1);
-            pass_tables<float>(p->m1, tm64, (cpx<float> *)p->twpm1, s);
+            k_round<float><<<(nn + 255) / 256, 256, 0, s>>>(nn, c64, (cpx<float> *)chirp);
+            k_bfilt<float><<<(mm + 127) / 128, 128, 0, s>>>(nn, mm, tm64, c64, (cpx<float> *)bfilt);
+            pass_tables<float>(mm, tm64, (cpx<float> *)twpm, s);
         }
         cudaStreamSynchronize(s);
         cudaFree(tm64);
@@ -462,6 +474,16 @@ int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
     cudaError_t e = row_transform(p, d_ref, d_sci, nullptr, false, s);
     if (e == cudaSuccess) e = subtract_from_rows(p, d_x, d_diff, s);
     return status_of(e);
+}
+
+int sfft_decorrelate(sfft_plan_t plan, const double *d_x, double xt0, double yt0, double sigma_ref,
+                     double sigma_sci, const void *d_diff, void *d_out, sfft_stream_t stream) {
+    if (!plan || !d_x || !d_diff || !d_out) return SFFT_ERR_INVALID;
+    if (!(sigma_sci > 0.0) || !(sigma_ref >= 0.0)) return SFFT_ERR_INVALID;
+    if (!(xt0 >= -1.0 && xt0 <= 1.0) || !(yt0 >= -1.0 && yt0 <= 1.0)) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    p->last_stream = (cudaStream_t)stream;
+    return status_of(decorrelate(p, d_x, xt0, yt0, sigma_ref, sigma_sci, d_diff, d_out, (cudaStream_t)stream));
 }
 
 int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask, double *d_M,

@@ -46,8 +46,10 @@ struct Plan {
     // Sizes that are not powers of two.  gen1: the row transforms are
     // Bluestein DFTs of length n1 through FFTs of length m1; gen0: the lag
     // sums along x are direct circular correlations (k_xcorr), no column FFT.
-    int gen0, gen1, m1;
+    int gen0, gen1, m0, m1;
     void *chirp1, *bfilt1, *twpm1;  // Bluestein tables for n1 (compute type)
+    void *chirp0, *bfilt0, *twpm0;  // Bluestein tables for n0 (noise decorrelation only)
+    double *kimg;                   // L0 x L1 kernel image (noise decorrelation)
     void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
     void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
     void *F;               // [(dk+2)][m][x] row transforms (compute type)
@@ -116,6 +118,8 @@ struct SolveBuffers {
 };
 cudaError_t solve_on_buffers(const SolveBuffers &b, const double *M, const double *rhs, double *x,
                              sfft_solve_info *info, cudaStream_t s);
+cudaError_t decorrelate(Plan *p, const double *x, double xt0, double yt0, double sigma_ref, double sigma_sci,
+                        const void *diff, void *out, cudaStream_t s);
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s);
 cudaError_t plan_tables(Plan *p, cudaStream_t s);
 

@@ -246,37 +246,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_inv_blu(in
     }
 }
 
+// D from its row transforms in p->U (layout [m][x]): the inverse real FFT of
+// every row, two rows per complex transform.
 template <typename T>
-static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
-    cudaError_t err;
-    double *ksum = p->xw + p->n + kSolveTail;  // after the solve's statistics and partial sums
-    p->launches += 4;
-    k_kernel_sums<<<p->nk, 256, 0, s>>>(p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x, ksum);
-    const size_t tot = (size_t)p->nk * p->L0 * p->h1c;
-    int blocks = (int)((tot + 255) / 256);
-    if (blocks > 8192) blocks = 8192;
-    k_kernel_table<T><<<blocks, 256, 0, s>>>(p->n1, p->nk, p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x,
-                                             ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
-    if ((err = cudaGetLastError())) return err;
-    {
-        const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
-        const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
-        const int nbkg_off = p->n - p->nb;
-        auto kern = p->gen0 ? k_sub_cols<T, false, -1> : k_sub_cols<T, true, -1>;
-        switch (p->cfg.w0) {  // the half-widths of the workloads, unrolled
-            case 4: kern = p->gen0 ? k_sub_cols<T, false, 4> : k_sub_cols<T, true, 4>; break;
-            case 5: kern = p->gen0 ? k_sub_cols<T, false, 5> : k_sub_cols<T, true, 5>; break;
-            case 6: kern = p->gen0 ? k_sub_cols<T, false, 6> : k_sub_cols<T, true, 6>; break;
-            case 7: kern = p->gen0 ? k_sub_cols<T, false, 7> : k_sub_cols<T, true, 7>; break;
-            case 8: kern = p->gen0 ? k_sub_cols<T, false, 8> : k_sub_cols<T, true, 8>; break;
-            default: break;
-        }
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
-                                        (const cpx<T> *)p->F, (const cpx<T> *)p->kap, (const cpx<T> *)p->yhat, x,
-                                        (cpx<T> *)p->U);
-        if ((err = cudaGetLastError())) return err;
-    }
+static cudaError_t launch_rows_inv(Plan *p, void *diff, cudaStream_t s) {
     if (p->gen1) {
         const int G = p->m1 / 16;
         int NG = (sizeof(T) == 4 ? 1024 : 512) / G;
@@ -324,6 +297,233 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
         }
     }
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
+    cudaError_t err;
+    double *ksum = p->xw + p->n + kSolveTail;  // after the solve's statistics and partial sums
+    p->launches += 4;
+    k_kernel_sums<<<p->nk, 256, 0, s>>>(p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x, ksum);
+    const size_t tot = (size_t)p->nk * p->L0 * p->h1c;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    k_kernel_table<T><<<blocks, 256, 0, s>>>(p->n1, p->nk, p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x,
+                                             ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
+    if ((err = cudaGetLastError())) return err;
+    {
+        const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
+        const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
+        const int nbkg_off = p->n - p->nb;
+        auto kern = p->gen0 ? k_sub_cols<T, false, -1> : k_sub_cols<T, true, -1>;
+        switch (p->cfg.w0) {  // the half-widths of the workloads, unrolled
+            case 4: kern = p->gen0 ? k_sub_cols<T, false, 4> : k_sub_cols<T, true, 4>; break;
+            case 5: kern = p->gen0 ? k_sub_cols<T, false, 5> : k_sub_cols<T, true, 5>; break;
+            case 6: kern = p->gen0 ? k_sub_cols<T, false, 6> : k_sub_cols<T, true, 6>; break;
+            case 7: kern = p->gen0 ? k_sub_cols<T, false, 7> : k_sub_cols<T, true, 7>; break;
+            case 8: kern = p->gen0 ? k_sub_cols<T, false, 8> : k_sub_cols<T, true, 8>; break;
+            default: break;
+        }
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
+                                        (const cpx<T> *)p->F, (const cpx<T> *)p->kap, (const cpx<T> *)p->yhat, x,
+                                        (cpx<T> *)p->U);
+        if ((err = cudaGetLastError())) return err;
+    }
+    if ((err = launch_rows_inv<T>(p, diff, s))) return err;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Noise decorrelation (App. C, Eq. 21-24) for one pair.  The spatial
+// variation of the kernel is ignored there, so the matching kernel of Eq. 6
+// is taken at one normalised position (xt0, yt0):
+//     K(a, b) = sum_t xt0^i yt0^j c_t(a, b)            (kernel image, FP64)
+// and the real filter of Eq. 24, normalised to unit kernel sum,
+//     Q(l, m) = sqrt((s_S^2 + s_R^2 K^(0,0)^2) / (s_S^2 + s_R^2 |K^(l, m)|^2)),
+// multiplies the 2-D transform of D:  D_dc = D (*) Q.  K^ is separable in the
+// same way as the subtraction: kappa(a, m) = sum_b K(a, b) exp(-2 pi i m b / N1)
+// and K^(l, m) = sum_a kappa(a, m) exp(-2 pi i l a / N0).
+
+__global__ void k_kernel_image(int w0, int w1, int dk, int cpr, double xt0, double yt0,
+                               const double *__restrict__ x, double *__restrict__ kimg) {
+    const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
+    const int nk = n_terms(dk);
+    for (int e = threadIdx.x; e < L; e += blockDim.x) {
+        const int a = e / L1 - w0, b = e % L1 - w1;
+        double v = 0.0;
+        for (int t = 0; t < nk; ++t) {
+            int i, j;
+            term_ij(t, &i, &j);
+            const double wt = ipow(xt0, i) * ipow(yt0, j);
+            if (a != 0 || b != 0) {
+                v += wt * x[unknown_index(t, a, b, w0, w1, cpr)];
+            } else {
+                const int u0 = unknown_index(t, 0, 0, w0, w1, cpr);
+                double c = u0 >= 0 ? x[u0] : 0.0;
+                for (int o = 0; o < L; ++o) {
+                    const int aa = o / L1 - w0, bb = o % L1 - w1;
+                    if (aa != 0 || bb != 0) c -= x[unknown_index(t, aa, bb, w0, w1, cpr)];
+                }
+                v += wt * c;
+            }
+        }
+        kimg[e] = v;
+    }
+}
+
+// kap[a + w0][m] = sum_b K(a, b) exp(-2 pi i m b / N1)
+template <typename T>
+__global__ void k_decorr_kappa(int n1, int w0, int w1, const double *__restrict__ kimg,
+                               const cpx<T> *__restrict__ tw1, cpx<T> *__restrict__ kap) {
+    const int h1c = n1 / 2 + 1, L0 = 2 * w0 + 1, L1 = 2 * w1 + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L0 * h1c; e += gridDim.x * blockDim.x) {
+        const int a = e / h1c, m = e - a * h1c;
+        cpx<T> v = mk((T)0, (T)0);
+        for (int bi = 0; bi < L1; ++bi) v = v + scale(tw1[imod(m * (bi - w1), n1)], (T)kimg[a * L1 + bi]);
+        kap[e] = v;
+    }
+}
+
+// Forward real transform of the rows of D, two rows per complex transform,
+// written as Dt[m][x] (m < N1/2 + 1): pow2 n1 by the radix-16 FFT, other n1
+// by Bluestein.
+template <typename T, typename I, bool BLU>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_decorr_rows(int n0, int n1, int mlen, int NG,
+                                                      const I *__restrict__ D, const cpx<T> *__restrict__ twg,
+                                                      const cpx<T> *__restrict__ chirp,
+                                                      const cpx<T> *__restrict__ bfilt, cpx<T> *__restrict__ Dt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = mlen / 16;
+    const int np = padded_len(mlen);
+    const int ntw = BLU ? 0 : pass_table_len(n1);
+    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // pass table (pow2)
+    cpx<T> *Z = tw + ntw;                                // NG * np
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int grp = tid / G, gt = tid - grp * G;
+    const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
+    for (int q = tid; q < ntw; q += nthr) tw[q] = twg[q];
+    cpx<T> *zr = Z + (size_t)grp * np;
+    for (int y = gt; y < n1; y += G) {
+        const T a = xa < n0 ? (T)D[(size_t)xa * n1 + y] : (T)0;
+        const T b = xb < n0 ? (T)D[(size_t)xb * n1 + y] : (T)0;
+        zr[pad16(y)] = mk(a, b);
+    }
+    __syncthreads();
+    if (BLU) bluestein(zr, n1, mlen, -1, chirp, bfilt, twg, gt, G);
+    else group_fft(zr, n1, -1, tw, gt, G);
+    const int h1c = n1 / 2 + 1;
+    for (int m = gt; m < h1c; m += G) {
+        const cpx<T> z = zr[pad16(m)];
+        const cpx<T> zc = conj(zr[pad16(m == 0 ? 0 : n1 - m)]);
+        if (xa < n0) Dt[(size_t)m * n0 + xa] = scale(z + zc, (T)0.5);
+        if (xb < n0) Dt[(size_t)m * n0 + xb] = mul_i(scale(z - zc, (T)0.5), -1);
+    }
+}
+
+// Per frequency column m: transform along x, multiply by Q(l, m), transform
+// back (scaled by 1/N0), in place in Dt[m][x].
+template <typename T, bool BLU>
+__global__ void __launch_bounds__(512) k_decorr_cols(int n0, int n1, int mlen, int w0,
+                                                      double sigma_ref, double sigma_sci,
+                                                      const cpx<T> *__restrict__ kap, const cpx<T> *__restrict__ tw0,
+                                                      const cpx<T> *__restrict__ twg, const cpx<T> *__restrict__ chirp,
+                                                      const cpx<T> *__restrict__ bfilt, cpx<T> *__restrict__ Dt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = mlen / 16;
+    const int ntw = BLU ? 0 : pass_table_len(n0);
+    const int L0 = 2 * w0 + 1;
+    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // pass table (pow2)
+    cpx<T> *kp = tw + ntw;                               // L0: kappa(a, m)
+    cpx<T> *zr = kp + L0;                                // padded mlen
+    const int tid = threadIdx.x, m = blockIdx.x;
+    const int h1c = n1 / 2 + 1;
+    for (int q = tid; q < ntw; q += G) tw[q] = twg[q];
+    for (int a = tid; a < L0; a += G) kp[a] = kap[(size_t)a * h1c + m];
+    double k00 = 0.0;  // K^(0, 0): the kernel sum
+    for (int a = 0; a < L0; ++a) k00 += (double)kap[(size_t)a * h1c].re;
+    cpx<T> *col = Dt + (size_t)m * n0;
+    for (int x = tid; x < n0; x += G) zr[pad16(x)] = col[x];
+    __syncthreads();
+    if (BLU) bluestein(zr, n0, mlen, -1, chirp, bfilt, twg, tid, G);
+    else group_fft(zr, n0, -1, tw, tid, G);
+    const double ss2 = sigma_sci * sigma_sci, sr2 = sigma_ref * sigma_ref;
+    const T num = (T)(ss2 + sr2 * k00 * k00);
+    for (int l = tid; l < n0; l += G) {
+        cpx<T> kh = mk((T)0, (T)0);
+        for (int a = 0; a < L0; ++a) kh = kh + cmul(kp[a], tw0[imod(l * (a - w0), n0)]);
+        const T q = sqrt(num / ((T)ss2 + (T)sr2 * (kh.re * kh.re + kh.im * kh.im)));
+        zr[pad16(l)] = scale(zr[pad16(l)], q);
+    }
+    __syncthreads();
+    if (BLU) bluestein(zr, n0, mlen, 1, chirp, bfilt, twg, tid, G);
+    else group_fft(zr, n0, 1, tw, tid, G);
+    const T inv = (T)1 / (T)n0;
+    for (int x = tid; x < n0; x += G) col[x] = scale(zr[pad16(x)], inv);
+}
+
+template <typename T>
+static cudaError_t decorr_t(Plan *p, const double *x, double xt0, double yt0, double sr, double ss,
+                            const void *diff, void *out, cudaStream_t s) {
+    cudaError_t err;
+    const int w0 = p->cfg.w0, w1 = p->cfg.w1;
+    k_kernel_image<<<1, 256, 0, s>>>(w0, w1, p->cfg.dk, p->cfg.const_phot_ratio, xt0, yt0, x, p->kimg);
+    const int tot = p->L0 * p->h1c;
+    k_decorr_kappa<T><<<(tot + 255) / 256, 256, 0, s>>>(p->n1, w0, w1, p->kimg, (const cpx<T> *)p->tw1,
+                                                        (cpx<T> *)p->kap);
+    p->launches += 2;
+    if ((err = cudaGetLastError())) return err;
+    {  // rows
+        const int G = p->m1 / 16;
+        int NG = (sizeof(T) == 4 ? 1024 : 512) / G;
+        if (NG < 1) NG = 1;
+        if (NG > 4) NG = 4;
+        if (NG > (p->n0 + 1) / 2) NG = (p->n0 + 1) / 2;
+        const int ntw = p->gen1 ? 0 : pass_table_len(p->n1);
+        auto smem_of = [&](int ng) { return ((size_t)ntw + (size_t)ng * padded_len(p->m1)) * sizeof(cpx<T>); };
+        while (NG > 1 && smem_of(NG) > 200 * 1024) NG /= 2;
+        const size_t smem = smem_of(NG);
+        const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
+        const cpx<T> *twg = (const cpx<T> *)(p->gen1 ? p->twpm1 : p->twp1);
+        const cpx<T> *ch = (const cpx<T> *)p->chirp1, *bf = (const cpx<T> *)p->bfilt1;
+        cpx<T> *Dt = (cpx<T> *)p->U;
+#define SFFT_DROWS(I, BLU)                                                                                    \
+    do {                                                                                                      \
+        cudaFuncSetAttribute(k_decorr_rows<T, I, BLU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_decorr_rows<T, I, BLU><<<blocks, NG * G, smem, s>>>(p->n0, p->n1, p->m1, NG, (const I *)diff, twg, ch, \
+                                                              bf, Dt);                                        \
+    } while (0)
+        if (p->cfg.dtype == SFFT_F64) {
+            if (p->gen1) SFFT_DROWS(double, true);
+            else SFFT_DROWS(double, false);
+        } else {
+            if (p->gen1) SFFT_DROWS(float, true);
+            else SFFT_DROWS(float, false);
+        }
+#undef SFFT_DROWS
+        p->launches++;
+        if ((err = cudaGetLastError())) return err;
+    }
+    {  // columns
+        const int G = p->m0 / 16;
+        const int ntw = p->gen0 ? 0 : pass_table_len(p->n0);
+        const size_t smem = ((size_t)ntw + p->L0 + padded_len(p->m0)) * sizeof(cpx<T>);
+        auto kern = p->gen0 ? k_decorr_cols<T, true> : k_decorr_cols<T, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<p->h1c, G, smem, s>>>(p->n0, p->n1, p->m0, w0, sr, ss, (const cpx<T> *)p->kap, (const cpx<T> *)p->tw0,
+                                     (const cpx<T> *)(p->gen0 ? p->twpm0 : p->twp0), (const cpx<T> *)p->chirp0,
+                                     (const cpx<T> *)p->bfilt0, (cpx<T> *)p->U);
+        p->launches++;
+        if ((err = cudaGetLastError())) return err;
+    }
+    p->launches++;
+    return launch_rows_inv<T>(p, out, s);
+}
+
+cudaError_t decorrelate(Plan *p, const double *x, double xt0, double yt0, double sigma_ref, double sigma_sci,
+                        const void *diff, void *out, cudaStream_t s) {
+    return p->fp64 ? decorr_t<double>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, s)
+                   : decorr_t<float>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, s);
 }
 
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s) {
