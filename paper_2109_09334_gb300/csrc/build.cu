@@ -662,6 +662,8 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, in
 
 // ---------------------------------------------------------------------------
 // Stage 2: sum over m.  One block per stage-1 row.
+constexpr int kS2Out = 8;  // lag outputs per warp task in k_stage2
+
 template <typename T>
 __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npairs,
                          const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ Q,
@@ -681,38 +683,76 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npa
     const int nr1 = 2 * h1 + 1;
     int nq = 1;
     if (pd.kind == PK_LAMBDA) nq = db - pd.b + 1;  // q = 0..db-p
-    const int nout = nr1 * nq;
     const cpx<T> *q = Q + (size_t)row * h1c;
     const double invP = 1.0 / ((double)n0 * (double)n1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = warp; o < nout; o += nw) {
-        const int qi = o / nr1, rho1 = o - qi * nr1 - h1;
-        Acc<T> a;
-        a.zero();
-        for (int mm = lane; mm < h1c; mm += 32) {
-            cpx<T> v = q[mm];
-            if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)qi * h1c + mm]);
-            cpx<T> e = conj(tw1[imod(mm * rho1, n1)]);
-            T wm = (mm == 0 || (2 * mm == n1)) ? (T)1 : (T)2;
-            a.add(wm * (v.re * e.re - v.im * e.im));
-        }
-        for (int s = 16; s > 0; s >>= 1) shfl_add(a, s);
-        if (lane == 0) {
-            double val = a.wide() * invP;
-            size_t idx;
-            if (pd.kind == PK_OMEGA) {
-                // pair index among a <= b
-                const int ia = pd.a, ib = pd.b;
-                const int pidx = ia * nk - ia * (ia - 1) / 2 + (ib - ia);
-                idx = off_om + ((size_t)pidx * (4 * w0 + 1) + (rho0 + 2 * w0)) * (4 * w1 + 1) + (rho1 + 2 * w1);
-            } else if (pd.kind == PK_LAMBDA) {
-                const int s = term_index(pd.b, qi);  // (p, q)
-                idx = off_la + (((size_t)pd.a * nbt + s) * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
-            } else {
-                idx = off_th + ((size_t)pd.a * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
+    // outputs in chunks of up to kS2Out consecutive rho1 of one q index (cpq
+    // chunks per q); warp w takes chunk w % nchr of the round and every
+    // nsp-th slice of the frequencies, nsp = nw / nchr
+    __shared__ Acc<T> part[8][kS2Out];
+    const int cpq = (nr1 + kS2Out - 1) / kS2Out;
+    const int nch = nq * cpq;
+    for (int c0 = 0; c0 < nch; c0 += nw) {
+        const int nchr = min(nw, nch - c0);  // chunks in this round
+        const int nsp = nw / nchr;
+        const int ch = c0 + warp % nchr, sp = warp / nchr;
+        const bool act = sp < nsp;
+        Acc<T> a[kS2Out];
+#pragma unroll
+        for (int k = 0; k < kS2Out; ++k) a[k].zero();
+        const int qi = ch / cpq, roff = (ch - qi * cpq) * kS2Out;
+        const int r0 = roff - h1;  // first rho1 of the chunk
+        if (act) {
+            for (int mm = sp * 32 + lane; mm < h1c; mm += nsp * 32) {
+                cpx<T> v = q[mm];
+                if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)qi * h1c + mm]);
+                const T wm = (mm == 0 || (2 * mm == n1)) ? (T)1 : (T)2;
+                v = scale(v, wm);
+                int idx = imod(mm * r0, n1);  // (mm rho1) mod n1, stepped by mm
+#pragma unroll
+                for (int k = 0; k < kS2Out; ++k) {
+                    if (roff + k < nr1) {
+                        const cpx<T> e = conj(tw1[idx]);
+                        a[k].add(v.re * e.re - v.im * e.im);
+                    }
+                    idx += mm;
+                    if (idx >= n1) idx -= n1;
+                }
             }
-            lag[idx] = val;
         }
+#pragma unroll
+        for (int k = 0; k < kS2Out; ++k)
+            for (int s = 16; s > 0; s >>= 1) shfl_add(a[k], s);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kS2Out; ++k) part[warp][k] = a[k];
+        }
+        __syncthreads();
+        // warps of the same chunk combine their slices in a fixed order
+        if (threadIdx.x < nchr * kS2Out) {
+            const int cc = threadIdx.x / kS2Out, k = threadIdx.x % kS2Out;
+            const int chw = c0 + cc;
+            const int qo = chw / cpq, rw = (chw - qo * cpq) * kS2Out + k;
+            Acc<T> t = part[cc][k];
+            for (int sp2 = 1; sp2 < nsp; ++sp2) t.add(part[cc + sp2 * nchr][k]);
+            if (rw < nr1) {
+                const int rho1 = rw - h1;
+                const double val = t.wide() * invP;
+                size_t idx;
+                if (pd.kind == PK_OMEGA) {
+                    const int ia = pd.a, ib = pd.b;
+                    const int pidx = ia * nk - ia * (ia - 1) / 2 + (ib - ia);
+                    idx = off_om + ((size_t)pidx * (4 * w0 + 1) + (rho0 + 2 * w0)) * (4 * w1 + 1) + (rho1 + 2 * w1);
+                } else if (pd.kind == PK_LAMBDA) {
+                    const int s2 = term_index(pd.b, qo);  // (p, q)
+                    idx = off_la + (((size_t)pd.a * nbt + s2) * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
+                } else {
+                    idx = off_th + ((size_t)pd.a * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
+                }
+                lag[idx] = val;
+            }
+        }
+        __syncthreads();
     }
 }
 
