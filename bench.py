@@ -304,6 +304,8 @@ def run_ours(args):
         Rt, St = dev_pairs[k & 1]
         binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, x, info, D, stream)
 
+    # launch shapes picked by timing (kept for the server's plans below)
+    tuning = plan.autotune(*dev_pairs[0])
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -388,6 +390,7 @@ def run_ours(args):
               "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                              "note": "one pair alone (sfft_run_pair), device-timed per step"},
               "serving": {"api": "sfft_submit", "depth": args.depth, "batch": args.batch, "ms_per_pair": ms_step},
+              "tuning": tuning,
               "sequential": {"api": "sfft_run_pair", "value": world * args.steps / (seq_ms / 1e3),
                              "ms_per_pair": seq_ms / args.steps, "gpu_launches": int(seq_launches)},
               "solve": inf}

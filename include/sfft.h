@@ -341,6 +341,23 @@ typedef enum {
                                 the row FFTs of the unmasked pair) */
 } sfft_stage;
 
+/*
+ * Autotuning of launch shapes (no counterpart in the paper): runs one pair on
+ * the given device buffers with sfft_run_pair, then times each tunable stage
+ * (sfft_replay_stage) over candidate launch shapes and keeps the fastest:
+ * rows per block of the row FFT, images per block of the column FFT, row
+ * pairs per block of the inverse row FFT, and the solve grid (one or two
+ * blocks per SM).  The shapes change how the work is split into blocks, not
+ * the arithmetic, so results are unchanged.  They stay with the plan and are
+ * remembered for later plans (and server slots, pool lanes) of the same image
+ * size, types and D_K in this process.  Synchronises the stream.
+ */
+int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, void *d_diff,
+                       sfft_stream_t stream);
+
+/* The plan's launch shapes {rows, images, row pairs, solve grid}; 0 = built-in choice. */
+int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes);
+
 /* Number of kernels this plan has enqueued since it was created. */
 int sfft_plan_launch_count(sfft_plan_t plan, uint64_t *count);
 

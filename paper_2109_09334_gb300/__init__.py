@@ -110,6 +110,14 @@ class SfftPlan:
         sfft_subtract(self.handle, ref, sci, x, D, self.stream)
         return D
 
+    def autotune(self, ref, sci):
+        """Pick the fastest launch shapes for this plan (sfft_plan_autotune); returns them."""
+        torch = _torch()
+        self._check_img(ref), self._check_img(sci)
+        D = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        binding.sfft_plan_autotune(self.handle, ref, sci, D, self.stream)
+        return binding.sfft_plan_tuning(self.handle)
+
     def decorrelate(self, x, diff, sigma_ref, sigma_sci, xt0=0.0, yt0=0.0, out=None):
         """Noise decorrelation of a difference image (App. C); see sfft_decorrelate."""
         torch = _torch()

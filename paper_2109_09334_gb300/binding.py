@@ -105,6 +105,8 @@ def library():
         lib.sfft_pool_poll.argtypes = [vp, ptk]
         lib.sfft_pool_wait.argtypes = [vp, ptk, ctypes.c_int64]
         lib.sfft_pool_usage.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32)]
+        lib.sfft_plan_autotune.argtypes = [vp, vp, vp, vp, vp]
+        lib.sfft_plan_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
         _lib = lib
@@ -314,6 +316,17 @@ def sfft_pool_usage(pool):
     b, n = ctypes.c_uint64(), ctypes.c_int32()
     _check(library().sfft_pool_usage(pool, ctypes.byref(b), ctypes.byref(n)), "sfft_pool_usage")
     return b.value, n.value
+
+
+def sfft_plan_autotune(plan, d_ref, d_sci, d_diff, stream=None):
+    _check(library().sfft_plan_autotune(plan, _p(d_ref), _p(d_sci), _p(d_diff), _s(stream)), "sfft_plan_autotune")
+
+
+def sfft_plan_tuning(plan):
+    out = (ctypes.c_int32 * 4)()
+    _check(library().sfft_plan_tuning(plan, out), "sfft_plan_tuning")
+    return {"rows_per_block": out[0], "images_per_block": out[1], "row_pairs_per_block": out[2],
+            "solve_grid": out[3]}
 
 
 def sfft_plan_launch_count(plan):

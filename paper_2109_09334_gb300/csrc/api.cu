@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -145,6 +146,44 @@ void plan_free(Plan *p) {
         }                                                             \
         p->ws_bytes += (bytes);                                       \
     } while (0)
+
+// Launch shapes found by sfft_plan_autotune, kept for later plans of the same
+// image size, types and kernel degree (server slots, pool lanes).
+struct TuneEntry {
+    int n0, n1, dtype, precision, dk;
+    int tr, gi, ng, sgrid;
+};
+constexpr int kTuneCache = 64;
+static TuneEntry g_tune[kTuneCache];
+static int g_ntune = 0;
+static std::mutex g_tune_mu;
+
+static bool tune_key_eq(const TuneEntry &e, const sfft_config *c) {
+    return e.n0 == c->n0 && e.n1 == c->n1 && e.dtype == c->dtype && e.precision == c->precision && e.dk == c->dk;
+}
+
+static void tune_lookup(Plan *p) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int k = 0; k < g_ntune; ++k)
+        if (tune_key_eq(g_tune[k], &p->cfg)) {
+            p->tune_tr = g_tune[k].tr;
+            p->tune_gi = g_tune[k].gi;
+            p->tune_ng = g_tune[k].ng;
+            p->tune_sgrid = g_tune[k].sgrid;
+        }
+}
+
+static void tune_store(const Plan *p) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    int k = 0;
+    while (k < g_ntune && !tune_key_eq(g_tune[k], &p->cfg)) ++k;
+    if (k == g_ntune) {
+        if (g_ntune == kTuneCache) k = 0;  // full: overwrite the oldest slot
+        else ++g_ntune;
+    }
+    const sfft_config &c = p->cfg;
+    g_tune[k] = TuneEntry{c.n0, c.n1, c.dtype, c.precision, c.dk, p->tune_tr, p->tune_gi, p->tune_ng, p->tune_sgrid};
+}
 
 int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     Plan *p = new (std::nothrow) Plan();
@@ -331,6 +370,7 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         plan_free(p);
         return SFFT_ERR_CUDA;
     }
+    tune_lookup(p);
     *out = p;
     return SFFT_OK;
 }
@@ -474,6 +514,78 @@ int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
     cudaError_t e = row_transform(p, d_ref, d_sci, nullptr, false, s);
     if (e == cudaSuccess) e = subtract_from_rows(p, d_x, d_diff, s);
     return status_of(e);
+}
+
+int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, void *d_diff,
+                       sfft_stream_t stream) {
+    if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
+    if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_pair(p, d_ref, d_sci, nullptr, nullptr, nullptr, nullptr, nullptr, d_diff, s);
+    if (rc != SFFT_OK) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SFFT_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SFFT_ERR_CUDA;
+    }
+    // time one stage (one warm-up, then 5 replays) with the plan's current shapes
+    auto time_stage = [&](int stage, float *ms) -> int {
+        int r = sfft_replay_stage(plan, stage, stream);
+        if (r != SFFT_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 5 && r == SFFT_OK; ++k) r = sfft_replay_stage(plan, stage, stream);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return SFFT_ERR_CUDA;
+        cudaEventElapsedTime(ms, e0, e1);
+        return r;
+    };
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    struct Knob {
+        int *field;
+        int stage;
+        int cand[5];
+    } knobs[] = {
+        {&p->tune_tr, SFFT_STAGE_ROWS, {0, 8, 4, 2, 1}},
+        {&p->tune_gi, SFFT_STAGE_COLS, {0, 3, 2, 1, -1}},
+        {&p->tune_ng, SFFT_STAGE_SUBTRACT, {0, 2, 1, -1, -1}},
+        {&p->tune_sgrid, SFFT_STAGE_SOLVE, {0, sms, -1, -1, -1}},
+    };
+    for (Knob &kb : knobs) {
+        if (kb.stage == SFFT_STAGE_COLS && p->gen0) continue;  // no column FFT
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int c : kb.cand) {
+            if (c < 0) continue;
+            *kb.field = c;
+            float ms = 0.f;
+            rc = time_stage(kb.stage, &ms);
+            if (rc != SFFT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        *kb.field = best;
+        if (rc != SFFT_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == SFFT_OK) tune_store(p);
+    return rc;
+}
+
+int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes) {
+    if (!plan || !shapes) return SFFT_ERR_INVALID;
+    const Plan *p = (const Plan *)plan;
+    shapes[0] = p->tune_tr;
+    shapes[1] = p->tune_gi;
+    shapes[2] = p->tune_ng;
+    shapes[3] = p->tune_sgrid;
+    return SFFT_OK;
 }
 
 int sfft_decorrelate(sfft_plan_t plan, const double *d_x, double xt0, double yt0, double sigma_ref,

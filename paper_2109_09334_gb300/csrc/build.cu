@@ -884,6 +884,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
         if (TR > 16) TR = 16;
         auto smem_of = [&](int tr) { return (size_t)tr * (padded_len(p->m1) + 4) * sizeof(cpx<T>); };
         while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
+        if (p->tune_tr > 0 && p->tune_tr < TR) TR = p->tune_tr;
         const size_t smem = smem_of(TR);
         auto kern = k_rows_blu<T, I>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -897,6 +898,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     if (TR > p->n0) TR = p->n0;
     auto smem_of = [&](int tr) { return ((size_t)p->n1 + (size_t)tr * (padded_len(p->n1) + 4)) * sizeof(cpx<T>); };
     while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
+    if (p->tune_tr > 0 && p->tune_tr < TR) TR = p->tune_tr;
     const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -929,6 +931,10 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     size_t smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
     while (GI > 1 && smem > 110 * 1024) {
         --GI;
+        smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+    }
+    if (p->tune_gi > 0 && p->tune_gi < GI) {
+        GI = p->tune_gi;
         smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
     }
     auto kern = k_cols<T>;

@@ -50,6 +50,8 @@ struct Plan {
     void *chirp1, *bfilt1, *twpm1;  // Bluestein tables for n1 (compute type)
     void *chirp0, *bfilt0, *twpm0;  // Bluestein tables for n0 (noise decorrelation only)
     double *kimg;                   // L0 x L1 kernel image (noise decorrelation)
+    // launch shapes chosen by sfft_plan_autotune (0: the built-in choice)
+    int tune_tr, tune_gi, tune_ng, tune_sgrid;
     void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
     void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
     void *F;               // [(dk+2)][m][x] row transforms (compute type)

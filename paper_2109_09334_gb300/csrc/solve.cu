@@ -675,7 +675,8 @@ static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *co
         ba.sys[b] = system_args<T>(p->n, M[b], rhs[b], x[b], info[b], p->dscale, p->xw, p->r, p->A, p->Wm, p->zv,
                                    p->flag);
     }
-    const cudaError_t err = launch_batch(ba, plans[0]->solve_grid, st);
+    const int sg = plans[0]->tune_sgrid;
+    const cudaError_t err = launch_batch(ba, (sg > count && sg <= plans[0]->solve_grid) ? sg : plans[0]->solve_grid, st);
     plans[0]->launches += 1;
     return err;
 }

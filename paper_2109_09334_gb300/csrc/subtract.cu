@@ -261,6 +261,10 @@ static cudaError_t launch_rows_inv(Plan *p, void *diff, cudaStream_t s) {
             NG /= 2;
             smem = (size_t)NG * padded_len(p->m1) * sizeof(cpx<T>);
         }
+        if (p->tune_ng > 0 && p->tune_ng < NG) {
+            NG = p->tune_ng;
+            smem = (size_t)NG * padded_len(p->m1) * sizeof(cpx<T>);
+        }
         const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
         const cpx<T> *ch = (const cpx<T> *)p->chirp1, *bf = (const cpx<T> *)p->bfilt1, *tw = (const cpx<T> *)p->twpm1;
         if (p->cfg.dtype == SFFT_F64) {
@@ -283,6 +287,10 @@ static cudaError_t launch_rows_inv(Plan *p, void *diff, cudaStream_t s) {
         size_t smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
         while (NG > 1 && smem > 110 * 1024) {
             NG /= 2;
+            smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+        }
+        if (p->tune_ng > 0 && p->tune_ng < NG) {
+            NG = p->tune_ng;
             smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
         }
         const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
