@@ -81,3 +81,42 @@ def test_sampled_parity(name, shape):
     De = oracle.subtract_pixels(R32, S32, x, c, pix)
     assert np.sqrt(np.mean((D.ravel()[pix] - De) ** 2)) <= 1e-3 * spec.sigma
     plan.close()
+
+
+def test_fp64_path_sampled_parity_4096():
+    """The plain FP64 GPU path (FP64 FFTs, products, sums and Cholesky) on the
+    4096^2 pair: sampled M and rhs within 1e-10 (relative, RMS over the
+    sample), the solution within 1e-8 of an FP64 solve of the GPU-built
+    system, and D within 1e-6 sigma RMS at sampled pixels."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, info_from_bytes
+    from paper_2109_09334_gb300.build import build
+    build()
+    spec = synth.PAIR4096
+    f = spec.fit
+    R, S = synth.make_pair(spec, seed=5)
+    R32, S32 = R.astype(np.float32), S.astype(np.float32)
+    plan = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype="float32",
+                    precision="fp64")
+    D, x, info, M, rhs = plan.run_pair(torch.from_numpy(R32).cuda(), torch.from_numpy(S32).cuda(),
+                                       keep_system=True)
+    torch.cuda.synchronize()
+    M, rhs, x, D = M.cpu().numpy(), rhs.cpu().numpy(), x.cpu().numpy(), D.cpu().numpy().astype(np.float64)
+    assert info_from_bytes(info.cpu().numpy())["status"] == 0
+    n = rhs.shape[0]
+    c = oracle.OracleConfig(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio)
+    rng = np.random.default_rng(13)
+    rows, cols = rng.integers(0, n, 200), rng.integers(0, n, 200)
+    Me = oracle.system_entries(R32, S32, c, rows, cols)
+    assert np.sqrt(np.mean((M[rows, cols] - Me) ** 2)) <= 1e-10 * np.sqrt(np.mean(Me ** 2))
+    rr = rng.integers(0, n, 100)
+    re = oracle.system_entries(R32, S32, c, rr, -np.ones_like(rr))
+    assert np.sqrt(np.mean((rhs[rr] - re) ** 2)) <= 1e-10 * np.sqrt(np.mean(re ** 2))
+    xs = np.linalg.solve(M, rhs)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    pix = rng.integers(0, spec.n0 * spec.n1, 2000)
+    De = oracle.subtract_pixels(R32, S32, x, c, pix)
+    # D is written as float32 (the image type): compare within its rounding too
+    assert np.sqrt(np.mean((D.ravel()[pix] - De) ** 2)) <= 1e-6 * spec.sigma + 1e-7 * np.sqrt(np.mean(De ** 2))
+    plan.close()
