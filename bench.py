@@ -49,6 +49,8 @@ def parse():
                     help="pair: only warmup + steps pairs through sfft_run_pair (for profiler captures)")
     ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
     ap.add_argument("--batch", type=int, default=4, help="systems solved per launch in the serving path")
+    ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
+                    help="sectors64: solve the sectors' systems eight per launch, or one per pair")
     return ap.parse_args()
 
 
@@ -626,9 +628,15 @@ def run_sectors(args):
         work.append((plan, Rt, St, D, x, info, n, f))
     stream = torch.cuda.Stream(dev)
 
-    def run_all():
+    def run_seq():
         for plan, Rt, St, D, x, info, n, f in work:
             binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, x, info, D, stream)
+
+    def run_batched():  # systems solved eight per launch (sfft_run_pairs)
+        binding.sfft_run_pairs([w[0].handle for w in work], [w[1] for w in work], [w[2] for w in work], None,
+                               [w[4] for w in work], [w[5] for w in work], [w[3] for w in work], stream)
+
+    run_all = run_seq if args.sector_solve == "single" else run_batched
 
     for _ in range(max(args.warmup, 1)):
         run_all()
@@ -664,6 +672,15 @@ def run_sectors(args):
 
     eager_ms = timed(run_all)
     ref = [w[3].clone() for w in work]  # the eager batch's difference images
+    if run_all is run_batched:  # batched solves give the single-pair results bit for bit
+        for w in work:
+            w[3].zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            run_seq()
+        torch.cuda.synchronize()
+        if not all(torch.equal(a, w[3]) for a, w in zip(ref, work)):
+            raise RuntimeError("batched solves differ from the single-pair path")
     graph_ms = None
     if graph is not None:
         for w in work:
@@ -681,7 +698,8 @@ def run_sectors(args):
            "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
            "data": "synthetic sectors cut from one seeded field (one source per 500 px^2)",
            "config": {"workload": "sectors64", "sizes": [w[6] for w in work],
-                      "fits": [[w[7].w0, w[7].dk, w[7].db] for w in work], "precision": args.precision},
+                      "fits": [[w[7].w0, w[7].dk, w[7].db] for w in work], "precision": args.precision,
+                      "solve": args.sector_solve},
            "graph": graph_note, "eager": {"value": world * len(work) * 1e3 / eager_ms, "ms_per_batch": eager_ms},
            "mpix_per_s": world * npix / (ms * 1e3), "gpu_launches": int(per_batch * K)}
     for w in work:

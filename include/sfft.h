@@ -203,6 +203,29 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci,
                   sfft_solve_info *d_info, void *d_diff, sfft_stream_t stream);
 
 /*
+ * Several whole pairs on device buffers, pair i with its own plan plans[i]
+ * (Sec. 3 subtracts the pairs of a survey one by one; the pairs here may
+ * differ in size and basis).  Every pair's system (Eq. 18) is built, the
+ * systems are then solved up to eight per launch of the batched solve
+ * (grouped by number of unknowns, largest first), and every pair is
+ * subtracted (Eq. 3).  Per pair the results equal those of
+ * sfft_run_pair on the same plan and inputs, bit for bit.
+ *   plans[count]   : distinct plans sharing cfg.precision; a plan listed
+ *                    twice, or a precision mismatch, is SFFT_ERR_INVALID.
+ *   d_refs, d_scis, d_diffs : count device image pointers, each as in
+ *                    sfft_run_pair (d_diffs[i] distinct from the inputs).
+ *   d_masks        : NULL, or count pointers, each NULL or a mask.
+ *   d_xs, d_infos  : NULL, or count pointers, each NULL (plan-owned buffer)
+ *                    or a device buffer as in sfft_run_pair.
+ * The normal matrices land in the plans' own buffers.  Errors found on the
+ * host return before any launch; a launch error stops the sequence and is
+ * returned.  Solve failures are reported per pair in its sfft_solve_info.
+ */
+int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs,
+                   const void *const *d_scis, const uint8_t *const *d_masks, double *const *d_xs,
+                   sfft_solve_info *const *d_infos, void *const *d_diffs, sfft_stream_t stream);
+
+/*
  * One whole pair from and to host memory: copies h_ref, h_sci (and h_mask if
  * not NULL) to plan-owned device buffers, runs build, solve and subtract,
  * copies the coefficients, the solve status and the difference image back,

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     sfft_plan_workspace_bytes,
     sfft_run_pair,
     sfft_run_pair_host,
+    sfft_run_pairs,
     sfft_server_create,
     sfft_server_destroy,
     sfft_server_workspace_bytes,
@@ -148,6 +149,24 @@ class SfftPlan:
         sfft_run_pair_host(self.handle, ref, sci, mask, x, info, D, self.stream)
         return D, x, {"status": info.status, "iters": info.iters, "rel_residual": info.rel_residual,
                       "min_pivot": info.min_pivot}
+
+
+def run_pairs(plans, refs, scis, masks=None, outs=None):
+    """Pairs i = 0..len(plans)-1, pair i on plans[i] (SfftPlan objects, all
+    distinct, one precision), through sfft_run_pairs on the first plan's
+    stream: systems built pair by pair, solved up to eight per launch, then
+    subtracted.  Returns [(D, x, info)] as SfftPlan.run_pair does."""
+    torch = _torch()
+    if not plans:
+        return []
+    for p, r, s in zip(plans, refs, scis):
+        p._check_img(r), p._check_img(s)
+    Ds = [outs[i] if outs is not None and outs[i] is not None else
+          torch.empty(p.shape, dtype=p.dtype, device=p.device) for i, p in enumerate(plans)]
+    xs = [torch.empty(p.n, dtype=torch.float64, device=p.device) for p in plans]
+    infos = [torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=p.device) for p in plans]
+    sfft_run_pairs([p.handle for p in plans], refs, scis, masks, xs, infos, Ds, plans[0].stream)
+    return list(zip(Ds, xs, infos))
 
 
 class SfftServer:

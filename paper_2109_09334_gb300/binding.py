@@ -88,6 +88,7 @@ def library():
         lib.sfft_subtract.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.sfft_run_pairs.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
         reqp, tkp = ctypes.POINTER(sfft_request), ctypes.POINTER(sfft_ticket)
         lib.sfft_server_create.argtypes = [cfgp, i32, i32, ctypes.POINTER(vp)]
         lib.sfft_flush.argtypes = [vp]
@@ -209,6 +210,26 @@ def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):
 def sfft_run_pair(plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, stream=None):
     _check(library().sfft_run_pair(plan, _p(d_ref), _p(d_sci), _p(d_mask), _p(d_M), _p(d_rhs), _p(d_x),
                                    _p(d_info), _p(d_diff), _s(stream)), "sfft_run_pair")
+
+
+def _ptr_array(items):
+    """A C array of the items' addresses, or NULL when items is None."""
+    if items is None:
+        return None
+    return (ctypes.c_void_p * len(items))(*[_p(v) for v in items])
+
+
+def sfft_run_pairs(plans, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, stream=None):
+    """Several pairs, each with its own plan; d_masks, d_xs, d_infos may be None or hold None."""
+    n = len(plans)
+    for name, v in (("d_refs", d_refs), ("d_scis", d_scis), ("d_diffs", d_diffs), ("d_masks", d_masks),
+                    ("d_xs", d_xs), ("d_infos", d_infos)):
+        if v is not None and len(v) != n:
+            raise ValueError(f"sfft_run_pairs: {name} has {len(v)} entries for {n} plans")
+    hp = (ctypes.c_void_p * n)(*plans)
+    _check(library().sfft_run_pairs(hp, n, _ptr_array(d_refs), _ptr_array(d_scis), _ptr_array(d_masks),
+                                    _ptr_array(d_xs), _ptr_array(d_infos), _ptr_array(d_diffs), _s(stream)),
+           "sfft_run_pairs")
 
 
 def sfft_run_pair_host(plan, h_ref, h_sci, h_mask, h_x, h_info, h_diff, stream=None):

@@ -1,5 +1,8 @@
 // api.cu -- the extern "C" entry points declared in include/sfft.h.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -603,6 +606,62 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
     if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
     if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
     return run_pair((Plan *)plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, (cudaStream_t)stream);
+}
+
+int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs, const void *const *d_scis,
+                   const uint8_t *const *d_masks, double *const *d_xs, sfft_solve_info *const *d_infos,
+                   void *const *d_diffs, sfft_stream_t stream) {
+    if (!plans || count < 1 || !d_refs || !d_scis || !d_diffs) return SFFT_ERR_INVALID;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !d_refs[i] || !d_scis[i] || !d_diffs[i]) return SFFT_ERR_INVALID;
+        if (d_diffs[i] == d_refs[i] || d_diffs[i] == d_scis[i]) return SFFT_ERR_INVALID;
+        if (((Plan *)plans[i])->fp64 != ((Plan *)plans[0])->fp64) return SFFT_ERR_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return SFFT_ERR_INVALID;  // one workspace per pair
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        Plan *p = (Plan *)plans[i];
+        p->last_ref = d_refs[i];
+        p->last_sci = d_scis[i];
+        p->last_mask = d_masks ? d_masks[i] : nullptr;
+        p->last_M = p->M_own;
+        p->last_rhs = p->rhs_own;
+        p->last_x = (d_xs && d_xs[i]) ? d_xs[i] : p->x_own;
+        p->last_info = (d_infos && d_infos[i]) ? d_infos[i] : p->info_own;
+        p->last_diff = d_diffs[i];
+        p->last_stream = s;
+        e = build_system(p, p->last_ref, p->last_sci, p->last_mask, p->M_own, p->rhs_own, s);
+    }
+    // A launch lasts as long as its largest system: group the systems by
+    // size, largest first (the order of the systems in a launch does not
+    // change their results).
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return ((Plan *)plans[a])->n > ((Plan *)plans[b])->n; });
+    for (int g = 0; g < count && e == cudaSuccess; g += kMaxSolveBatch) {
+        const int cnt = count - g < kMaxSolveBatch ? count - g : kMaxSolveBatch;
+        Plan *ps[kMaxSolveBatch];
+        const double *M[kMaxSolveBatch], *rhs[kMaxSolveBatch];
+        double *x[kMaxSolveBatch];
+        sfft_solve_info *info[kMaxSolveBatch];
+        for (int b = 0; b < cnt; ++b) {
+            ps[b] = (Plan *)plans[order[g + b]];
+            M[b] = ps[b]->last_M;
+            rhs[b] = ps[b]->last_rhs;
+            x[b] = ps[b]->last_x;
+            info[b] = ps[b]->last_info;
+        }
+        e = solve_batch(ps, cnt, M, rhs, x, info, s);
+    }
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        Plan *p = (Plan *)plans[i];
+        if (p->last_mask) e = row_transform(p, p->last_ref, p->last_sci, nullptr, false, s);
+        if (e == cudaSuccess) e = subtract_from_rows(p, p->last_x, p->last_diff, s);
+    }
+    return status_of(e);
 }
 
 int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci, const uint8_t *h_mask,

@@ -17,6 +17,8 @@ constexpr int kMaxNA = 64;
 // (2 per block), then the subtraction's kernel sums.
 constexpr int kMaxSolveGrid = 512;
 constexpr int kSolveTail = 8 + 2 * kMaxSolveGrid;
+// Systems solved together by one launch of the batched solve.
+constexpr int kMaxSolveBatch = 8;
 
 enum PairKind { PK_OMEGA = 0, PK_LAMBDA = 1, PK_THETA = 2 };
 

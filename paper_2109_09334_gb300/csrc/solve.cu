@@ -42,7 +42,7 @@ constexpr double kTol = 1e-12;  // ||r|| / ||rhs||
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSM = 2;  // resident FP32 solve blocks per SM (more loads in flight); FP64 takes 1
 constexpr int kSeg = 8;         // row segments of the W^T y product
-constexpr int kMaxBatch = 8;    // systems solved together by one launch
+constexpr int kMaxBatch = kMaxSolveBatch;  // systems solved together by one launch
 
 template <typename T>
 struct SolveArgs {
@@ -412,15 +412,23 @@ __device__ void update_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int 
     }
 }
 
-// Up to kMaxBatch systems of the same size, solved together: every phase
-// spreads the tasks of all systems over the grid, and block b factors the
-// diagonal blocks of system b, so the serial chains of the systems run side
-// by side.
+// Up to kMaxBatch systems, of equal or different sizes, solved together:
+// every phase spreads the tasks of all systems over the grid, and block b
+// factors the diagonal blocks of system b, so the serial chains of the
+// systems run side by side.  Each system sees the operations of a solve on
+// its own, in the same order.
 template <typename T>
 struct BatchArgs {
     int nsys;
     SolveArgs<T> sys[kMaxBatch];
 };
+
+// system of a flat task index, from the prefix sums offs[0..nsys]
+__device__ __forceinline__ int sys_of(const int *offs, int nsys, int task) {
+    int b = 0;
+    while (b + 1 < nsys && task >= offs[b + 1]) ++b;
+    return b;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k_solve_coop(BatchArgs<T> ba) {
@@ -431,7 +439,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     const int gtid = bid * kThreads + tid, gthreads = nbk * kThreads;
     const int warp = tid >> 5, lane = tid & 31, nw = kThreads / 32;
     const int nsys = ba.nsys;
-    const int n = ba.sys[0].n, nblk = ba.sys[0].nblk;  // the same for every system
+    // sizes may differ between systems: rows of all systems as one flat range
+    int nrow[kMaxBatch + 1];
+    nrow[0] = 0;
+    int nblk_max = 0;
+    for (int b = 0; b < nsys; ++b) {
+        nrow[b + 1] = nrow[b] + ba.sys[b].n;
+        nblk_max = max(nblk_max, ba.sys[b].nblk);
+    }
+    const int nrows_all = nrow[nsys];
 
     // ---- status reset; Jacobi scaling, zero W and x -------------------------
     if (bid == 0 && tid < nsys) {
@@ -443,6 +459,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     grid.sync();
     for (int b = 0; b < nsys; ++b) {
         const SolveArgs<T> &s = ba.sys[b];
+        const int n = s.n;
         for (int i = gtid; i < n; i += gthreads) {
             const double d = s.M[(size_t)i * n + i];
             if (!(d > 0.0)) s.flag[0] = SFFT_ERR_SINGULAR;
@@ -452,9 +469,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         for (size_t e = gtid; e < (size_t)n * n; e += gthreads) s.W[e] = (T)0;
     }
     grid.sync();
-    for (int row = bid; row < nsys * n; row += nbk) {
-        const int b = row / n, i = row - b * n;
+    for (int row = bid; row < nrows_all; row += nbk) {
+        const int b = sys_of(nrow, nsys, row), i = row - nrow[b];
         const SolveArgs<T> &s = ba.sys[b];
+        const int n = s.n;
         const double di = s.dsc[i];
         const double *Mi = s.M + (size_t)i * n;
         T *Ai = s.A + (size_t)i * n;
@@ -477,48 +495,71 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     grid.sync();
 
     // ---- Cholesky and W = L^-1 ----------------------------------------------
-    // A system whose status turned negative (written before a barrier, so
-    // read alike by every block) is skipped from then on.
+    // A system whose status turned negative is skipped from then on, and one
+    // whose panels are done waits for the larger ones.  The task counts must
+    // be the same in every block, so each step reads the status flags once,
+    // right after a barrier and before the update phase in which factor_inv
+    // may write them again.
     if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_inv(ba.sys[bid], sm.fac, 0);
     grid.sync();
-    for (int kb = 0; kb < nblk; ++kb) {
+    for (int kb = 0; kb < nblk_max; ++kb) {
         const int k0 = kb * kNB;
-        const int kn = min(kNB, n - k0);
         const int base = k0 + kNB;  // first trailing row
-        const int rows = n - base;  // may be <= 0 on the last block
-        {
-            const int npt = rows > 0 ? (rows + kTile - 1) / kTile : 0;
-            const int nwt = (k0 + kTile - 1) / kTile;
-            const int per = npt + nwt;
-            for (int task = bid; task < nsys * per; task += nbk) {
-                const int b = task / per;
-                if (ba.sys[b].flag[0] < 0) continue;
-                panel_task(ba.sys[b], sm.tile, k0, kn, base, npt, task - b * per);
+        unsigned live = 0;
+        for (int b = 0; b < nsys; ++b)
+            if (kb < ba.sys[b].nblk && ba.sys[b].flag[0] == 0) live |= 1u << b;
+        int offs[kMaxBatch + 1];
+        offs[0] = 0;
+        for (int b = 0; b < nsys; ++b) {
+            const SolveArgs<T> &s = ba.sys[b];
+            int cnt = 0;
+            if (live & (1u << b)) {
+                const int rows = s.n - base;
+                cnt = (rows > 0 ? (rows + kTile - 1) / kTile : 0) + (k0 + kTile - 1) / kTile;
             }
+            offs[b + 1] = offs[b] + cnt;
+        }
+        for (int task = bid; task < offs[nsys]; task += nbk) {
+            const int b = sys_of(offs, nsys, task);
+            const SolveArgs<T> &s = ba.sys[b];
+            const int rows = s.n - base;
+            const int npt = rows > 0 ? (rows + kTile - 1) / kTile : 0;
+            panel_task(s, sm.tile, k0, min(kNB, s.n - k0), base, npt, task - offs[b]);
         }
         grid.sync();
-        if (rows <= 0) break;  // last block: nothing below (same in every block)
         // Block b takes task 0 of system b (the tile holding its next diagonal
         // block) and factors that block at once; the other blocks share the
         // remaining tasks of all systems.
-        {
-            const int nt = (rows + kTile - 1) / kTile;
-            const int ntiles = nt * (nt + 1) / 2;
-            const int ncw = (k0 + kNB + kTile - 1) / kTile;
-            const int per = ntiles + nt * ncw - 1;  // tasks besides task 0
-            if (bid < nsys) {
-                const SolveArgs<T> &s = ba.sys[bid];
-                if (s.flag[0] == 0) {
-                    update_task(s, sm.tile, k0, base, ntiles, ncw, 0);
-                    __syncthreads();  // the tile's writes are visible to the block
-                    factor_inv(s, sm.fac, kb + 1);
-                }
-            } else {
-                for (int task = bid - nsys; task < nsys * per; task += nbk - nsys) {
-                    const int b = task / per;
-                    if (ba.sys[b].flag[0] < 0) continue;
-                    update_task(ba.sys[b], sm.tile, k0, base, ntiles, ncw, 1 + task - b * per);
-                }
+        bool any = false;
+        offs[0] = 0;
+        for (int b = 0; b < nsys; ++b) {
+            const SolveArgs<T> &s = ba.sys[b];
+            const int rows = s.n - base;
+            int per = 0;
+            if ((live & (1u << b)) && rows > 0) {
+                const int nt = (rows + kTile - 1) / kTile;
+                per = nt * (nt + 1) / 2 + nt * ((k0 + kNB + kTile - 1) / kTile) - 1;  // besides task 0
+                any = true;
+            }
+            offs[b + 1] = offs[b] + per;
+        }
+        if (!any) break;  // every system's panels are done (same in every block)
+        if (bid < nsys) {
+            const SolveArgs<T> &s = ba.sys[bid];
+            const int rows = s.n - base;
+            if ((live & (1u << bid)) && rows > 0) {
+                const int nt = (rows + kTile - 1) / kTile;
+                update_task(s, sm.tile, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile, 0);
+                __syncthreads();  // the tile's writes are visible to the block
+                factor_inv(s, sm.fac, kb + 1);
+            }
+        } else {
+            for (int task = bid - nsys; task < offs[nsys]; task += nbk - nsys) {
+                const int b = sys_of(offs, nsys, task);
+                const SolveArgs<T> &s = ba.sys[b];
+                const int nt = (s.n - base + kTile - 1) / kTile;
+                update_task(s, sm.tile, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile,
+                            1 + task - offs[b]);
             }
         }
         grid.sync();
@@ -535,17 +576,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     const unsigned all = (1u << nsys) - 1u;
     if (warp < nsys) {
         const SolveArgs<T> &s = ba.sys[warp];
-        const double bb = dot_warp<double>(s.rhs, s.rhs, lane, n);
+        const double bb = dot_warp<double>(s.rhs, s.rhs, lane, s.n);
         if (lane == 0) sums[warp][1] = bb;
     }
     __syncthreads();
+    int wofs[kMaxBatch + 1];  // flat W^T y tasks of all systems
+    wofs[0] = 0;
+    for (int b = 0; b < nsys; ++b) wofs[b + 1] = wofs[b] + ((ba.sys[b].n + 31) / 32) * kSeg;
     for (int it = 0; it <= kMaxIters && done != all; ++it) {
         // r = rhs - M x (FP64); z = D r
-        for (int row = bid * nw + warp; row < nsys * n; row += nbk * nw) {
-            const int b = row / n, i = row - b * n;
+        for (int row = bid * nw + warp; row < nrows_all; row += nbk * nw) {
+            const int b = sys_of(nrow, nsys, row), i = row - nrow[b];
             if (done & (1u << b)) continue;
             const SolveArgs<T> &s = ba.sys[b];
-            const double a = dot_warp<double>(s.M + (size_t)i * n, s.x, lane, n);
+            const double a = dot_warp<double>(s.M + (size_t)i * s.n, s.x, lane, s.n);
             const double ri = s.rhs[i] - a;
             if (lane == 0) {
                 s.r[i] = ri;
@@ -555,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         grid.sync();
         if (warp < nsys && !(done & (1u << warp))) {
             const SolveArgs<T> &s = ba.sys[warp];
-            const double rr = dot_warp<double>(s.r, s.r, lane, n);
+            const double rr = dot_warp<double>(s.r, s.r, lane, s.n);
             if (lane == 0) sums[warp][0] = rr;
         }
         __syncthreads();
@@ -578,45 +622,42 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         }
         if (done == all) break;
         // y = W z  (W lower triangular)
-        for (int row = bid * nw + warp; row < nsys * n; row += nbk * nw) {
-            const int b = row / n, i = row - b * n;
+        for (int row = bid * nw + warp; row < nrows_all; row += nbk * nw) {
+            const int b = sys_of(nrow, nsys, row), i = row - nrow[b];
             if (done & (1u << b)) continue;
             const SolveArgs<T> &s = ba.sys[b];
-            const T a = dot_warp<T>(s.W + (size_t)i * n, s.z, lane, i + 1);
+            const T a = dot_warp<T>(s.W + (size_t)i * s.n, s.z, lane, i + 1);
             if (lane == 0) s.y[i] = a;
         }
         grid.sync();
         // w = W^T y in kSeg row segments (coalesced rows of W), summed in a fixed order
-        {
+        for (int task = bid * nw + warp; task < wofs[nsys]; task += nbk * nw) {
+            const int b = sys_of(wofs, nsys, task), q = task - wofs[b];
+            if (done & (1u << b)) continue;
+            const SolveArgs<T> &s = ba.sys[b];
+            const int n = s.n;
             const int segrows = (n + kSeg - 1) / kSeg;
-            const int nchunk = (n + 31) / 32;
-            const int per = nchunk * kSeg;
-            for (int task = bid * nw + warp; task < nsys * per; task += nbk * nw) {
-                const int b = task / per, q = task - b * per;
-                if (done & (1u << b)) continue;
-                const SolveArgs<T> &s = ba.sys[b];
-                const int ch = q / kSeg, sg = q % kSeg;
-                const int i = ch * 32 + lane;
-                const int k0 = max(ch * 32, sg * segrows), k1 = min(n, (sg + 1) * segrows);
-                if (i < n) s.wseg[(size_t)sg * n + i] = col_dot<T>(s.W, s.y, n, i, k0, k1);
-            }
+            const int ch = q / kSeg, sg = q % kSeg;
+            const int i = ch * 32 + lane;
+            const int k0 = max(ch * 32, sg * segrows), k1 = min(n, (sg + 1) * segrows);
+            if (i < n) s.wseg[(size_t)sg * n + i] = col_dot<T>(s.W, s.y, n, i, k0, k1);
         }
         grid.sync();
-        for (int e = gtid; e < nsys * n; e += gthreads) {
-            const int b = e / n, i = e - b * n;
+        for (int e = gtid; e < nrows_all; e += gthreads) {
+            const int b = sys_of(nrow, nsys, e), i = e - nrow[b];
             if (done & (1u << b)) continue;
             const SolveArgs<T> &s = ba.sys[b];
             T a = (T)0;
 #pragma unroll
-            for (int sg = 0; sg < kSeg; ++sg) a += s.wseg[(size_t)sg * n + i];
+            for (int sg = 0; sg < kSeg; ++sg) a += s.wseg[(size_t)sg * s.n + i];
             s.x[i] += s.dsc[i] * (double)a;
         }
         if (bid == 0 && tid < nsys && !(done & (1u << tid))) ba.sys[tid].flag[1] += 1;
         grid.sync();
     }
     // ---- results ------------------------------------------------------------
-    for (int e = gtid; e < nsys * n; e += gthreads) {
-        const int b = e / n, i = e - b * n;
+    for (int e = gtid; e < nrows_all; e += gthreads) {
+        const int b = sys_of(nrow, nsys, e), i = e - nrow[b];
         ba.sys[b].xout[i] = ba.sys[b].x[i];
     }
     if (bid == 0 && tid < nsys) {
@@ -685,7 +726,7 @@ cudaError_t solve_batch(Plan *const *plans, int count, const double *const *M, c
                         double *const *x, sfft_solve_info *const *info, cudaStream_t s) {
     if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
     for (int b = 1; b < count; ++b)
-        if (plans[b]->n != plans[0]->n || plans[b]->fp64 != plans[0]->fp64) return cudaErrorInvalidValue;
+        if (plans[b]->fp64 != plans[0]->fp64) return cudaErrorInvalidValue;  // sizes may differ
     return plans[0]->fp64 ? solve_batch_t<double>(plans, count, M, rhs, x, info, s)
                           : solve_batch_t<float>(plans, count, M, rhs, x, info, s);
 }
