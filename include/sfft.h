@@ -378,8 +378,26 @@ typedef enum {
 int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, void *d_diff,
                        sfft_stream_t stream);
 
-/* The plan's launch shapes {rows, images, row pairs, solve grid}; 0 = built-in choice. */
+/*
+ * Launch shapes, SFFT_TUNING_LEN values, 0 = built-in choice:
+ *   [0] rows per block of the row FFT (0 or a power of two <= 16; capped by
+ *       the block size),
+ *   [1] images per block of the column FFT (0..4),
+ *   [2] row pairs per block of the inverse row FFT (0..4),
+ *   [3] blocks of the solve grid (0 or up to 512; used only when it exceeds
+ *       the systems in the launch and is at most the built-in grid).
+ */
+#define SFFT_TUNING_LEN 4
+
+/* The plan's launch shapes (shapes: SFFT_TUNING_LEN values, written). */
 int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes);
+
+/*
+ * Set the plan's launch shapes (SFFT_TUNING_LEN values, read), e.g. to
+ * reproduce an earlier sfft_plan_autotune.  Results do not depend on them.
+ * SFFT_ERR_INVALID for a value outside the ranges above (nothing changed).
+ */
+int sfft_plan_set_tuning(sfft_plan_t plan, const int32_t *shapes);
 
 /* Number of kernels this plan has enqueued since it was created. */
 int sfft_plan_launch_count(sfft_plan_t plan, uint64_t *count);

@@ -108,6 +108,7 @@ def library():
         lib.sfft_pool_usage.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32)]
         lib.sfft_plan_autotune.argtypes = [vp, vp, vp, vp, vp]
         lib.sfft_plan_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.sfft_plan_set_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
         _lib = lib
@@ -343,11 +344,24 @@ def sfft_plan_autotune(plan, d_ref, d_sci, d_diff, stream=None):
     _check(library().sfft_plan_autotune(plan, _p(d_ref), _p(d_sci), _p(d_diff), _s(stream)), "sfft_plan_autotune")
 
 
+SFFT_TUNING_LEN = 4
+TUNING_KEYS = ("rows_per_block", "images_per_block", "row_pairs_per_block", "solve_grid")
+
+
 def sfft_plan_tuning(plan):
-    out = (ctypes.c_int32 * 4)()
+    out = (ctypes.c_int32 * SFFT_TUNING_LEN)()
     _check(library().sfft_plan_tuning(plan, out), "sfft_plan_tuning")
-    return {"rows_per_block": out[0], "images_per_block": out[1], "row_pairs_per_block": out[2],
-            "solve_grid": out[3]}
+    return dict(zip(TUNING_KEYS, list(out)))
+
+
+def sfft_plan_set_tuning(plan, shapes):
+    """shapes: a dict with TUNING_KEYS (missing keys: 0) or SFFT_TUNING_LEN integers."""
+    if isinstance(shapes, dict):
+        shapes = [int(shapes.get(k, 0)) for k in TUNING_KEYS]
+    if len(shapes) != SFFT_TUNING_LEN:
+        raise ValueError(f"sfft_plan_set_tuning: {SFFT_TUNING_LEN} values expected")
+    _check(library().sfft_plan_set_tuning(plan, (ctypes.c_int32 * SFFT_TUNING_LEN)(*shapes)),
+           "sfft_plan_set_tuning")
 
 
 def sfft_plan_launch_count(plan):

@@ -154,8 +154,22 @@ void plan_free(Plan *p) {
 // image size, types and kernel degree (server slots, pool lanes).
 struct TuneEntry {
     int n0, n1, dtype, precision, dk;
-    int tr, gi, ng, sgrid;
+    int32_t shapes[SFFT_TUNING_LEN];
 };
+
+static void get_shapes(const Plan *p, int32_t *v) {
+    v[0] = p->tune_tr;
+    v[1] = p->tune_gi;
+    v[2] = p->tune_ng;
+    v[3] = p->tune_sgrid;
+}
+
+static void set_shapes(Plan *p, const int32_t *v) {
+    p->tune_tr = v[0];
+    p->tune_gi = v[1];
+    p->tune_ng = v[2];
+    p->tune_sgrid = v[3];
+}
 constexpr int kTuneCache = 64;
 static TuneEntry g_tune[kTuneCache];
 static int g_ntune = 0;
@@ -168,12 +182,7 @@ static bool tune_key_eq(const TuneEntry &e, const sfft_config *c) {
 static void tune_lookup(Plan *p) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (int k = 0; k < g_ntune; ++k)
-        if (tune_key_eq(g_tune[k], &p->cfg)) {
-            p->tune_tr = g_tune[k].tr;
-            p->tune_gi = g_tune[k].gi;
-            p->tune_ng = g_tune[k].ng;
-            p->tune_sgrid = g_tune[k].sgrid;
-        }
+        if (tune_key_eq(g_tune[k], &p->cfg)) set_shapes(p, g_tune[k].shapes);
 }
 
 static void tune_store(const Plan *p) {
@@ -185,7 +194,8 @@ static void tune_store(const Plan *p) {
         else ++g_ntune;
     }
     const sfft_config &c = p->cfg;
-    g_tune[k] = TuneEntry{c.n0, c.n1, c.dtype, c.precision, c.dk, p->tune_tr, p->tune_gi, p->tune_ng, p->tune_sgrid};
+    g_tune[k] = TuneEntry{c.n0, c.n1, c.dtype, c.precision, c.dk, {}};
+    get_shapes(p, g_tune[k].shapes);
 }
 
 int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
@@ -552,7 +562,7 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
         int stage;
         int cand[5];
     } knobs[] = {
-        {&p->tune_tr, SFFT_STAGE_ROWS, {0, 8, 4, 2, 1}},
+        {&p->tune_tr, SFFT_STAGE_ROWS, {0, 4, 2, 1, -1}},
         {&p->tune_gi, SFFT_STAGE_COLS, {0, 3, 2, 1, -1}},
         {&p->tune_ng, SFFT_STAGE_SUBTRACT, {0, 2, 1, -1, -1}},
         {&p->tune_sgrid, SFFT_STAGE_SOLVE, {0, sms, -1, -1, -1}},
@@ -583,11 +593,17 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
 
 int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes) {
     if (!plan || !shapes) return SFFT_ERR_INVALID;
-    const Plan *p = (const Plan *)plan;
-    shapes[0] = p->tune_tr;
-    shapes[1] = p->tune_gi;
-    shapes[2] = p->tune_ng;
-    shapes[3] = p->tune_sgrid;
+    get_shapes((const Plan *)plan, shapes);
+    return SFFT_OK;
+}
+
+int sfft_plan_set_tuning(sfft_plan_t plan, const int32_t *shapes) {
+    if (!plan || !shapes) return SFFT_ERR_INVALID;
+    const int32_t tr = shapes[0];
+    if (tr < 0 || tr > 16 || (tr & (tr - 1)) != 0) return SFFT_ERR_INVALID;  // 0 or a power of two
+    if (shapes[1] < 0 || shapes[1] > 4 || shapes[2] < 0 || shapes[2] > 4) return SFFT_ERR_INVALID;
+    if (shapes[3] < 0 || shapes[3] > kMaxSolveGrid) return SFFT_ERR_INVALID;
+    set_shapes((Plan *)plan, shapes);
     return SFFT_OK;
 }
 
