@@ -44,16 +44,17 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         u8p = ctypes.POINTER(ctypes.c_uint8)
         i = ctypes.c_int
-        lib.orc_num_unknowns.argtypes = [i, i, i, i, i]
-        lib.orc_build_system.argtypes = [i, i, i, i, i, i, i, dp, dp, u8p, dp, dp]
-        lib.orc_system_entries.argtypes = [i, i, i, i, i, i, i, dp, dp, u8p, i, ip, ip, dp]
+        lib.orc_num_unknowns.argtypes = [ip]
+        lib.orc_build_system.argtypes = [ip, dp, dp, u8p, dp, dp]
+        lib.orc_system_entries.argtypes = [ip, dp, dp, u8p, i, ip, ip, dp]
         lib.orc_cholesky_solve.argtypes = [i, dp, dp, dp]
-        lib.orc_subtract.argtypes = [i, i, i, i, i, i, i, dp, dp, dp, dp]
-        lib.orc_subtract_pixels.argtypes = [i, i, i, i, i, i, i, dp, dp, dp, i,
-                                            ctypes.POINTER(ctypes.c_longlong), dp]
+        lib.orc_subtract.argtypes = [ip, dp, dp, dp, dp]
+        lib.orc_subtract_pixels.argtypes = [ip, dp, dp, dp, i, ctypes.POINTER(ctypes.c_longlong), dp]
         lib.orc_lag_sum.argtypes = [i, i, dp, dp, i, i]
         lib.orc_lag_sum.restype = ctypes.c_double
-        lib.orc_decode_unknown.argtypes = [i, i, i, i, i, i, ip]
+        lib.orc_decode_unknown.argtypes = [ip, i, ip]
+        lib.orc_bspline.argtypes = [i, i, i, ctypes.c_double]
+        lib.orc_bspline.restype = ctypes.c_double
         lib.orc_threads.argtypes = []
         _lib = lib
     return _lib
@@ -61,7 +62,13 @@ def _load():
 
 @dataclass(frozen=True)
 class OracleConfig:
-    """Fit parameters of one image pair (Sec. 3.3, Table A1)."""
+    """Fit parameters of one image pair (Sec. 3.3, Table A1).
+
+    basis "poly": polynomial kernel and background variation of degrees dk,
+    db (Eq. 2, 6).  basis "bspline": tensor-product B-splines (Eq. 8-9) of
+    degree kdeg with kint interior knots for the kernel and bdeg, bint for
+    the background (dk, db unused), on clamped uniform knots over the
+    normalised coordinates."""
     n0: int
     n1: int
     w0: int
@@ -69,9 +76,18 @@ class OracleConfig:
     dk: int
     db: int
     const_phot_ratio: bool
+    basis: str = "poly"
+    kdeg: int = 0
+    kint: int = 0
+    bdeg: int = 0
+    bint: int = 0
 
     def args(self):
-        return (self.n0, self.n1, self.w0, self.w1, self.dk, self.db, int(self.const_phot_ratio))
+        """The 12-int configuration array of sfft_oracle.c."""
+        v = (self.n0, self.n1, self.w0, self.w1, self.dk, self.db, int(self.const_phot_ratio),
+             {"poly": 0, "bspline": 1}[self.basis], self.kdeg, self.kint, self.bdeg, self.bint)
+        a = (ctypes.c_int * 12)(*v)
+        return (a,)
 
 
 def _f64(a):
@@ -94,13 +110,17 @@ def threads() -> int:
 
 
 def num_unknowns(cfg: OracleConfig) -> int:
-    return int(_load().orc_num_unknowns(cfg.w0, cfg.w1, cfg.dk, cfg.db, int(cfg.const_phot_ratio)))
+    return int(_load().orc_num_unknowns(*cfg.args()))
+
+
+def bspline(deg: int, nint: int, i: int, u: float) -> float:
+    """B-spline basis function i (degree deg, nint interior knots, clamped uniform on [-1, 1]) at u."""
+    return float(_load().orc_bspline(deg, nint, i, float(u)))
 
 
 def decode_unknown(cfg: OracleConfig, u: int):
     out = np.zeros(4, dtype=np.int32)
-    rc = _load().orc_decode_unknown(cfg.w0, cfg.w1, cfg.dk, cfg.db, int(cfg.const_phot_ratio), u,
-                                    _ptr(out, ctypes.c_int))
+    rc = _load().orc_decode_unknown(*cfg.args(), u, _ptr(out, ctypes.c_int))
     if rc:
         raise ValueError(f"unknown index {u} out of range")
     return bool(out[0]), int(out[1]), int(out[2]), int(out[3])

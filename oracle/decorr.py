@@ -19,20 +19,33 @@ import numpy as np
 from . import bruteforce
 
 
-def kernel_image(x, w0, w1, dk, db, const_phot_ratio, xt0, yt0):
+def term_weight_at(label, xt0, yt0, spline=None):
+    """Weight of a kernel term (label as in bruteforce.kernel_terms) at one
+    normalised position: xt0^i yt0^j (Eq. 6), B_i(xt0) B_j(yt0) (Eq. 8), or 1."""
+    if label[0] == "one":
+        return 1.0
+    if label[0] == "spl":
+        kdeg, kint = spline[0], spline[1]
+        return float(bruteforce.spline_basis(kdeg, kint, [xt0])[label[1], 0] *
+                     bruteforce.spline_basis(kdeg, kint, [yt0])[label[2], 0])
+    i, j = label
+    return xt0 ** i * yt0 ** j
+
+
+def kernel_image(x, w0, w1, dk, db, const_phot_ratio, xt0, yt0, spline=None):
     """Matching kernel at (xt0, yt0) as an image k[alpha + w0, beta + w1].
 
     With the delta basis of Eq. 3-4, K_ab = delta(a, b) - delta(0, 0) for
     (a, b) != 0 and K_00 = delta(0, 0), so a coefficient of offset (a, b) != 0
     adds at the offset and subtracts at the centre; Eq. 6 weights the
-    coefficients of term (i, j) by xt0^i yt0^j.
+    coefficients of term (i, j) by xt0^i yt0^j (Eq. 8: by B_i(xt0) B_j(yt0)).
     """
     k = np.zeros((2 * w0 + 1, 2 * w1 + 1))
-    for u, unk in enumerate(bruteforce.unknown_list(w0, w1, dk, db, const_phot_ratio)):
+    for u, unk in enumerate(bruteforce.unknown_list(w0, w1, dk, db, const_phot_ratio, spline)):
         if unk[0] != "k":
             continue
-        (i, j), (a, b) = unk[1], unk[2]
-        c = x[u] * xt0 ** i * yt0 ** j
+        (a, b) = unk[2]
+        c = x[u] * term_weight_at(unk[1], xt0, yt0, spline)
         if (a, b) == (0, 0):
             k[w0, w1] += c
         else:

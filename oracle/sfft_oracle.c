@@ -32,6 +32,15 @@
  *     from -w0 to w0 outer; with a constant photometric ratio the offsets
  *     (alpha,beta)=(0,0) of terms other than (0,0) are omitted; then the
  *     background terms (p,q) in the same monomial order.
+ *   - B-spline bases (Eq. 7-9): the same basis along x and y, on the
+ *     normalised coordinates, clamped uniform knots on [-1, 1] (degree k,
+ *     n_int interior knots, K = n_int + k + 1 functions, evaluated by the
+ *     Cox-de Boor recursion; the right end x = 1 belongs to the last knot
+ *     span).  Kernel terms (i, j), i, j < K, ordered i outer, weight
+ *     B_i(xt) B_j(yt); background terms (p, q) likewise with their own degree
+ *     and knots.  With a constant photometric ratio the (0,0) offset of the
+ *     kernel has one unknown whose weight is 1 (the sum of all B_i B_j), put
+ *     first as term 0; the spline terms then omit that offset.
  *
  * Pins (tests, on the CPU): brute-force design matrix and least squares on
  * tiny images, the closed-form w=0 regression, the one-pixel shift case,
@@ -49,13 +58,48 @@
 #define ORC_ERR_NOMEM (-2)
 #define ORC_ERR_NOT_PD (-4)
 
+/* Configuration as passed in by the caller: 12 ints
+ *   n0, n1, w0, w1, dk, db, cpr, basis (0 polynomial, 1 B-spline),
+ *   kdeg, kint (kernel spline degree, interior knots),
+ *   bdeg, bint (background spline degree, interior knots). */
+#define ORC_CFG_LEN 12
+
 typedef struct {
     int n0, n1, w0, w1, dk, db, cpr;
+    int basis, kdeg, kint, bdeg, bint;
 } orc_cfg;
+
+static orc_cfg cfg_from(const int *v) {
+    orc_cfg c;
+    c.n0 = v[0]; c.n1 = v[1]; c.w0 = v[2]; c.w1 = v[3]; c.dk = v[4]; c.db = v[5];
+    c.cpr = v[6] ? 1 : 0; c.basis = v[7]; c.kdeg = v[8]; c.kint = v[9]; c.bdeg = v[10]; c.bint = v[11];
+    return c;
+}
 
 /* ---- indexing ---------------------------------------------------------- */
 
 static int n_terms(int d) { return (d + 1) * (d + 2) / 2; }
+
+/* number of B-spline functions per axis */
+static int n_spl(int deg, int nint) { return nint + deg + 1; }
+
+/* kernel terms: polynomial terms, or the B-spline products (plus the constant
+ * term 0 when the photometric ratio is constant) */
+static int kernel_terms(const orc_cfg *c) {
+    if (c->basis == 0) return n_terms(c->dk);
+    int K = n_spl(c->kdeg, c->kint);
+    return K * K + (c->cpr ? 1 : 0);
+}
+
+static int background_terms(const orc_cfg *c) {
+    if (c->basis == 0) return n_terms(c->db);
+    int K = n_spl(c->bdeg, c->bint);
+    return K * K;
+}
+
+/* which offsets a kernel term carries: the (0,0) offset and/or the others */
+static int term_has00(const orc_cfg *c, int t) { return c->cpr ? t == 0 : 1; }
+static int term_hasother(const orc_cfg *c, int t) { return (c->basis == 1 && c->cpr) ? t != 0 : 1; }
 
 /* k-th monomial (i,j) with i+j <= d, ordered by total degree, then i descending */
 static void term_ij(int k, int *i, int *j) {
@@ -66,81 +110,155 @@ static void term_ij(int k, int *i, int *j) {
     *j = off;
 }
 
-static double coord(int x, int n) { return (2.0 * x - (n - 1)) / (double)(n - 1); }
-
 static double ipow(double v, int e) {
     double r = 1.0;
     for (int k = 0; k < e; k++) r *= v;
     return r;
 }
 
+static double coord(int x, int n) { return (2.0 * x - (n - 1)) / (double)(n - 1); }
+
+/* knot r of the clamped uniform knot vector on [-1, 1] (r = 0 .. nint + 2 deg + 1) */
+static double knot(int deg, int nint, int r) {
+    if (r <= deg) return -1.0;
+    if (r >= nint + deg + 1) return 1.0;
+    return -1.0 + 2.0 * (double)(r - deg) / (double)(nint + 1);
+}
+
+/* B-spline basis function i of degree deg at u in [-1, 1], by the Cox-de Boor
+ * recursion B_{i,0} = [t_i <= u < t_{i+1}],
+ * B_{i,d} = (u - t_i)/(t_{i+d} - t_i) B_{i,d-1} + (t_{i+d+1} - u)/(t_{i+d+1} - t_{i+1}) B_{i+1,d-1},
+ * with 0/0 terms taken as 0 and u = 1 placed in the last non-empty span. */
+static double bspline(int deg, int nint, int i, double u) {
+    int K = n_spl(deg, nint);
+    double b[64];
+    if (i < 0 || i >= K || deg + 1 > 32) return 0.0;
+    /* degree 0 functions i .. i + deg (those that feed B_{i,deg}) */
+    for (int r = 0; r <= deg; r++) {
+        int q = i + r;
+        double t0 = knot(deg, nint, q), t1 = knot(deg, nint, q + 1);
+        int in = (u >= t0 && u < t1);
+        if (u >= 1.0 && t1 >= 1.0 && t0 < 1.0) in = 1;  /* right end: last non-empty span */
+        b[r] = in ? 1.0 : 0.0;
+    }
+    for (int d = 1; d <= deg; d++) {
+        for (int r = 0; r + d <= deg; r++) {
+            int q = i + r;
+            double tq = knot(deg, nint, q), tqd = knot(deg, nint, q + d);
+            double tq1 = knot(deg, nint, q + 1), tqd1 = knot(deg, nint, q + d + 1);
+            double left = (tqd > tq) ? (u - tq) / (tqd - tq) * b[r] : 0.0;
+            double right = (tqd1 > tq1) ? (tqd1 - u) / (tqd1 - tq1) * b[r + 1] : 0.0;
+            b[r] = left + right;
+        }
+    }
+    return b[0];
+}
+
+double orc_bspline(int deg, int nint, int i, double u) { return bspline(deg, nint, i, u); }
+
+/* weight of kernel term t at pixel (x, y) */
+static double kernel_weight(const orc_cfg *c, int t, int x, int y) {
+    double xt = coord(x, c->n0), yt = coord(y, c->n1);
+    if (c->basis == 0) {
+        int i, j;
+        term_ij(t, &i, &j);
+        return ipow(xt, i) * ipow(yt, j);
+    }
+    if (c->cpr) {
+        if (t == 0) return 1.0;
+        t -= 1;
+    }
+    int K = n_spl(c->kdeg, c->kint);
+    return bspline(c->kdeg, c->kint, t / K, xt) * bspline(c->kdeg, c->kint, t % K, yt);
+}
+
+/* weight of background term s at pixel (x, y) */
+static double background_weight(const orc_cfg *c, int s, int x, int y) {
+    double xt = coord(x, c->n0), yt = coord(y, c->n1);
+    if (c->basis == 0) {
+        int p, q;
+        term_ij(s, &p, &q);
+        return ipow(xt, p) * ipow(yt, q);
+    }
+    int K = n_spl(c->bdeg, c->bint);
+    return bspline(c->bdeg, c->bint, s / K, xt) * bspline(c->bdeg, c->bint, s % K, yt);
+}
+
 static int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 
-int orc_num_unknowns(int w0, int w1, int dk, int db, int cpr) {
-    int L = (2 * w0 + 1) * (2 * w1 + 1);
-    int nk = n_terms(dk), nb = n_terms(db);
-    if (cpr) return nk * (L - 1) + 1 + nb;
-    return nk * L + nb;
+/* unknowns of kernel term t: its (0,0) offset and/or the L-1 others */
+static int term_unknowns(const orc_cfg *c, int t) {
+    int L = (2 * c->w0 + 1) * (2 * c->w1 + 1);
+    return (term_has00(c, t) ? 1 : 0) + (term_hasother(c, t) ? L - 1 : 0);
+}
+
+static int num_unknowns(const orc_cfg *c) {
+    int n = 0, nk = kernel_terms(c);
+    for (int t = 0; t < nk; t++) n += term_unknowns(c, t);
+    return n + background_terms(c);
+}
+
+int orc_num_unknowns(const int *cfg) {
+    orc_cfg c = cfg_from(cfg);
+    return num_unknowns(&c);
 }
 
 /* Decode unknown index u into (is_kernel, term, alpha, beta) */
 static void decode_unknown(const orc_cfg *c, int u, int *is_k, int *t, int *a, int *b) {
     int L1 = 2 * c->w1 + 1;
     int L = (2 * c->w0 + 1) * L1;
-    int nk = n_terms(c->dk);
-    int per = c->cpr ? L - 1 : L;      /* offsets kept for terms other than (0,0) */
     int centre = (L - 1) / 2;          /* row-major position of (alpha,beta)=(0,0) */
-    int off;
-    if (u < L) {
-        *t = 0;
-        off = u;
-    } else if (u - L < (nk - 1) * per) {
-        int v = u - L;
-        *t = 1 + v / per;
-        off = v % per;
-        if (c->cpr && off >= centre) off += 1;
-    } else {
-        *is_k = 0; *t = u - L - (nk - 1) * per; *a = 0; *b = 0;
-        return;
+    int nk = kernel_terms(c);
+    for (int k = 0; k < nk; k++) {
+        int cnt = term_unknowns(c, k);
+        if (u < cnt) {
+            int off;
+            if (!term_hasother(c, k)) off = centre;          /* only the (0,0) offset */
+            else if (!term_has00(c, k)) off = u >= centre ? u + 1 : u;  /* all but (0,0) */
+            else off = u;
+            *is_k = 1;
+            *t = k;
+            *a = off / L1 - c->w0;
+            *b = off % L1 - c->w1;
+            return;
+        }
+        u -= cnt;
     }
-    *is_k = 1;
-    *a = off / L1 - c->w0;
-    *b = off % L1 - c->w1;
+    *is_k = 0; *t = u; *a = 0; *b = 0;
 }
 
 static int check_cfg(const orc_cfg *c) {
     if (c->n0 < 2 || c->n1 < 2) return ORC_ERR_INVALID;
     if (c->w0 < 0 || c->w1 < 0 || c->dk < 0 || c->db < 0) return ORC_ERR_INVALID;
     if (2 * c->w0 + 1 > c->n0 || 2 * c->w1 + 1 > c->n1) return ORC_ERR_INVALID;
+    if (c->basis != 0 && c->basis != 1) return ORC_ERR_INVALID;
+    if (c->basis == 1 && (c->kdeg < 0 || c->kint < 0 || c->bdeg < 0 || c->bint < 0 || c->kdeg > 8 ||
+                          c->bdeg > 8 || c->kint > 30 || c->bint > 30))
+        return ORC_ERR_INVALID;
     return ORC_OK;
 }
 
 /* ---- images ------------------------------------------------------------ */
 
-/* g_t = xt^i yt^j * Rm, for every kernel term t (Eq. 10-11: R^{ij} = T^{ij} R) */
+/* g_t = w_t * Rm for every kernel term t, w_t = xt^i yt^j (Eq. 10-11:
+ * R^{ij} = T^{ij} R) or B_i(xt) B_j(yt) (Eq. 8) */
 static double *make_weighted(const orc_cfg *c, const double *Rm, int t) {
     size_t P = (size_t)c->n0 * c->n1;
     double *g = (double *)malloc(P * sizeof(double));
     if (!g) return NULL;
-    int i, j;
-    term_ij(t, &i, &j);
     for (int x = 0; x < c->n0; x++)
         for (int y = 0; y < c->n1; y++)
-            g[(size_t)x * c->n1 + y] = ipow(coord(x, c->n0), i) * ipow(coord(y, c->n1), j) *
-                                       Rm[(size_t)x * c->n1 + y];
+            g[(size_t)x * c->n1 + y] = kernel_weight(c, t, x, y) * Rm[(size_t)x * c->n1 + y];
     return g;
 }
 
-/* T^{pq} = xt^p yt^q (Eq. 2) */
+/* background basis image T^{pq} = xt^p yt^q (Eq. 2) or B'_p(xt) B'_q(yt) (Eq. 9) */
 static double *make_poly(const orc_cfg *c, int s) {
     size_t P = (size_t)c->n0 * c->n1;
     double *T = (double *)malloc(P * sizeof(double));
     if (!T) return NULL;
-    int p, q;
-    term_ij(s, &p, &q);
     for (int x = 0; x < c->n0; x++)
-        for (int y = 0; y < c->n1; y++)
-            T[(size_t)x * c->n1 + y] = ipow(coord(x, c->n0), p) * ipow(coord(y, c->n1), q);
+        for (int y = 0; y < c->n1; y++) T[(size_t)x * c->n1 + y] = background_weight(c, s, x, y);
     return T;
 }
 
@@ -213,8 +331,8 @@ static int make_images(tables *tb, const orc_cfg *c, const double *R, const doub
                        const uint8_t *mask) {
     memset(tb, 0, sizeof(*tb));
     tb->c = *c;
-    tb->nk = n_terms(c->dk);
-    tb->nb = n_terms(c->db);
+    tb->nk = kernel_terms(c);
+    tb->nb = background_terms(c);
     tb->h0 = 2 * c->w0;
     tb->h1 = 2 * c->w1;
     double *Rm = masked_copy(c, R, mask);
@@ -323,15 +441,15 @@ static double rhs_from_tables(const tables *tb, int row) {
 }
 
 /* Full system: M (n*n row-major) and rhs (n) */
-int orc_build_system(int n0, int n1, int w0, int w1, int dk, int db, int cpr, const double *R,
-                     const double *S, const uint8_t *mask, double *M, double *rhs) {
-    orc_cfg c = {n0, n1, w0, w1, dk, db, cpr ? 1 : 0};
+int orc_build_system(const int *cfg, const double *R, const double *S, const uint8_t *mask, double *M,
+                     double *rhs) {
+    orc_cfg c = cfg_from(cfg);
     int rc = check_cfg(&c);
     if (rc) return rc;
     tables tb;
     if ((rc = make_images(&tb, &c, R, S, mask))) return rc;
     if ((rc = fill_tables(&tb))) { free_tables(&tb); return rc; }
-    int n = orc_num_unknowns(w0, w1, dk, db, c.cpr);
+    int n = num_unknowns(&c);
 #pragma omp parallel for schedule(static)
     for (int r = 0; r < n; r++) {
         for (int k = 0; k < n; k++) M[(size_t)r * n + k] = entry_from_tables(&tb, r, k);
@@ -353,16 +471,15 @@ static double lag_value(const tables *tb, int kind, int t, int u, int r0, int r1
     return orc_lag_sum(c->n0, c->n1, tb->g[t], tb->Sm, r0, r1);
 }
 
-int orc_system_entries(int n0, int n1, int w0, int w1, int dk, int db, int cpr, const double *R,
-                       const double *S, const uint8_t *mask, int count, const int *rows,
-                       const int *cols, double *out) {
-    orc_cfg c = {n0, n1, w0, w1, dk, db, cpr ? 1 : 0};
+int orc_system_entries(const int *cfg, const double *R, const double *S, const uint8_t *mask, int count,
+                       const int *rows, const int *cols, double *out) {
+    orc_cfg c = cfg_from(cfg);
     int rc = check_cfg(&c);
     if (rc) return rc;
     tables tb;
     if ((rc = make_images(&tb, &c, R, S, mask))) return rc;
-    int n = orc_num_unknowns(w0, w1, dk, db, c.cpr);
-    size_t P = (size_t)n0 * n1;
+    int n = num_unknowns(&c);
+    size_t P = (size_t)c.n0 * c.n1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < count; q++) {
         int row = rows[q], col = cols[q];
@@ -452,68 +569,60 @@ int orc_cholesky_solve(int n, const double *M, const double *rhs, double *x) {
 
 /* ---- subtract (Eq. 12) -------------------------------------------------- */
 
-/* D(x) at one pixel: S - sum_{t,ab} a_{t,ab} (g_t o K_ab)(x) - sum_pq b_pq T^pq(x),
+/* D(x) at one pixel: S - sum_{t,ab} a_{t,ab} (g_t o K_ab)(x) - sum_s b_s T^s(x),
  * with (g o K_ab)(x) = g(x - ab) - g(x) for ab != 0 and g(x) for ab = 0. */
 static double diff_pixel(const orc_cfg *c, const double *R, const double *S, const double *x,
                          int px, int py) {
-    int nk = n_terms(c->dk), nb = n_terms(c->db);
+    int nk = kernel_terms(c), nb = background_terms(c);
     double d = S[(size_t)px * c->n1 + py];
     int u = 0;
     for (int t = 0; t < nk; t++) {
-        int i, j;
-        term_ij(t, &i, &j);
-        double g0 = ipow(coord(px, c->n0), i) * ipow(coord(py, c->n1), j) * R[(size_t)px * c->n1 + py];
+        double g0 = kernel_weight(c, t, px, py) * R[(size_t)px * c->n1 + py];
         for (int a = -c->w0; a <= c->w0; a++) {
             for (int b = -c->w1; b <= c->w1; b++) {
-                if (c->cpr && t != 0 && a == 0 && b == 0) continue;
+                int zero = (a == 0 && b == 0);
+                if (zero ? !term_has00(c, t) : !term_hasother(c, t)) continue;
                 double coef = x[u++];
-                if (a == 0 && b == 0) { d -= coef * g0; continue; }
+                if (zero) { d -= coef * g0; continue; }
                 int qx = imod(px - a, c->n0), qy = imod(py - b, c->n1);
-                double gs = ipow(coord(qx, c->n0), i) * ipow(coord(qy, c->n1), j) *
-                            R[(size_t)qx * c->n1 + qy];
+                double gs = kernel_weight(c, t, qx, qy) * R[(size_t)qx * c->n1 + qy];
                 d -= coef * (gs - g0);
             }
         }
     }
-    for (int s = 0; s < nb; s++) {
-        int p, q;
-        term_ij(s, &p, &q);
-        d -= x[u++] * ipow(coord(px, c->n0), p) * ipow(coord(py, c->n1), q);
-    }
+    for (int s = 0; s < nb; s++) d -= x[u++] * background_weight(c, s, px, py);
     return d;
 }
 
-int orc_subtract(int n0, int n1, int w0, int w1, int dk, int db, int cpr, const double *R,
-                 const double *S, const double *x, double *D) {
-    orc_cfg c = {n0, n1, w0, w1, dk, db, cpr ? 1 : 0};
+int orc_subtract(const int *cfg, const double *R, const double *S, const double *x, double *D) {
+    orc_cfg c = cfg_from(cfg);
     int rc = check_cfg(&c);
     if (rc) return rc;
 #pragma omp parallel for schedule(static)
-    for (int px = 0; px < n0; px++)
-        for (int py = 0; py < n1; py++) D[(size_t)px * n1 + py] = diff_pixel(&c, R, S, x, px, py);
+    for (int px = 0; px < c.n0; px++)
+        for (int py = 0; py < c.n1; py++) D[(size_t)px * c.n1 + py] = diff_pixel(&c, R, S, x, px, py);
     return ORC_OK;
 }
 
 /* D at a list of flat pixel indices */
-int orc_subtract_pixels(int n0, int n1, int w0, int w1, int dk, int db, int cpr, const double *R,
-                        const double *S, const double *x, int count, const long long *pix,
-                        double *out) {
-    orc_cfg c = {n0, n1, w0, w1, dk, db, cpr ? 1 : 0};
+int orc_subtract_pixels(const int *cfg, const double *R, const double *S, const double *x, int count,
+                        const long long *pix, double *out) {
+    orc_cfg c = cfg_from(cfg);
     int rc = check_cfg(&c);
     if (rc) return rc;
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < count; k++) {
         long long p = pix[k];
-        if (p < 0 || p >= (long long)n0 * n1) { out[k] = NAN; continue; }
-        out[k] = diff_pixel(&c, R, S, x, (int)(p / n1), (int)(p % n1));
+        if (p < 0 || p >= (long long)c.n0 * c.n1) { out[k] = NAN; continue; }
+        out[k] = diff_pixel(&c, R, S, x, (int)(p / c.n1), (int)(p % c.n1));
     }
     return ORC_OK;
 }
 
 /* Decoded unknown: kind (1 kernel, 0 background), term, alpha, beta */
-int orc_decode_unknown(int w0, int w1, int dk, int db, int cpr, int u, int *out4) {
-    orc_cfg c = {2, 2, w0, w1, dk, db, cpr ? 1 : 0};
-    int n = orc_num_unknowns(w0, w1, dk, db, c.cpr);
+int orc_decode_unknown(const int *cfg, int u, int *out4) {
+    orc_cfg c = cfg_from(cfg);
+    int n = num_unknowns(&c);
     if (u < 0 || u >= n) return ORC_ERR_INVALID;
     decode_unknown(&c, u, &out4[0], &out4[1], &out4[2], &out4[3]);
     return ORC_OK;
