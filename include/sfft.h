@@ -24,6 +24,18 @@
  *   nk*(L-1) + 1 + nb with a constant photometric ratio, where L =
  *   (2w0+1)(2w1+1), nk = (dk+1)(dk+2)/2, nb = (db+1)(db+2)/2.
  *
+ * B-spline basis (Eq. 7-9, cfg.basis = SFFT_BASIS_BSPLINE): the polynomials
+ * are replaced by tensor products of B-splines on the normalised
+ * coordinates, the same basis along x and y, with clamped uniform knots on
+ * [-1, 1]: degree kdeg and kint interior knots give K = kint + kdeg + 1
+ * functions B_0..B_(K-1) per axis (the right end xt = 1 belongs to the last
+ * knot span).  Kernel terms are (i,j), i,j < K, ordered i outer, weight
+ * B_i(xt) B_j(yt), each with all L offsets; with a constant photometric
+ * ratio a first term of weight 1 carries the (0,0) offset alone (one
+ * unknown: the kernel sum) and the K*K spline terms omit that offset.  The
+ * background terms are (p,q), p,q < K' = bint + bdeg + 1, p outer, weight
+ * B'_p(xt) B'_q(yt).  n = K*K*L + K'*K', or 1 + K*K*(L-1) + K'*K'.
+ *
  * Memory: every pointer named d_* is device memory owned by the caller; h_*
  * is host memory owned by the caller (page-locked for asynchronous copies).
  * A plan owns its workspace; it is not thread-safe and serves one pair at a
@@ -66,15 +78,23 @@ typedef enum {
                             the Jacobi-scaled matrix, FP64 residual refinement */
 } sfft_precision;
 
+typedef enum {
+    SFFT_BASIS_POLY = 0,    /* polynomial variation (Eq. 2 and 6), degrees dk and db */
+    SFFT_BASIS_BSPLINE = 1  /* tensor-product B-splines (Eq. 7-9), see the unknown order above */
+} sfft_basis;
+
 /* Fit parameters of one image pair (Sec. 3.3 and Table A1). */
 typedef struct {
-    int32_t n0, n1;           /* image size; each a power of two in [16, 4096] */
+    int32_t n0, n1;           /* image size, each in [16, 4096] (any length) */
     int32_t w0, w1;           /* kernel half-widths: L0 = 2*w0+1, L1 = 2*w1+1 (Eq. 3-4) */
-    int32_t dk;               /* kernel polynomial degree D_K (Eq. 6), 0..3 */
-    int32_t db;               /* background polynomial degree D_B (Eq. 2), 0..3 */
+    int32_t dk;               /* kernel polynomial degree D_K (Eq. 6), 0..3; 0 for B-splines */
+    int32_t db;               /* background polynomial degree D_B (Eq. 2), 0..3; 0 for B-splines */
     int32_t const_phot_ratio; /* 1: kernel sum constant over the field (Sec. 2.2) */
     int32_t dtype;            /* sfft_dtype of the images R, S and of the output D */
     int32_t precision;        /* sfft_precision */
+    int32_t basis;            /* sfft_basis; the fields below are used by SFFT_BASIS_BSPLINE only */
+    int32_t kdeg, kint;       /* kernel B-splines: degree 0..3, interior knots; K = kint+kdeg+1 <= 6 */
+    int32_t bdeg, bint;       /* background B-splines: degree 0..3, interior knots; K' <= 6 */
 } sfft_config;
 
 /* Written by sfft_solve in device memory. */
@@ -368,9 +388,9 @@ typedef enum {
  * Autotuning of launch shapes (no counterpart in the paper): runs one pair on
  * the given device buffers with sfft_run_pair, then times each tunable stage
  * (sfft_replay_stage) over candidate launch shapes and keeps the fastest:
- * rows per block of the row FFT, images per block of the column FFT, row
- * pairs per block of the inverse row FFT, and the solve grid (one or two
- * blocks per SM).  The shapes change how the work is split into blocks, not
+ * rows per block of the row FFT, images per block of the column FFT and
+ * row pairs per block of the inverse row FFT (the solve grid stays as set:
+ * a single system's time does not predict batched solves).  The shapes change how the work is split into blocks, not
  * the arithmetic, so results are unchanged.  They stay with the plan and are
  * remembered for later plans (and server slots, pool lanes) of the same image
  * size, types and D_K in this process.  Synchronises the stream.

@@ -57,9 +57,11 @@ class SfftPlan:
     """One plan (workspace + tables) for a fixed image size and fit configuration."""
 
     def __init__(self, n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed",
-                 stream=None):
+                 stream=None, spline=None):
+        """spline: None (polynomial basis of degrees dk, db) or (kdeg, kint, bdeg, bint) for
+        tensor-product B-splines (Eq. 7-9), with dk = db = 0."""
         torch = _torch()
-        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision, spline)
         self.n = sfft_num_unknowns(self.cfg)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = sfft_plan_create(self.cfg, self.stream)
@@ -179,9 +181,9 @@ class SfftServer:
     """
 
     def __init__(self, n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed", depth=2,
-                 batch=1):
+                 batch=1, spline=None):
         torch = _torch()
-        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision, spline)
         self.n = sfft_num_unknowns(self.cfg)
         self.shape = (n0, n1)
         self.dtype = {"float32": torch.float32, "f32": torch.float32,
@@ -268,13 +270,13 @@ class SfftPool:
         self._keep = {}
 
     def submit(self, ref, sci, w0, w1, dk, db, const_phot_ratio, precision="mixed", mask=None, diff=None,
-               stream=None):
+               stream=None, spline=None):
         """Enqueue a pair; returns (ticket, diff, x, info), or None if it cannot be admitted now."""
         torch = _torch()
         host = not ref.is_cuda
         dtype = {torch.float32: "float32", torch.float64: "float64"}[ref.dtype]
         n0, n1 = ref.shape
-        cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision)
+        cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision, spline)
         n = sfft_num_unknowns(cfg)
         dev = "cpu" if host else ref.device
         pin = dict(pin_memory=True) if host else {}

@@ -35,7 +35,8 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 class sfft_config(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in
-                ("n0", "n1", "w0", "w1", "dk", "db", "const_phot_ratio", "dtype", "precision")]
+                ("n0", "n1", "w0", "w1", "dk", "db", "const_phot_ratio", "dtype", "precision", "basis",
+                 "kdeg", "kint", "bdeg", "bint")]
 
 
 class sfft_solve_info(ctypes.Structure):
@@ -153,10 +154,18 @@ def status_string(status):
     return library().sfft_status_string(status).decode()
 
 
-def make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed"):
+SFFT_BASIS_POLY, SFFT_BASIS_BSPLINE = 0, 1
+
+
+def make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed", spline=None):
+    """spline: None (polynomial basis) or (kdeg, kint, bdeg, bint) for the B-spline basis (dk = db = 0)."""
     dt = {"float32": SFFT_F32, "f32": SFFT_F32, "float64": SFFT_F64, "f64": SFFT_F64}[str(dtype)]
     pr = {"fp64": SFFT_PREC_FP64, "mixed": SFFT_PREC_MIXED}[precision]
-    return sfft_config(n0, n1, w0, w1, dk, db, int(bool(const_phot_ratio)), dt, pr)
+    if spline is None:
+        return sfft_config(n0, n1, w0, w1, dk, db, int(bool(const_phot_ratio)), dt, pr, SFFT_BASIS_POLY, 0, 0, 0, 0)
+    kdeg, kint, bdeg, bint = spline
+    return sfft_config(n0, n1, w0, w1, dk, db, int(bool(const_phot_ratio)), dt, pr, SFFT_BASIS_BSPLINE,
+                       kdeg, kint, bdeg, bint)
 
 
 def sfft_num_unknowns(cfg):

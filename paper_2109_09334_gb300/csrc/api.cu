@@ -85,18 +85,20 @@ __global__ void k_round(int n, const cpx<double> *src, cpx<T> *dst) {
         dst[q] = mk((T)src[q].re, (T)src[q].im);
 }
 
-// 1-D DFT of xt^p (FP64, direct sum with the FP64 table), written in the
-// compute type.  perm: output index of bin l (permuted layout for x, natural for y).
+// 1-D DFT of the background functions of one axis (FP64, direct sum with the
+// FP64 table), written in the compute type: function p is xt^p, or row p of
+// tab (FP64, [nfun][n]) when tab is not null.  perm: output index of bin l
+// (permuted layout for x, natural for y).
 template <typename T>
-__global__ void k_poly_dft(int n, int nout, int pmax, const cpx<double> *tw, int na, int nbk, int permute,
-                           cpx<T> *out) {
-    const int total = (pmax + 1) * nout;
+__global__ void k_poly_dft(int n, int nout, int nfun, const cpx<double> *tw, int na, int nbk, int permute,
+                           const double *tab, cpx<T> *out) {
+    const int total = nfun * nout;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int p = e / nout, l = e % nout;
         double re = 0.0, im = 0.0;
         int q = 0;  // l x mod n, stepped by l
         for (int x = 0; x < n; ++x) {
-            const double v = ipow(coord<double>(x, n), p);
+            const double v = tab ? tab[(size_t)p * n + x] : ipow(coord<double>(x, n), p);
             const cpx<double> w = tw[q];
             re += v * w.re;
             im += v * w.im;
@@ -114,8 +116,9 @@ static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int plan_validate(const sfft_config *c) {
     if (!c) return SFFT_ERR_INVALID;
     if (c->n0 < 16 || c->n1 < 16 || c->n0 > 4096 || c->n1 > 4096) return SFFT_ERR_UNSUPPORTED;
-    if (c->w0 < 0 || c->w1 < 0 || c->dk < 0 || c->db < 0) return SFFT_ERR_INVALID;
-    if (c->dk > 3 || c->db > 3) return SFFT_ERR_UNSUPPORTED;
+    if (c->w0 < 0 || c->w1 < 0) return SFFT_ERR_INVALID;
+    const int bvr = basis_validate(c);
+    if (bvr) return bvr;
     // lag ranges: |rho| <= 2w must stay inside one period; along x the split
     // pruned transform of power-of-two n0 further needs 4 w0 + 1 <= NA
     const int na = !is_pow2(c->n0) ? c->n0 : (c->n0 < kMaxNA ? c->n0 : kMaxNA);
@@ -125,18 +128,16 @@ int plan_validate(const sfft_config *c) {
     return SFFT_OK;
 }
 
-static int unknowns(const sfft_config *c) {
-    const int L = (2 * c->w0 + 1) * (2 * c->w1 + 1);
-    const int nk = n_terms(c->dk), nb = n_terms(c->db);
-    return c->const_phot_ratio ? nk * (L - 1) + 1 + nb : nk * L + nb;
-}
-
 void plan_free(Plan *p) {
-    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->chirp1, p->bfilt1, p->twpm1, p->chirp0, p->bfilt0, p->twpm0, p->kimg, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->mom,
-                    p->lag, p->A, p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own,
-                    p->x_own, p->info_own, p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap};
+    void *bufs[] = {p->tw0, p->tw1, p->twp0, p->twp1, p->chirp1, p->bfilt1, p->twpm1, p->chirp0, p->bfilt0,
+                    p->twpm0, p->kimg, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->lag, p->A,
+                    p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own, p->x_own, p->info_own,
+                    p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap, p->d_int, p->ftab, p->ftab64,
+                    p->bxy64, p->d_zdesc, p->d_rdesc, p->z0, p->cmat, p->unk};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    free(p->h_int);
+    free(p->host_pairs);
     delete p;
 }
 
@@ -153,7 +154,7 @@ void plan_free(Plan *p) {
 // Launch shapes found by sfft_plan_autotune, kept for later plans of the same
 // image size, types and kernel degree (server slots, pool lanes).
 struct TuneEntry {
-    int n0, n1, dtype, precision, dk;
+    int n0, n1, dtype, precision, dk, basis, kdeg, kint;
     int32_t shapes[SFFT_TUNING_LEN];
 };
 
@@ -176,7 +177,8 @@ static int g_ntune = 0;
 static std::mutex g_tune_mu;
 
 static bool tune_key_eq(const TuneEntry &e, const sfft_config *c) {
-    return e.n0 == c->n0 && e.n1 == c->n1 && e.dtype == c->dtype && e.precision == c->precision && e.dk == c->dk;
+    return e.n0 == c->n0 && e.n1 == c->n1 && e.dtype == c->dtype && e.precision == c->precision && e.dk == c->dk &&
+           e.basis == c->basis && e.kdeg == c->kdeg && e.kint == c->kint;
 }
 
 static void tune_lookup(Plan *p) {
@@ -194,7 +196,7 @@ static void tune_store(const Plan *p) {
         else ++g_ntune;
     }
     const sfft_config &c = p->cfg;
-    g_tune[k] = TuneEntry{c.n0, c.n1, c.dtype, c.precision, c.dk, {}};
+    g_tune[k] = TuneEntry{c.n0, c.n1, c.dtype, c.precision, c.dk, c.basis, c.kdeg, c.kint, {}};
     get_shapes(p, g_tune[k].shapes);
 }
 
@@ -206,9 +208,8 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     p->n0 = cfg->n0;
     p->n1 = cfg->n1;
     p->h1c = cfg->n1 / 2 + 1;
-    p->nk = n_terms(cfg->dk);
-    p->nb = n_terms(cfg->db);
-    p->n = unknowns(cfg);
+    basis_terms(cfg, &p->nk, &p->nb);
+    p->n = basis_unknowns(cfg);
     p->L0 = 2 * cfg->w0 + 1;
     p->L1 = 2 * cfg->w1 + 1;
     p->gen0 = !is_pow2(cfg->n0);
@@ -221,7 +222,21 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     p->fp64 = cfg->precision == SFFT_PREC_FP64;
     p->csz = p->fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
     p->last_stream = s;
+    {
+        const int rc = basis_build(p, s);
+        if (rc != SFFT_OK) {
+            cudaGetLastError();
+            plan_free(p);
+            return rc;
+        }
+    }
     // gather pairs
+    p->host_pairs = (PairDesc *)malloc(
+        (size_t)(p->nk * (p->nk + 1) / 2 + p->nk * p->nbx + p->nk) * sizeof(PairDesc));
+    if (!p->host_pairs) {
+        plan_free(p);
+        return SFFT_ERR_OOM;
+    }
     int np = 0, rows = 0;
     auto push = [&](int kind, int a, int b, int h0) {
         PairDesc d;
@@ -236,11 +251,10 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     for (int a = 0; a < p->nk; ++a)
         for (int b = a; b < p->nk; ++b) push(PK_OMEGA, a, b, 2 * cfg->w0);
     for (int a = 0; a < p->nk; ++a)
-        for (int q = 0; q <= cfg->db; ++q) push(PK_LAMBDA, a, q, cfg->w0);
+        for (int q = 0; q < p->nbx; ++q) push(PK_LAMBDA, a, q, cfg->w0);
     for (int a = 0; a < p->nk; ++a) push(PK_THETA, a, p->nk, cfg->w0);
     p->npairs = np;
     p->nrows = rows;
-    p->nmom = (2 * cfg->dk + 1) + (cfg->dk + cfg->db + 1) + (cfg->dk + 1) + (cfg->db + 1);
 
     const size_t P = (size_t)p->n0 * p->n1;
     const size_t half = (size_t)p->h1c * p->n0;
@@ -260,9 +274,9 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->tw1, p->n1 * csz);
     SFFT_ALLOC(p->twp0, p->n0 * csz);
     SFFT_ALLOC(p->twp1, p->n1 * csz);
-    SFFT_ALLOC(p->xhat, (size_t)(cfg->db + 1) * p->n0 * csz);
-    SFFT_ALLOC(p->yhat, (size_t)(cfg->db + 1) * p->h1c * csz);
-    SFFT_ALLOC(p->F, (size_t)(cfg->dk + 2) * half * csz);
+    SFFT_ALLOC(p->xhat, (size_t)p->nbx * p->n0 * csz);
+    SFFT_ALLOC(p->yhat, (size_t)p->nby * p->h1c * csz);
+    SFFT_ALLOC(p->F, (size_t)(p->nfy + 1) * half * csz);
     // the column spectra (power-of-two n0); the subtraction reuses U for D~
     SFFT_ALLOC(p->U, (size_t)(p->gen0 ? 1 : p->nimg) * half * csz);
     SFFT_ALLOC(p->kimg, (size_t)p->L0 * p->L1 * sizeof(double));
@@ -279,7 +293,6 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->Q, (size_t)p->nrows * p->h1c * csz);
     SFFT_ALLOC(p->pairs, (size_t)np * sizeof(PairDesc));
     SFFT_ALLOC(p->rowmom, (size_t)p->n0 * p->nmom * sizeof(double));
-    SFFT_ALLOC(p->mom, (size_t)(24 * 7 + 16) * sizeof(double));
     SFFT_ALLOC(p->lag, nlag * sizeof(double));
     SFFT_ALLOC(p->A, n * n * rsz);
     SFFT_ALLOC(p->Wm, n * n * rsz);
@@ -305,19 +318,6 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         plan_free(p);
         return SFFT_ERR_CUDA;
     }
-    double csum[16];
-    for (int e = 0; e < 8; ++e) {
-        double a = 0.0, b = 0.0;
-        for (int x = 0; x < p->n0; ++x) a += pow((2.0 * x - (p->n0 - 1)) / (p->n0 - 1), e);
-        for (int y = 0; y < p->n1; ++y) b += pow((2.0 * y - (p->n1 - 1)) / (p->n1 - 1), e);
-        csum[e] = a;
-        csum[8 + e] = b;
-    }
-    // csum is copied from a host stack array: make the copy synchronous
-    if ((err = cudaMemcpy(p->mom + 24 * 7, csum, sizeof(csum), cudaMemcpyHostToDevice))) {
-        plan_free(p);
-        return SFFT_ERR_CUDA;
-    }
     cpx<double> *t64a = nullptr, *t64b = nullptr;
     if (cudaMalloc((void **)&t64a, p->n0 * sizeof(cpx<double>)) != cudaSuccess ||
         cudaMalloc((void **)&t64b, p->n1 * sizeof(cpx<double>)) != cudaSuccess) {
@@ -328,21 +328,25 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     }
     k_twiddle64<<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a);
     k_twiddle64<<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b);
-    const int bx = ((cfg->db + 1) * p->n0 + 127) / 128, by = ((cfg->db + 1) * p->h1c + 127) / 128;
+    const int bx = (p->nbx * p->n0 + 127) / 128, by = (p->nby * p->h1c + 127) / 128;
+    // background functions: powers computed in the kernel, or the B-spline tables
+    const double *tbx = p->bxy64, *tby = p->bxy64 ? p->bxy64 + (size_t)p->nbx * p->n0 : nullptr;
     if (p->fp64) {
         k_round<double><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<double> *)p->tw0);
         k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<double> *)p->tw1);
         if (!p->gen0) pass_tables<double>(p->n0, t64a, (cpx<double> *)p->twp0, s);
         if (!p->gen1) pass_tables<double>(p->n1, t64b, (cpx<double> *)p->twp1, s);
-        k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<double> *)p->xhat);
-        k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<double> *)p->yhat);
+        k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
+                                              (cpx<double> *)p->xhat);
+        k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, p->nby, t64b, 0, 1, 0, tby, (cpx<double> *)p->yhat);
     } else {
         k_round<float><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<float> *)p->tw0);
         k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<float> *)p->tw1);
         if (!p->gen0) pass_tables<float>(p->n0, t64a, (cpx<float> *)p->twp0, s);
         if (!p->gen1) pass_tables<float>(p->n1, t64b, (cpx<float> *)p->twp1, s);
-        k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, cfg->db, t64a, p->na, p->nbk, 1, (cpx<float> *)p->xhat);
-        k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, cfg->db, t64b, 0, 1, 0, (cpx<float> *)p->yhat);
+        k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
+                                             (cpx<float> *)p->xhat);
+        k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, p->nby, t64b, 0, 1, 0, tby, (cpx<float> *)p->yhat);
     }
     for (int ax = 0; ax < 2; ++ax) {  // Bluestein tables of the axes that are not powers of two
         const bool gen = ax == 0 ? p->gen0 : p->gen1;
@@ -443,8 +447,10 @@ const char *sfft_status_string(int status) {
 
 int sfft_num_unknowns(const sfft_config *cfg, int32_t *n) {
     if (!cfg || !n) return SFFT_ERR_INVALID;
-    if (cfg->w0 < 0 || cfg->w1 < 0 || cfg->dk < 0 || cfg->db < 0) return SFFT_ERR_INVALID;
-    *n = unknowns(cfg);
+    if (cfg->w0 < 0 || cfg->w1 < 0) return SFFT_ERR_INVALID;
+    const int v = basis_validate(cfg);
+    if (v == SFFT_ERR_INVALID) return v;
+    *n = basis_unknowns(cfg);
     return SFFT_OK;
 }
 
@@ -554,9 +560,6 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
         cudaEventElapsedTime(ms, e0, e1);
         return r;
     };
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     struct Knob {
         int *field;
         int stage;
@@ -565,8 +568,10 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
         {&p->tune_tr, SFFT_STAGE_ROWS, {0, 4, 2, 1, -1}},
         {&p->tune_gi, SFFT_STAGE_COLS, {0, 3, 2, 1, -1}},
         {&p->tune_ng, SFFT_STAGE_SUBTRACT, {0, 2, 1, -1, -1}},
-        {&p->tune_sgrid, SFFT_STAGE_SOLVE, {0, sms, -1, -1, -1}},
     };
+    // The solve grid is not tuned here: a single system's time does not
+    // predict the batched solves of the serving path (sfft_plan_set_tuning
+    // sets it by hand).
     for (Knob &kb : knobs) {
         if (kb.stage == SFFT_STAGE_COLS && p->gen0) continue;  // no column FFT
         int best = 0;

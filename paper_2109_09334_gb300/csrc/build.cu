@@ -28,7 +28,6 @@
 namespace sfft {
 
 constexpr int kMaxMom = 24;  // per-row moments for dk, db <= 3
-constexpr int kUMax = 7;     // powers of xt in the moment tables (u <= 6)
 
 struct MomLayout {
     int fRR, fR, fRS, fS, n;
@@ -52,9 +51,10 @@ __device__ __forceinline__ double load_img(const I *p, size_t k) { return (doubl
 // transformed together and separated after; the transforms are written
 // transposed ([image][m][x]) for the column pass.
 template <typename T, typename I>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, int n1, int dk, int TR, const I *__restrict__ R,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, int n1, int nfy, int TR, const I *__restrict__ R,
                                                const I *__restrict__ S, const uint8_t *__restrict__ mask,
-                                               cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1g) {
+                                               cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1g,
+                                               const T *__restrict__ fy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
     const int np = padded_len(n1) + 4;  // +4: rows start in different banks
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     cpx<T> *Z = tw + n1;                                 // TR * np
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int grp = tid / G, gt = tid - grp * G;
-    const int nseq = dk + 2;
+    const int nseq = nfy + 1;
     const int nfft = (nseq + 1) / 2;
     // packed pair index fastest: blocks that read the same rows run together
     const int f = blockIdx.x % nfft;
@@ -91,8 +91,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const T yt = coord<T>(y0 + c, n1);
-            const T va = (sa <= dk) ? rv[c] * ipow(yt, sa) : sv[c];
-            const T vb = (sb <= dk) ? rv[c] * ipow(yt, sb) : (sb == dk + 1 ? sv[c] : (T)0);
+            // weights yt^j (polynomial) or the tabulated y-functions (B-spline)
+            const T wa = fy ? (sa < nfy ? fy[(size_t)sa * n1 + y0 + c] : (T)0) : ipow(yt, sa);
+            const T wb = fy ? (sb < nfy ? fy[(size_t)sb * n1 + y0 + c] : (T)0) : ipow(yt, sb);
+            const T va = (sa < nfy) ? rv[c] * wa : sv[c];
+            const T vb = (sb < nfy) ? rv[c] * wb : (sb == nfy ? sv[c] : (T)0);
             zr[pad16(y0 + c)] = mk(va, vb);
         }
     }
@@ -121,18 +124,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
 // threads per row, TR rows per block, otherwise as k_rows (two real
 // sequences per complex transform, transposed output).
 template <typename T, typename I>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0, int n1, int m1, int dk, int TR,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0, int n1, int m1, int nfy, int TR,
                                                const I *__restrict__ R, const I *__restrict__ S,
                                                const uint8_t *__restrict__ mask, cpx<T> *__restrict__ F,
                                                const cpx<T> *__restrict__ chirp, const cpx<T> *__restrict__ bfilt,
-                                               const cpx<T> *__restrict__ twpm) {
+                                               const cpx<T> *__restrict__ twpm, const T *__restrict__ fy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = m1 / 16;
     const int np = padded_len(m1) + 4;
     cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // TR * np
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int grp = tid / G, gt = tid - grp * G;
-    const int nseq = dk + 2;
+    const int nseq = nfy + 1;
     const int nfft = (nseq + 1) / 2;
     const int f = blockIdx.x % nfft;
     const int x0b = (blockIdx.x / nfft) * TR;
@@ -145,8 +148,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0
             const T rv = keep ? (T)R[rowoff + y] : (T)0;
             const T sv = keep ? (T)S[rowoff + y] : (T)0;
             const T yt = coord<T>(y, n1);
-            const T va = (sa <= dk) ? rv * ipow(yt, sa) : sv;
-            const T vb = (sb <= dk) ? rv * ipow(yt, sb) : (sb == dk + 1 ? sv : (T)0);
+            const T wa = fy ? (sa < nfy ? fy[(size_t)sa * n1 + y] : (T)0) : ipow(yt, sa);
+            const T wb = fy ? (sb < nfy ? fy[(size_t)sb * n1 + y] : (T)0) : ipow(yt, sb);
+            const T va = (sa < nfy) ? rv * wa : sv;
+            const T vb = (sb < nfy) ? rv * wb : (sb == nfy ? sv : (T)0);
             zr[pad16(y)] = mk(va, vb);
         }
     }
@@ -229,23 +234,81 @@ __global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, c
     }
 }
 
+// Per-row moments of the B-spline basis: moment d of row x is
+//   sum_y v_kind(y) ytab[ya](y) (ytab[yb](y) if yb >= 0),
+// v = Rm^2 (kind 0), Rm (1), Rm Sm (2), Sm (3); ytab = [fy | by] rows.
+// Block (row, chunk of kMomChunk moments): plain per-thread partials, then a
+// two-sum reduction across the block, as in k_row_moments.
+constexpr int kMomChunk = 12;
+
+template <typename T, typename I>
+__global__ void k_row_moments_tab(int n1, int nmom, const int *__restrict__ rdesc, const T *__restrict__ ytab,
+                                  const I *__restrict__ R, const I *__restrict__ S,
+                                  const uint8_t *__restrict__ mask, double *__restrict__ rowmom) {
+    __shared__ Acc<T> red[32][kMomChunk];
+    const int x0 = blockIdx.x, d0 = blockIdx.y * kMomChunk, tid = threadIdx.x, nthr = blockDim.x;
+    const size_t rowoff = (size_t)x0 * n1;
+    int kind[kMomChunk], ya[kMomChunk], yb[kMomChunk];
+    T part[kMomChunk];
+#pragma unroll
+    for (int k = 0; k < kMomChunk; ++k) {
+        const bool ok = d0 + k < nmom;
+        kind[k] = ok ? rdesc[3 * (d0 + k)] : -1;
+        ya[k] = ok ? rdesc[3 * (d0 + k) + 1] : 0;
+        yb[k] = ok ? rdesc[3 * (d0 + k) + 2] : -1;
+        part[k] = (T)0;
+    }
+    for (int y = tid; y < n1; y += nthr) {
+        const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
+        const T rv = (T)R[rowoff + y] * keep;
+        const T sv = (T)S[rowoff + y] * keep;
+#pragma unroll
+        for (int k = 0; k < kMomChunk; ++k) {
+            if (kind[k] < 0) continue;
+            T w = ytab[(size_t)ya[k] * n1 + y];
+            if (yb[k] >= 0) w *= ytab[(size_t)yb[k] * n1 + y];
+            const T v = kind[k] == 0 ? rv * rv : (kind[k] == 1 ? rv : (kind[k] == 2 ? rv * sv : sv));
+            part[k] += v * w;
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+    for (int k = 0; k < kMomChunk; ++k) {
+        Acc<T> a;
+        a.zero();
+        a.add(part[k]);
+        for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
+        if (lane == 0) red[warp][k] = a;
+    }
+    __syncthreads();
+    if (tid < kMomChunk && d0 + tid < nmom) {
+        Acc<T> a = red[0][tid];
+        for (int w = 1; w < nw; ++w) a.add(red[w][tid]);
+        rowmom[(size_t)x0 * nmom + d0 + tid] = a.wide();
+    }
+}
+
 // ---------------------------------------------------------------------------
-// mom[k][u] = sum_x0 xt0^u * rowmom[x0][k]   (FP64)
-__global__ void k_moments(int n0, int nmom, const double *__restrict__ rowmom, double *__restrict__ mom) {
-    const int k = blockIdx.x / kUMax, u = blockIdx.x % kUMax;
+// Zero-lag values (FP64): z0[e] = sum_x xtab[xa](x) (xtab[xb](x) if xb >= 0)
+// rowmom[x][d] for descriptor e = (d, xa, xb).
+__global__ void k_zero_lag(int n0, int nmom, const int *__restrict__ zdesc, const double *__restrict__ xtab,
+                           const double *__restrict__ rowmom, double *__restrict__ z0) {
+    const int e = blockIdx.x;
+    const int d = zdesc[3 * e], xa = zdesc[3 * e + 1], xb = zdesc[3 * e + 2];
     double acc = 0.0;
     for (int x = threadIdx.x; x < n0; x += blockDim.x) {
-        double xt = coord<double>(x, n0);
-        acc += ipow(xt, u) * rowmom[(size_t)x * nmom + k];
+        double w = xtab[(size_t)xa * n0 + x];
+        if (xb >= 0) w *= xtab[(size_t)xb * n0 + x];
+        acc += w * rowmom[(size_t)x * nmom + d];
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        mom[(size_t)k * kUMax + u] = s;
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        z0[e] = v;
     }
 }
 
@@ -256,9 +319,9 @@ __global__ void k_moments(int n0, int nmom, const double *__restrict__ rowmom, d
 // the term (i, j): the row transform of yt^j * Rm weighted by xt^i; t = nk
 // is Sm.  Output layout U[t][m][lb*NA + r] = spectrum at l = lb + NB*r.
 template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int n1, int dk, int na, int nbk, int GI,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int n1, BasisView bv, int na, int nbk, int GI,
                                                const cpx<T> *__restrict__ F, cpx<T> *__restrict__ U,
-                                               const cpx<T> *__restrict__ tw0g) {
+                                               const cpx<T> *__restrict__ tw0g, const T *__restrict__ fx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n0 / 16;
     const int np = padded_len(n0);
@@ -268,7 +331,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
     const int grp = tid / G, gt = tid - grp * G;
     const int m = blockIdx.y;
     const int h1c = n1 / 2 + 1;
-    const int nk = n_terms(dk);
+    const int nk = bv.nk;
     const int t = blockIdx.x * GI + grp;
     const bool act = t <= nk;
     const int ntw = pass_table_len(n0);
@@ -276,8 +339,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
     cpx<T> *zr = Z + (size_t)grp * np;
     if (act) {
         // thread gt loads elements gt + G c, c < 16: coalesced, all in flight
-        int i = 0, j = dk + 1;
-        if (t < nk) term_ij(t, &i, &j);
+        int i = 0, j = bv.nfy;  // t = nk: Sm, weight 1
+        if (t < nk) {
+            i = bv.ti(t);
+            j = bv.tj(t);
+        }
         const cpx<T> *col = F + ((size_t)j * h1c + m) * n0 + gt;
         cpx<T> v[16];
 #pragma unroll
@@ -285,7 +351,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int x = gt + G * c;
-            zr[pad16(x)] = scale(v[c], ipow(coord<T>(x, n0), i));
+            const T wx = (fx && t < nk) ? fx[(size_t)i * n0 + x] : ipow(coord<T>(x, n0), i);
+            zr[pad16(x)] = scale(v[c], wx);
         }
     }
     __syncthreads();
@@ -349,16 +416,14 @@ __device__ __forceinline__ int out_slot(int c, int s1) {
 }
 
 template <typename T, int G, int NS>
-__global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_gather(int n0, int n1, int dk, int db, int nbk, int npairs, int hmax,
+__global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_gather(int n0, int n1, int nk, int nxp, int nbk, int npairs, int hmax,
                                                 const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
                                                 const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
                                                 cpx<T> *__restrict__ Q) {
     constexpr int NA = 8 * G;
     constexpr int NAP = NA + kPad;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nk = n_terms(dk);
     const int nimg = nk + 1;
-    const int nxp = db + 1;
     const int tile = (nimg + nxp) * NAP;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ngroups = nthr / G;
@@ -529,25 +594,30 @@ constexpr int kXcFold = 4;
 constexpr int kXcThreads = 256;
 
 // Element x of a sequence at column m: idx < 0 is image t = -idx - 1 (t = nk
-// is S), idx >= 0 the monomial xt^idx; `centre` subtracts its mean.
+// is S), idx >= 0 the background x-function idx (xt^idx or its table);
+// `centre` subtracts its mean.
 template <typename T>
-__device__ __forceinline__ cpx<T> xc_seq(int idx, int dk, int m, bool centre, int x, int h1c, int n0,
-                                         const cpx<T> *__restrict__ F, const T *xt, const double *mu_re,
-                                         const double *mu_im, const double *mu_p) {
+__device__ __forceinline__ cpx<T> xc_seq(int idx, const BasisView &bv, const FTab<T> &ft, int m, bool centre, int x,
+                                         int h1c, int n0, const cpx<T> *__restrict__ F, const T *xt,
+                                         const double *mu_re, const double *mu_im, const double *mu_p) {
     if (idx >= 0) {
-        const T v = ipow(xt[x], idx) - (centre ? (T)mu_p[idx] : (T)0);
+        const T w = ft.bx ? ft.bx[(size_t)idx * n0 + x] : ipow(xt[x], idx);
+        const T v = w - (centre ? (T)mu_p[idx] : (T)0);
         return mk(v, (T)0);
     }
     const int t = -idx - 1;
-    const int nk = n_terms(dk);
-    int i = 0, j = dk + 1;
-    if (t < nk) term_ij(t, &i, &j);
-    const cpx<T> v = scale(F[((size_t)j * h1c + m) * n0 + x], ipow(xt[x], i));
+    int i = 0, j = bv.nfy;
+    if (t < bv.nk) {
+        i = bv.ti(t);
+        j = bv.tj(t);
+    }
+    const T wx = (ft.fx && t < bv.nk) ? ft.fx[(size_t)i * n0 + x] : ipow(xt[x], i);
+    const cpx<T> v = scale(F[((size_t)j * h1c + m) * n0 + x], wx);
     return centre ? v - mk((T)mu_re[t], (T)mu_im[t]) : v;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, int db, int npairs, int hmax,
+__global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, BasisView bv, FTab<T> ft, int npairs, int hmax,
                                                       const PairDesc *__restrict__ pairs,
                                                       const cpx<T> *__restrict__ F, cpx<T> *__restrict__ Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -555,20 +625,20 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, in
     cpx<T> *A = reinterpret_cast<cpx<T> *>(smem_raw);            // n0 + 8
     cpx<T> *B = A + n0 + 8;                                      // n0 + 2 hB + 8
     T *xt = reinterpret_cast<T *>(B + n0 + 2 * hB + 8);          // n0
-    __shared__ double mu_re[12], mu_im[12], mu_p[4];
+    __shared__ double mu_re[kMaxKTerms + 1], mu_im[kMaxKTerms + 1], mu_p[kMaxFun];
     __shared__ double red[kXcThreads / 32][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = blockIdx.x, h1c = n1 / 2 + 1;
-    const int nk = n_terms(dk);
+    const int nk = bv.nk;
     for (int x = tid; x < n0; x += kXcThreads) xt[x] = coord<T>(x, n0);
     __syncthreads();
     if (m == 0) {
         // means of every sequence at m = 0 (the DC bin is removed there)
-        for (int q = 0; q < nk + 1 + db + 1; ++q) {
+        for (int q = 0; q < nk + 1 + bv.nbx; ++q) {
             const int idx = q <= nk ? -q - 1 : q - nk - 1;
             double sr = 0.0, si = 0.0;
             for (int x = tid; x < n0; x += kXcThreads) {
-                const cpx<T> v = xc_seq<T>(idx, dk, 0, false, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
+                const cpx<T> v = xc_seq<T>(idx, bv, ft, 0, false, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
                 sr += (double)v.re;
                 si += (double)v.im;
             }
@@ -603,11 +673,12 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, in
         const int ia = -pd.a - 1;
         const int ib = pd.kind == PK_LAMBDA ? pd.b : -pd.b - 1;  // Theta: b = nk (S)
         for (int x = tid; x < n0 + 8; x += kXcThreads)
-            A[x] = x < n0 ? conj(xc_seq<T>(ia, dk, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p)) : mk((T)0, (T)0);
+            A[x] = x < n0 ? conj(xc_seq<T>(ia, bv, ft, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p))
+                          : mk((T)0, (T)0);
         for (int e = tid; e < n0 + 2 * hB + 8; e += kXcThreads) {
             int x = (e - hB) % n0;
             if (x < 0) x += n0;
-            B[e] = xc_seq<T>(ib, dk, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
+            B[e] = xc_seq<T>(ib, bv, ft, m, m == 0, x, h1c, n0, F, xt, mu_re, mu_im, mu_p);
         }
         __syncthreads();
         const int nlag = 2 * h0 + 1;
@@ -665,7 +736,7 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, int dk, in
 constexpr int kS2Out = 8;  // lag outputs per warp task in k_stage2
 
 template <typename T>
-__global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npairs,
+__global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npairs,
                          const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ Q,
                          const cpx<T> *__restrict__ yhat, const cpx<T> *__restrict__ tw1,
                          double *__restrict__ lag, int off_om, int off_la, int off_th) {
@@ -677,12 +748,12 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npa
     const PairDesc pd = pairs[pi];
     const int rho0 = row - pd.row0 - pd.h0;
     const int h1c = n1 / 2 + 1;
-    const int nk = n_terms(dk);
-    const int nbt = n_terms(db);
+    const int nk = bv.nk;
+    const int nbt = bv.nb;
     const int h1 = (pd.kind == PK_OMEGA) ? 2 * w1 : w1;
     const int nr1 = 2 * h1 + 1;
     int nq = 1;
-    if (pd.kind == PK_LAMBDA) nq = db - pd.b + 1;  // q = 0..db-p
+    if (pd.kind == PK_LAMBDA) nq = bv.lamn(pd.b);  // background terms whose x-function is p = b
     const cpx<T> *q = Q + (size_t)row * h1c;
     const double invP = 1.0 / ((double)n0 * (double)n1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -705,7 +776,7 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npa
         if (act) {
             for (int mm = sp * 32 + lane; mm < h1c; mm += nsp * 32) {
                 cpx<T> v = q[mm];
-                if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)qi * h1c + mm]);
+                if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)bv.lamq(pd.b, qi) * h1c + mm]);
                 const T wm = (mm == 0 || (2 * mm == n1)) ? (T)1 : (T)2;
                 v = scale(v, wm);
                 int idx = imod(mm * r0, n1);  // (mm rho1) mod n1, stepped by mm
@@ -744,7 +815,7 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npa
                     const int pidx = ia * nk - ia * (ia - 1) / 2 + (ib - ia);
                     idx = off_om + ((size_t)pidx * (4 * w0 + 1) + (rho0 + 2 * w0)) * (4 * w1 + 1) + (rho1 + 2 * w1);
                 } else if (pd.kind == PK_LAMBDA) {
-                    const int s2 = term_index(pd.b, qo);  // (p, q)
+                    const int s2 = bv.lams(pd.b, qo);  // background term (p, q)
                     idx = off_la + (((size_t)pd.a * nbt + s2) * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
                 } else {
                     idx = off_th + ((size_t)pd.a * (2 * w0 + 1) + (rho0 + w0)) * (2 * w1 + 1) + (rho1 + w1);
@@ -758,35 +829,6 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, int dk, int db, int npa
 
 // ---------------------------------------------------------------------------
 // Assembly of M and rhs (Eq. B5, B7, B9, B11, B13, B15).
-struct Unk {
-    int kern, t, a, b;
-};
-__device__ __forceinline__ Unk decode(int u, int w0, int w1, int nk, int cpr) {
-    const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
-    const int per = cpr ? L - 1 : L;
-    const int ctr = (L - 1) / 2;
-    Unk r;
-    int off;
-    if (u < L) {
-        r.t = 0;
-        off = u;
-    } else if (u - L < (nk - 1) * per) {
-        const int v = u - L;
-        r.t = 1 + v / per;
-        off = v % per;
-        if (cpr && off >= ctr) ++off;
-    } else {
-        r.kern = 0;
-        r.t = u - L - (nk - 1) * per;
-        r.a = r.b = 0;
-        return r;
-    }
-    r.kern = 1;
-    r.a = off / L1 - w0;
-    r.b = off % L1 - w1;
-    return r;
-}
-
 struct LagView {
     const double *lag;
     int off_om, off_la, off_th;
@@ -811,62 +853,53 @@ struct LagView {
     }
 };
 
-__global__ void k_assemble(int n, int w0, int w1, int dk, int db, int cpr, LagView lv,
-                           const double *__restrict__ mom, const double *__restrict__ csum,
-                           double *__restrict__ M, double *__restrict__ rhs) {
-    const MomLayout ml = mom_layout(dk, db);
-    const int nk = n_terms(dk);
+// Zero-lag values z0: Omega_tu(0,0) by pair index (t <= u), then
+// Lambda_ts(0,0) [t][s], Theta_t(0,0), E_s; C (Eq. B11) in cmat[s][s'].
+// unk[u] = (kernel term?, term, alpha, beta).
+__global__ void k_assemble(int n, const int4 *__restrict__ unk, LagView lv, const double *__restrict__ z0,
+                           const double *__restrict__ cmat, double *__restrict__ M, double *__restrict__ rhs) {
+    const int nk = lv.nk, nb = lv.nbt;
+    const int z_la = nk * (nk + 1) / 2, z_th = z_la + nk * nb, z_e = z_th + nk;
     const size_t total = (size_t)n * n;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total + n;
          e += (size_t)gridDim.x * blockDim.x) {
         if (e >= total) {  // rhs
             const int row = (int)(e - total);
-            Unk ur = decode(row, w0, w1, nk, cpr);
+            const int4 ur = unk[row];
             double v;
-            int i, j;
-            term_ij(ur.t, &i, &j);
-            if (ur.kern) {
-                if (ur.a == 0 && ur.b == 0) v = mom[(size_t)(ml.fRS + j) * kUMax + i];  // Theta(0,0)
-                else v = lv.th(ur.t, ur.a, ur.b) - lv.th(ur.t, 0, 0);
+            if (ur.x) {
+                if (ur.z == 0 && ur.w == 0) v = z0[z_th + ur.y];  // Theta(0,0)
+                else v = lv.th(ur.y, ur.z, ur.w) - lv.th(ur.y, 0, 0);
             } else {
-                v = mom[(size_t)(ml.fS + j) * kUMax + i];  // E (Eq. B15)
+                v = z0[z_e + ur.y];  // E (Eq. B15)
             }
             rhs[row] = v;
             continue;
         }
         const int row = (int)(e / n), col = (int)(e % n);
-        Unk ur = decode(row, w0, w1, nk, cpr), uc = decode(col, w0, w1, nk, cpr);
-        int ri, rj, ci, cj;
-        term_ij(ur.t, &ri, &rj);
-        term_ij(uc.t, &ci, &cj);
+        const int4 ur = unk[row], uc = unk[col];
         double v;
-        if (ur.kern && uc.kern) {
-            const bool rz = (ur.a == 0 && ur.b == 0), cz = (uc.a == 0 && uc.b == 0);
+        if (ur.x && uc.x) {
+            const bool rz = (ur.z == 0 && ur.w == 0), cz = (uc.z == 0 && uc.w == 0);
             if (rz && cz) {
-                v = mom[(size_t)(ml.fRR + rj + cj) * kUMax + (ri + ci)];  // Omega(0,0)
+                const int t = min(ur.y, uc.y), u = max(ur.y, uc.y);
+                v = z0[t * nk - t * (t - 1) / 2 + (u - t)];  // Omega(0,0)
             } else if (rz) {
-                v = lv.om(ur.t, uc.t, -uc.a, -uc.b) - lv.om(ur.t, uc.t, 0, 0);
+                v = lv.om(ur.y, uc.y, -uc.z, -uc.w) - lv.om(ur.y, uc.y, 0, 0);
             } else if (cz) {
-                v = lv.om(ur.t, uc.t, ur.a, ur.b) - lv.om(ur.t, uc.t, 0, 0);
+                v = lv.om(ur.y, uc.y, ur.z, ur.w) - lv.om(ur.y, uc.y, 0, 0);
             } else {
-                v = lv.om(ur.t, uc.t, ur.a - uc.a, ur.b - uc.b) - lv.om(ur.t, uc.t, ur.a, ur.b) -
-                    lv.om(ur.t, uc.t, -uc.a, -uc.b) + lv.om(ur.t, uc.t, 0, 0);
+                v = lv.om(ur.y, uc.y, ur.z - uc.z, ur.w - uc.w) - lv.om(ur.y, uc.y, ur.z, ur.w) -
+                    lv.om(ur.y, uc.y, -uc.z, -uc.w) + lv.om(ur.y, uc.y, 0, 0);
             }
-        } else if (ur.kern) {  // B (Eq. B7)
-            int p, q;
-            term_ij(uc.t, &p, &q);
-            if (ur.a == 0 && ur.b == 0) v = mom[(size_t)(ml.fR + rj + q) * kUMax + (ri + p)];
-            else v = lv.la(ur.t, uc.t, ur.a, ur.b) - lv.la(ur.t, uc.t, 0, 0);
-        } else if (uc.kern) {  // B~ (Eq. B9)
-            int p, q;
-            term_ij(ur.t, &p, &q);
-            if (uc.a == 0 && uc.b == 0) v = mom[(size_t)(ml.fR + cj + q) * kUMax + (ci + p)];
-            else v = lv.la(uc.t, ur.t, uc.a, uc.b) - lv.la(uc.t, ur.t, 0, 0);
-        } else {  // C (Eq. B11): separable sums of coordinate powers
-            int p, q, p2, q2;
-            term_ij(ur.t, &p, &q);
-            term_ij(uc.t, &p2, &q2);
-            v = csum[p + p2] * csum[8 + q + q2];
+        } else if (ur.x) {  // B (Eq. B7)
+            if (ur.z == 0 && ur.w == 0) v = z0[z_la + ur.y * nb + uc.y];
+            else v = lv.la(ur.y, uc.y, ur.z, ur.w) - lv.la(ur.y, uc.y, 0, 0);
+        } else if (uc.x) {  // B~ (Eq. B9)
+            if (uc.z == 0 && uc.w == 0) v = z0[z_la + uc.y * nb + ur.y];
+            else v = lv.la(uc.y, ur.y, uc.z, uc.w) - lv.la(uc.y, ur.y, 0, 0);
+        } else {  // C (Eq. B11)
+            v = cmat[(size_t)ur.y * nb + uc.y];
         }
         M[e] = v;
     }
@@ -876,7 +909,8 @@ __global__ void k_assemble(int n, int w0, int w1, int dk, int db, int cpr, LagVi
 template <typename T, typename I>
 static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
                                bool moments, cudaStream_t s) {
-    const int nfft = (p->cfg.dk + 3) / 2;
+    const int nfft = (p->nfy + 2) / 2;
+    const FTab<T> ft = ftab_of<T>(p);
     if (p->gen1) {
         const int G = p->m1 / 16;
         int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
@@ -889,8 +923,8 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
         auto kern = k_rows_blu<T, I>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(
-            p->n0, p->n1, p->m1, p->cfg.dk, TR, (const I *)ref, (const I *)sci, mask, (cpx<T> *)p->F,
-            (const cpx<T> *)p->chirp1, (const cpx<T> *)p->bfilt1, (const cpx<T> *)p->twpm1);
+            p->n0, p->n1, p->m1, p->nfy, TR, (const I *)ref, (const I *)sci, mask, (cpx<T> *)p->F,
+            (const cpx<T> *)p->chirp1, (const cpx<T> *)p->bfilt1, (const cpx<T> *)p->twpm1, ft.fy);
     } else {
     const int G = p->n1 / 16;
     int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
@@ -902,14 +936,19 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, TR, (const I *)ref,
+    kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->nfy, TR, (const I *)ref,
                                                               (const I *)sci, mask, (cpx<T> *)p->F,
-                                                              (const cpx<T> *)p->twp1);
+                                                              (const cpx<T> *)p->twp1, ft.fy);
     }
     p->launches++;
-    if (moments) {
+    if (moments && !p->bspline) {
         k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
                                                   p->rowmom);
+        p->launches++;
+    } else if (moments) {  // ytab = fy | by
+        dim3 grid(p->n0, (p->nmom + kMomChunk - 1) / kMomChunk);
+        k_row_moments_tab<T, I><<<grid, 256, 0, s>>>(p->n1, p->nmom, p->d_rdesc, ft.fy, (const I *)ref,
+                                                     (const I *)sci, mask, p->rowmom);
         p->launches++;
     }
     return cudaGetLastError();
@@ -917,8 +956,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
 
 template <typename T>
 static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
-    const MomLayout ml = mom_layout(p->cfg.dk, p->cfg.db);
-    k_moments<<<ml.n * kUMax, 256, 0, s>>>(p->n0, ml.n, p->rowmom, p->mom);
+    k_zero_lag<<<p->nzm, 256, 0, s>>>(p->n0, p->nmom, p->d_zdesc, p->ftab64, p->rowmom, p->z0);
     p->launches++;
     if (p->gen0) return cudaGetLastError();  // the lag sums along x need no column spectra
     const int G = p->n0 / 16;
@@ -940,8 +978,8 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     auto kern = k_cols<T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((nimg + GI - 1) / GI, p->h1c);
-    kern<<<grid, GI * G, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->na, p->nbk, GI, (const cpx<T> *)p->F,
-                                    (cpx<T> *)p->U, (const cpx<T> *)p->twp0);
+    kern<<<grid, GI * G, smem, s>>>(p->n0, p->n1, p->bv, p->na, p->nbk, GI, (const cpx<T> *)p->F,
+                                    (cpx<T> *)p->U, (const cpx<T> *)p->twp0, ftab_of<T>(p).fx);
     p->launches++;
     return cudaGetLastError();
 }
@@ -952,13 +990,13 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
         const int hmax = 2 * p->cfg.w0;
         const size_t smem = (size_t)(2 * p->n0 + 2 * (hmax + 8) + 16) * sizeof(cpx<T>) + (size_t)p->n0 * sizeof(T);
         cudaFuncSetAttribute(k_xcorr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_xcorr<T><<<p->h1c, kXcThreads, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->npairs, hmax, p->pairs,
+        k_xcorr<T><<<p->h1c, kXcThreads, smem, s>>>(p->n0, p->n1, p->bv, ftab_of<T>(p), p->npairs, hmax, p->pairs,
                                                     (const cpx<T> *)p->F, (cpx<T> *)p->Q);
         p->launches++;
         return cudaGetLastError();
     }
     const int G = p->na / 8;
-    const int nimg = p->nimg, nxp = p->cfg.db + 1;
+    const int nimg = p->nimg, nxp = p->nbx;
     // one group of G lanes per product, whole warps, at most 384 threads per
     // block; more products go to further blocks along y
     const int max_groups = 384 / G;
@@ -979,7 +1017,7 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
     if (!kern) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(p->h1c, nchunks);
-    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->nbk, p->npairs, hmax, p->pairs,
+    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, p->nbx, p->nbk, p->npairs, hmax, p->pairs,
                                   (const cpx<T> *)p->U, (const cpx<T> *)p->xhat, (const cpx<T> *)p->tw0,
                                   (cpx<T> *)p->Q);
     p->launches++;
@@ -989,7 +1027,7 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
 template <typename T>
 static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) {
     cudaError_t err;
-    k_stage2<T><<<p->nrows, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db, p->npairs,
+    k_stage2<T><<<p->nrows, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->bv, p->npairs,
                                          p->pairs, (const cpx<T> *)p->Q, (const cpx<T> *)p->yhat,
                                          (const cpx<T> *)p->tw1, p->lag, p->lag_om, p->lag_la, p->lag_th);
     p->launches++;
@@ -1006,8 +1044,7 @@ static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) 
     const size_t total = (size_t)p->n * p->n + p->n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->cfg.w0, p->cfg.w1, p->cfg.dk, p->cfg.db, p->cfg.const_phot_ratio,
-                                      lv, p->mom, p->mom + (size_t)kMaxMom * kUMax, M, rhs);
+    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->unk, lv, p->z0, p->cmat, M, rhs);
     p->launches++;
     return cudaGetLastError();
 }

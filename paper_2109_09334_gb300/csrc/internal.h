@@ -30,6 +30,52 @@ struct PairDesc {
     int row0;  // first row of this pair in the stage-1 table Q[row][m]
 };
 
+// Spatial-variation basis (Eq. 2 and 6, or Eq. 7-9).  Kernel term t weights
+// R by fx_i(x) fy_j(y) with i = ti[t], j = tj[t]; background term s is
+// bx_p(x) by_q(y) with p = sp[s], q = sq[s].  Polynomial: fx_i = xt^i etc.,
+// computed in the kernels; B-spline: tabulated functions (ftab).  The int
+// tables live in one array; BasisView holds their offsets.
+struct BasisView {
+    const int *d;  // int tables (device)
+    int nk, nb, nfx, nfy, nbx, nby;
+    int o_ti, o_tj, o_fl, o_uoff, o_sp, o_sq, o_lamn, o_lams, o_lamq, o_jcnt, o_jterm, total;
+    int w0, w1;
+    __host__ __device__ int ti(int t) const { return d[o_ti + t]; }
+    __host__ __device__ int tj(int t) const { return d[o_tj + t]; }
+    // bit 0: the term has the (0,0) offset; bit 1: it has the other offsets
+    __host__ __device__ int flags(int t) const { return d[o_fl + t]; }
+    __host__ __device__ int sp(int s) const { return d[o_sp + s]; }
+    __host__ __device__ int sq(int s) const { return d[o_sq + s]; }
+    // background terms whose x-function is p: lamn(p) of them, lams/lamq(p, k)
+    __host__ __device__ int lamn(int p) const { return d[o_lamn + p]; }
+    __host__ __device__ int lams(int p, int k) const { return d[o_lams + p * nby + k]; }
+    __host__ __device__ int lamq(int p, int k) const { return d[o_lamq + p * nby + k]; }
+    // kernel terms whose y-function is j: jcnt(j) of them, jterm(j, k)
+    __host__ __device__ int jcnt(int j) const { return d[o_jcnt + j]; }
+    __host__ __device__ int jterm(int j, int k) const { return d[o_jterm + j * nk + k]; }
+    // unknown index of offset (a, b) of kernel term t, or -1 if the term lacks it
+    __host__ __device__ int unknown(int t, int a, int b) const {
+        const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
+        const int off = (a + w0) * L1 + (b + w1), ctr = (L - 1) / 2;
+        const int f = flags(t), u0 = d[o_uoff + t];
+        if (off == ctr) return (f & 1) ? ((f & 2) ? u0 + off : u0) : -1;
+        if (!(f & 2)) return -1;
+        return u0 + ((f & 1) ? off : (off > ctr ? off - 1 : off));
+    }
+};
+
+// Tabulated functions of the B-spline basis in the compute type (all null
+// for the polynomial basis): fx [nfx][n0], fy [nfy][n1], bx [nbx][n0], by [nby][n1].
+template <typename T>
+struct FTab {
+    const T *fx, *fy, *bx, *by;
+};
+
+// Largest basis sizes (kernel terms, background terms, functions per axis).
+constexpr int kMaxKTerms = 40;
+constexpr int kMaxBTerms = 36;
+constexpr int kMaxFun = 8;
+
 struct Plan {
     sfft_config cfg;
     int n0, n1, h1c;       // h1c = n1/2 + 1 half-spectrum columns
@@ -54,14 +100,28 @@ struct Plan {
     double *kimg;                   // L0 x L1 kernel image (noise decorrelation)
     // launch shapes chosen by sfft_plan_autotune (0: the built-in choice)
     int tune_tr, tune_gi, tune_ng, tune_sgrid;
-    void *xhat;            // [p][lb][r] 1-D spectra of x^p, permuted (compute type), p <= db
-    void *yhat;            // [q][m] 1-D spectra of y^q, m < h1c (compute type)
-    void *F;               // [(dk+2)][m][x] row transforms (compute type)
+    // basis (see BasisView); the tables are built at plan creation
+    int bspline;           // 0 polynomial, 1 B-spline
+    int nfx, nfy, nbx, nby;
+    BasisView bv;          // offsets; bv.d points to d_int
+    int *h_int, *d_int;    // int tables (host copy, device copy)
+    void *ftab;            // B-spline function tables, compute type: fx | fy | bx | by
+    double *ftab64;        // FP64 x-functions for the zero-lag sums: [nallx][n0]
+    double *bxy64;         // B-spline: FP64 background functions bx [nbx][n0] then by [nby][n1]
+    int nallx;
+    int nzm;               // zero-lag values: Omega(0,0) of each pair, Lambda(0,0), Theta(0,0), E
+    int *d_zdesc;          // [nzm][3] (row moment, x-function a, x-function b or -1)
+    int *d_rdesc;          // [nmom][3] B-spline row moments (kind, y-function a, b or -1)
+    double *z0;            // [nzm] zero-lag values (FP64)
+    double *cmat;          // C of Eq. B11, [nb][nb] (FP64, depends on the basis only)
+    int4 *unk;             // [n] decoded unknowns: (kernel term?, term, alpha, beta)
+    void *xhat;            // [p][lb][r] 1-D spectra of the background x-functions, permuted (compute type)
+    void *yhat;            // [q][m] 1-D spectra of the background y-functions, m < h1c (compute type)
+    void *F;               // [(nfy+1)][m][x] row transforms (compute type)
     void *U;               // [nimg][m][lb][r] full spectra, permuted (compute type); reused for Dt
     void *Q;               // [nrows][m] stage-1 results (compute type complex)
     PairDesc *pairs;       // device copy
     double *rowmom;        // [n0][nmom] per-row moment sums
-    double *mom;           // moments table (see build.cu)
     double *lag;           // lag tables (Omega, Lambda, Theta), FP64
     int lag_om, lag_la, lag_th;  // offsets into lag
     // solve workspace
@@ -87,7 +147,7 @@ struct Plan {
     sfft_solve_info *last_info;
     void *last_diff;
     cudaStream_t last_stream;
-    PairDesc host_pairs[256];
+    PairDesc *host_pairs;  // [npairs]
 };
 
 // plans (api.cu): validation, allocation + tables, release
@@ -95,6 +155,27 @@ int plan_validate(const sfft_config *c);
 int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out);  // cfg already validated
 void plan_free(Plan *p);
 int status_of(cudaError_t e);
+
+// the function tables of a B-spline plan in the compute type (all null for
+// the polynomial basis); ftab holds fx | bx | fy | by
+template <typename T>
+inline FTab<T> ftab_of(const Plan *p) {
+    FTab<T> f{nullptr, nullptr, nullptr, nullptr};
+    if (!p->ftab) return f;
+    f.fx = (const T *)p->ftab;
+    f.bx = f.fx + (size_t)p->nfx * p->n0;
+    f.fy = f.bx + (size_t)p->nbx * p->n0;
+    f.by = f.fy + (size_t)p->nfy * p->n1;
+    return f;
+}
+
+// basis (basis.cu)
+int basis_validate(const sfft_config *c);
+int basis_unknowns(const sfft_config *c);
+int basis_terms(const sfft_config *c, int *nk, int *nb);
+int basis_build(Plan *p, cudaStream_t s);  // p->n, sizes and cfg set; allocations owned by p
+// weights of the kernel terms at one normalised position (w: nk values)
+void basis_term_weights(const Plan *p, double xt0, double yt0, double *w);
 
 // launchers (return cudaError_t of the last launch)
 cudaError_t build_system(Plan *p, const void *ref, const void *sci, const uint8_t *mask, double *M,

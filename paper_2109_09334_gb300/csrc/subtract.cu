@@ -1,7 +1,8 @@
 // subtract.cu -- difference image of Eq. 12-13 from the solved coefficients.
 //
-// D = S - sum_t sum_(a,b) c_t(a,b) g_t(x - a, y - b) - sum_pq b_pq T^pq, with
-// g_t = xt^i yt^j R and the per-term kernel c_t of the delta basis (Eq. 3-4):
+// D = S - sum_t sum_(a,b) c_t(a,b) g_t(x - a, y - b) - sum_s b_s T^s, with
+// g_t = xt^i yt^j R (Eq. 10-11) or B_i(xt) B_j(yt) R (Eq. 8), T^s the
+// background basis, and the per-term kernel c_t of the delta basis (Eq. 3-4):
 // c_t(a,b) = a_t,ab for (a,b) != 0 and c_t(0,0) = a_t,00 - sum_(a,b)!=0 a_t,ab.
 // Along y the convolution is taken in Fourier space (Eq. 13): with the row
 // transforms G~_t(x, m) of the build, the row transform of D is
@@ -18,27 +19,16 @@
 
 namespace sfft {
 
-__device__ __forceinline__ int unknown_index(int t, int a, int b, int w0, int w1, int cpr) {
-    const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
-    const int off = (a + w0) * L1 + (b + w1);
-    if (t == 0) return off;
-    const int ctr = (L - 1) / 2;
-    if (cpr) {
-        if (off == ctr) return -1;
-        return L + (t - 1) * (L - 1) + (off > ctr ? off - 1 : off);
-    }
-    return L + (t - 1) * L + off;
-}
-
 // ksum[t] = sum over (a,b) != 0 of a_t,ab  (FP64)
-__global__ void k_kernel_sums(int w0, int w1, int cpr, const double *__restrict__ x, double *__restrict__ ksum) {
+__global__ void k_kernel_sums(BasisView bv, const double *__restrict__ x, double *__restrict__ ksum) {
     const int t = blockIdx.x;
     double s = 0.0;
-    const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
+    const int L1 = 2 * bv.w1 + 1, L = (2 * bv.w0 + 1) * L1;
     for (int off = threadIdx.x; off < L; off += blockDim.x) {
-        const int a = off / L1 - w0, b = off % L1 - w1;
+        const int a = off / L1 - bv.w0, b = off % L1 - bv.w1;
         if (a == 0 && b == 0) continue;
-        s += x[unknown_index(t, a, b, w0, w1, cpr)];
+        const int u = bv.unknown(t, a, b);
+        if (u >= 0) s += x[u];
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -53,24 +43,20 @@ __global__ void k_kernel_sums(int w0, int w1, int cpr, const double *__restrict_
 
 // kap[t][a + w0][m]
 template <typename T>
-__global__ void k_kernel_table(int n1, int nk, int w0, int w1, int cpr, const double *__restrict__ x,
-                               const double *__restrict__ ksum, const cpx<T> *__restrict__ tw1,
-                               cpx<T> *__restrict__ kap) {
+__global__ void k_kernel_table(int n1, BasisView bv, const double *__restrict__ x, const double *__restrict__ ksum,
+                               const cpx<T> *__restrict__ tw1, cpx<T> *__restrict__ kap) {
+    const int w0 = bv.w0, w1 = bv.w1;
     const int h1c = n1 / 2 + 1, L0 = 2 * w0 + 1;
-    const size_t total = (size_t)nk * L0 * h1c;
+    const size_t total = (size_t)bv.nk * L0 * h1c;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const int m = (int)(e % h1c);
         const int ta = (int)(e / h1c);
         const int t = ta / L0, a = ta % L0 - w0;
         T re = (T)0, im = (T)0;
         for (int b = -w1; b <= w1; ++b) {
-            double c;
-            if (a == 0 && b == 0) {
-                const int u = unknown_index(t, 0, 0, w0, w1, cpr);
-                c = (u >= 0 ? x[u] : 0.0) - ksum[t];
-            } else {
-                c = x[unknown_index(t, a, b, w0, w1, cpr)];
-            }
+            const int u = bv.unknown(t, a, b);
+            double c = u >= 0 ? x[u] : 0.0;
+            if (a == 0 && b == 0) c -= ksum[t];
             cpx<T> w = tw1[imod(m * b, n1)];  // exp(-2 pi i m b / n1)
             re += (T)c * w.re;
             im += (T)c * w.im;
@@ -92,14 +78,15 @@ __host__ __device__ constexpr int sub_q() { return sizeof(T) == 4 ? 4 : 8; }
 // W0 >= 0: the kernel half-width is the compile-time W0 (the tap loop unrolls
 // completely, so the window shifts are register renames); W0 < 0: w0 at run time.
 template <typename T, bool P2, int W0>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0, int n1, int dk, int db, int w0,
-                                                                         int nbkg_off, const cpx<T> *__restrict__ F,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0, int n1, BasisView bv, FTab<T> ft,
+                                                                         int w0, int nbkg_off,
+                                                                         const cpx<T> *__restrict__ F,
                                                                          const cpx<T> *__restrict__ kap,
                                                                          const cpx<T> *__restrict__ yhat,
                                                                          const double *__restrict__ x,
                                                                          cpx<T> *__restrict__ Dt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nk = n_terms(dk), nbt = n_terms(db);
+    const int nk = bv.nk, nbt = bv.nb;
     if (W0 >= 0) w0 = W0;
     const int L0 = 2 * w0 + 1;
     cpx<T> *kp = reinterpret_cast<cpx<T> *>(smem_raw);  // nk * L0
@@ -116,33 +103,42 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
     T xt[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) xt[q] = coord<T>(x0 + q, n0);
-    // S~ minus the background B~(x, m) = sum_pq b_pq xt^p Y^q(m)
+    // S~ minus the background B~(x, m) = sum_s b_s bx_p(x) Y_q(m)
     cpx<T> acc[Q];
     {
-        const cpx<T> *Sc = F + ((size_t)(dk + 1) * h1c + m) * n0 + x0;
+        const cpx<T> *Sc = F + ((size_t)bv.nfy * h1c + m) * n0 + x0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) acc[q] = (P2 || x0 + q < n0) ? Sc[q] : mk((T)0, (T)0);
         for (int s = 0; s < nbt; ++s) {
-            int p, qq;
-            term_ij(s, &p, &qq);
+            const int p = bv.sp(s), qq = bv.sq(s);
             const cpx<T> yq = yhat[(size_t)qq * h1c + m];
             const T bpq = (T)x[nbkg_off + s];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) acc[q] = acc[q] - scale(yq, bpq * ipow(xt[q], p));
+            for (int q = 0; q < Q; ++q) {
+                const T wx = ft.bx ? ((P2 || x0 + q < n0) ? ft.bx[(size_t)p * n0 + x0 + q] : (T)0) : ipow(xt[q], p);
+                acc[q] = acc[q] - scale(yq, bpq * wx);
+            }
         }
     }
-    for (int j = 0; j <= dk; ++j) {
+    // terms grouped by their y-function j: F_j is loaded once per group
+    for (int j = 0; j < bv.nfy; ++j) {
+        const int ncj = bv.jcnt(j);
+        if (ncj == 0) continue;
         cpx<T> f[Q];
         const cpx<T> *Fj = F + ((size_t)j * h1c + m) * n0 + x0;
 #pragma unroll
         for (int q = 0; q < Q; ++q) f[q] = (P2 || x0 + q < n0) ? Fj[q] : mk((T)0, (T)0);
-        for (int i = 0; i + j <= dk; ++i) {
+        for (int k = 0; k < ncj; ++k) {
+            const int t = bv.jterm(j, k), i = bv.ti(t);
             __syncthreads();  // previous term's window reads are done
 #pragma unroll
             for (int q = 0; q < Q; ++q)
-                if (P2 || x0 + q < n0) W[padq(x0 + q)] = scale(f[q], ipow(xt[q], i));
+                if (P2 || x0 + q < n0) {
+                    const T wx = ft.fx ? ft.fx[(size_t)i * n0 + x0 + q] : ipow(xt[q], i);
+                    W[padq(x0 + q)] = scale(f[q], wx);
+                }
             __syncthreads();
-            const cpx<T> *kt = kp + term_index(i, j) * L0;
+            const cpx<T> *kt = kp + t * L0;
             cpx<T> win[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) win[q] = W[padq(wrapx(x0 - w0 + q))];
@@ -312,12 +308,11 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
     cudaError_t err;
     double *ksum = p->xw + p->n + kSolveTail;  // after the solve's statistics and partial sums
     p->launches += 4;
-    k_kernel_sums<<<p->nk, 256, 0, s>>>(p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x, ksum);
+    k_kernel_sums<<<p->nk, 256, 0, s>>>(p->bv, x, ksum);
     const size_t tot = (size_t)p->nk * p->L0 * p->h1c;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 8192) blocks = 8192;
-    k_kernel_table<T><<<blocks, 256, 0, s>>>(p->n1, p->nk, p->cfg.w0, p->cfg.w1, p->cfg.const_phot_ratio, x,
-                                             ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
+    k_kernel_table<T><<<blocks, 256, 0, s>>>(p->n1, p->bv, x, ksum, (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
     if ((err = cudaGetLastError())) return err;
     {
         const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
@@ -333,7 +328,7 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
             default: break;
         }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->cfg.dk, p->cfg.db, p->cfg.w0, nbkg_off,
+        kern<<<p->h1c, nthr, smem, s>>>(p->n0, p->n1, p->bv, ftab_of<T>(p), p->cfg.w0, nbkg_off,
                                         (const cpx<T> *)p->F, (const cpx<T> *)p->kap, (const cpx<T> *)p->yhat, x,
                                         (cpx<T> *)p->U);
         if ((err = cudaGetLastError())) return err;
@@ -353,25 +348,31 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
 // same way as the subtraction: kappa(a, m) = sum_b K(a, b) exp(-2 pi i m b / N1)
 // and K^(l, m) = sum_a kappa(a, m) exp(-2 pi i l a / N0).
 
-__global__ void k_kernel_image(int w0, int w1, int dk, int cpr, double xt0, double yt0,
-                               const double *__restrict__ x, double *__restrict__ kimg) {
+// Term weights at one normalised position (host-computed): xt0^i yt0^j,
+// B_i(xt0) B_j(yt0), or 1 for the constant term.
+struct TermWeights {
+    double w[kMaxKTerms];
+};
+
+__global__ void k_kernel_image(BasisView bv, TermWeights tw, const double *__restrict__ x, double *__restrict__ kimg) {
+    const int w0 = bv.w0, w1 = bv.w1;
     const int L1 = 2 * w1 + 1, L = (2 * w0 + 1) * L1;
-    const int nk = n_terms(dk);
     for (int e = threadIdx.x; e < L; e += blockDim.x) {
         const int a = e / L1 - w0, b = e % L1 - w1;
         double v = 0.0;
-        for (int t = 0; t < nk; ++t) {
-            int i, j;
-            term_ij(t, &i, &j);
-            const double wt = ipow(xt0, i) * ipow(yt0, j);
+        for (int t = 0; t < bv.nk; ++t) {
+            const double wt = tw.w[t];
             if (a != 0 || b != 0) {
-                v += wt * x[unknown_index(t, a, b, w0, w1, cpr)];
+                const int u = bv.unknown(t, a, b);
+                if (u >= 0) v += wt * x[u];
             } else {
-                const int u0 = unknown_index(t, 0, 0, w0, w1, cpr);
+                const int u0 = bv.unknown(t, 0, 0);
                 double c = u0 >= 0 ? x[u0] : 0.0;
                 for (int o = 0; o < L; ++o) {
                     const int aa = o / L1 - w0, bb = o % L1 - w1;
-                    if (aa != 0 || bb != 0) c -= x[unknown_index(t, aa, bb, w0, w1, cpr)];
+                    if (aa == 0 && bb == 0) continue;
+                    const int u = bv.unknown(t, aa, bb);
+                    if (u >= 0) c -= x[u];
                 }
                 v += wt * c;
             }
@@ -475,7 +476,9 @@ static cudaError_t decorr_t(Plan *p, const double *x, double xt0, double yt0, do
                             const void *diff, void *out, cudaStream_t s) {
     cudaError_t err;
     const int w0 = p->cfg.w0, w1 = p->cfg.w1;
-    k_kernel_image<<<1, 256, 0, s>>>(w0, w1, p->cfg.dk, p->cfg.const_phot_ratio, xt0, yt0, x, p->kimg);
+    TermWeights tw;
+    basis_term_weights(p, xt0, yt0, tw.w);
+    k_kernel_image<<<1, 256, 0, s>>>(p->bv, tw, x, p->kimg);
     const int tot = p->L0 * p->h1c;
     k_decorr_kappa<T><<<(tot + 255) / 256, 256, 0, s>>>(p->n1, w0, w1, p->kimg, (const cpx<T> *)p->tw1,
                                                         (cpx<T> *)p->kap);

@@ -46,7 +46,7 @@ def test_num_unknowns_rejects_negative(lib):
 
 
 def test_struct_layouts(lib):
-    assert ctypes.sizeof(binding.sfft_config) == 9 * 4
+    assert ctypes.sizeof(binding.sfft_config) == 14 * 4
     assert ctypes.sizeof(binding.sfft_solve_info) == 24
 
 
@@ -56,3 +56,31 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         binding.library()
+
+
+def test_unknown_counts_match_the_oracle(lib):
+    """sfft_num_unknowns (no GPU use) for polynomial and B-spline bases equals
+    the oracle's count of the same configuration."""
+    import oracle
+    cases = [((16, 16, 2, 2, 2, 2, 1), None), ((16, 16, 3, 1, 1, 0, 0), None),
+             ((16, 16, 2, 2, 0, 0, 1), (2, 1, 1, 0)), ((16, 16, 1, 3, 0, 0, 0), (3, 2, 2, 3)),
+             ((16, 16, 0, 0, 0, 0, 1), (0, 0, 0, 0))]
+    for (n0, n1, w0, w1, dk, db, cpr), spline in cases:
+        cfg = binding.make_config(n0, n1, w0, w1, dk, db, cpr, spline=spline)
+        oc = oracle.OracleConfig(n0, n1, w0, w1, dk, db, bool(cpr), "poly" if spline is None else "bspline",
+                                 *(spline or (0, 0, 0, 0)))
+        assert binding.sfft_num_unknowns(cfg) == oracle.num_unknowns(oc)
+
+
+def test_bspline_config_checks(lib):
+    """Basis fields are checked before any CUDA call."""
+    h = ctypes.c_void_p()
+    for spline, dk, want in (((4, 0, 1, 0), 0, binding.SFFT_ERR_UNSUPPORTED),   # degree above 3
+                             ((2, 4, 1, 0), 0, binding.SFFT_ERR_UNSUPPORTED),   # K = 7 > 6
+                             ((2, 0, 1, 0), 1, binding.SFFT_ERR_INVALID),       # dk must be 0
+                             ((-1, 0, 1, 0), 0, binding.SFFT_ERR_INVALID)):
+        cfg = binding.make_config(64, 64, 2, 2, dk, 0, 1, spline=spline)
+        assert lib.sfft_plan_create(ctypes.byref(cfg), None, ctypes.byref(h)) == want
+    bad = binding.make_config(64, 64, 2, 2, 0, 0, 1)
+    bad.basis = 7
+    assert lib.sfft_plan_create(ctypes.byref(bad), None, ctypes.byref(h)) == binding.SFFT_ERR_INVALID

@@ -66,3 +66,26 @@ def test_decorrelation_matches_oracle(case, precision):
     assert np.sqrt(np.mean((od - ref) ** 2)) <= tol
     assert np.array_equal(inplace.cpu().numpy(), out.cpu().numpy())
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cpr", [0, 1])
+def test_bspline_decorrelation_matches_oracle(cpr):
+    """The kernel of Eq. 8 at (xt0, yt0) (B-spline weights) in the filter of Eq. 24."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan
+    n0, n1, w0, w1 = 64, 48, 2, 2
+    spline = (2, 1, 1, 0)
+    R = random_field(n0, n1, 77)
+    S = 0.9 * np.roll(R, (1, -1), axis=(0, 1)) + 0.3 * random_field(n0, n1, 78)
+    plan = SfftPlan(n0, n1, w0, w1, 0, 0, cpr, dtype="float64", precision="fp64", spline=spline)
+    D, x, info, _, _ = plan.run_pair(torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda())
+    xt0, yt0, sr, ss = -0.3, 0.55, 5.0, 7.0
+    out = plan.decorrelate(x, D, sr, ss, xt0, yt0)
+    torch.cuda.synchronize()
+    xd, Dd, od = x.cpu().numpy(), D.cpu().numpy(), out.cpu().numpy()
+    k = decorr.kernel_image(xd, w0, w1, 0, 0, bool(cpr), xt0, yt0, spline=spline)
+    ref = decorr.decorrelate(Dd, k, sr, ss)
+    assert np.sqrt(np.mean((od - ref) ** 2)) <= 1e-10 * np.sqrt(np.mean(Dd ** 2))
+    plan.close()

@@ -33,10 +33,10 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def gpu_run(R, S, w0, w1, dk, db, cpr, precision, dtype, mask=None):
+def gpu_run(R, S, w0, w1, dk, db, cpr, precision, dtype, mask=None, spline=None):
     from paper_2109_09334_gb300 import SfftPlan, info_from_bytes
     n0, n1 = R.shape
-    plan = SfftPlan(n0, n1, w0, w1, dk, db, cpr, dtype=dtype, precision=precision)
+    plan = SfftPlan(n0, n1, w0, w1, dk, db, cpr, dtype=dtype, precision=precision, spline=spline)
     tdt = torch.float32 if dtype == "float32" else torch.float64
     Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda", tdt)
     St = torch.from_numpy(np.ascontiguousarray(S)).to("cuda", tdt)
@@ -73,6 +73,56 @@ SMALL = [
     (17, 19, 1, 1, 1, 0, 0, False),
     (100, 96, 4, 4, 2, 2, 1, False),
 ]
+
+
+# B-spline bases (Eq. 7-9): n0, n1, w0, w1, cpr, kdeg, kint, bdeg, bint, masked
+SPLINE = [
+    (32, 32, 2, 2, 1, 1, 0, 1, 0, False),   # linear, no interior knot, constant ratio
+    (64, 48, 2, 3, 0, 2, 1, 1, 1, True),    # quadratic, varying ratio, Bluestein rows
+    (48, 64, 3, 2, 1, 3, 0, 2, 1, False),   # cubic, direct lag sums along x
+    (64, 64, 2, 2, 1, 0, 2, 0, 1, True),    # piecewise constant in three spans
+    (128, 64, 3, 2, 1, 2, 2, 2, 0, False),
+    (40, 37, 1, 2, 0, 1, 1, 1, 0, False),   # neither axis a power of two
+]
+
+
+def check_against_oracle(R, S, c, precision, mask, g):
+    """The tolerances of the module docstring, oracle config c vs GPU result g."""
+    Mo, ro = oracle.build_system(R, S, c, mask=mask)
+    xo = oracle.cholesky_solve(Mo, ro)
+    Do = oracle.subtract(R, S, xo, c)
+    assert g["info"]["status"] == 0, g["info"]
+    if precision == "fp64":
+        assert rel(g["M"], Mo) <= 1e-10
+        assert rel(g["rhs"], ro) <= 1e-10
+        assert rel(g["x"], xo) <= 1e-8
+        assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
+    else:
+        # inputs rounded to float32 on both sides for the system check
+        R32, S32 = R.astype(np.float32).astype(np.float64), S.astype(np.float32).astype(np.float64)
+        Mo32, ro32 = oracle.build_system(R32, S32, c, mask=mask)
+        assert rel(g["M"], Mo32) <= 1e-5
+        assert rel(g["rhs"], ro32) <= 1e-5
+        xs = np.linalg.solve(g["M"], g["rhs"])
+        assert rel(g["x"], xs) <= 1e-8
+        Do32 = oracle.subtract(R32, S32, oracle.cholesky_solve(Mo32, ro32), c)
+        assert np.sqrt(np.mean((g["D"] - Do32) ** 2)) <= 1e-3 * SIGMA
+
+
+@pytest.mark.parametrize("case", SPLINE)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bspline_cases_against_oracle(case, precision):
+    n0, n1, w0, w1, cpr, kdeg, kint, bdeg, bint, masked = case
+    R, S = small_pair(n0, n1, seed=n0 + 5 * n1 + kdeg)
+    mask = None
+    if masked:
+        mask = (np.random.default_rng(n1).random((n0, n1)) > 0.15).astype(np.uint8)
+    c = oracle.OracleConfig(n0, n1, w0, w1, 0, 0, bool(cpr), "bspline", kdeg, kint, bdeg, bint)
+    dtype = "float64" if precision == "fp64" else "float32"
+    g = gpu_run(R, S, w0, w1, 0, 0, cpr, precision, dtype, mask, spline=(kdeg, kint, bdeg, bint))
+    assert g["M"].shape == (oracle.num_unknowns(c),) * 2
+    check_against_oracle(R, S, c, precision, mask, g)
+    g["plan"].close()
 
 
 @pytest.mark.parametrize("case", SMALL)
