@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stages", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 single-pair comparison")
+    ap.add_argument("--no-bspline", action="store_true", help="skip the B-spline basis measurement")
     ap.add_argument("--mode", default="full", choices=["full", "pair"],
                     help="pair: only warmup + steps pairs through sfft_run_pair (for profiler captures)")
     ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
@@ -540,6 +541,50 @@ def run_ours(args):
                                       "note": "plain FP64 path, sfft_run_pair, same inputs; D of the mixed path "
                                               "compared with it on pair 0"}
         p64.close()
+
+    # the same pairs with the B-spline basis of Eq. 7-9 (piecewise-linear
+    # kernel variation with one interior knot, quadratic background with one
+    # interior knot), one pair at a time, with its stage times
+    if not args.no_bspline:
+        spl = (1, 1, 2, 1)
+        pb = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, 0, 0, f.const_phot_ratio, dtype=spec.dtype,
+                      precision=args.precision, spline=spl)
+        sb = pb.stream
+        Db = torch.empty_like(D)
+        xb = torch.empty(pb.n, dtype=torch.float64, device=dev)
+        ib = torch.zeros_like(info)
+        for k in range(2):
+            binding.sfft_run_pair(pb.handle, dev_pairs[k & 1][0], dev_pairs[k & 1][1], None, None, None, xb, ib,
+                                  Db, sb)
+        kb = 10
+        l0 = binding.sfft_plan_launch_count(pb.handle)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sb)
+        for k in range(kb):
+            binding.sfft_run_pair(pb.handle, dev_pairs[k & 1][0], dev_pairs[k & 1][1], None, None, None, xb, ib,
+                                  Db, sb)
+        e1.record(sb)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / kb
+        lb = binding.sfft_plan_launch_count(pb.handle) - l0
+        bst = {}
+        for st, name in enumerate(binding.STAGE_NAMES):
+            for _ in range(2):
+                binding.sfft_replay_stage(pb.handle, st, sb)
+            e0.record(sb)
+            for _ in range(5):
+                binding.sfft_replay_stage(pb.handle, st, sb)
+            e1.record(sb)
+            torch.cuda.synchronize()
+            bst[name] = round(e0.elapsed_time(e1) / 5, 4)
+        result["bspline"] = {"value": world * 1e3 / tb, "unit": UNIT, "ms_per_pair": tb, "steps": kb,
+                             "gpu_launches": int(lb), "n": pb.n,
+                             "basis": {"kernel_degree": spl[0], "kernel_interior_knots": spl[1],
+                                       "background_degree": spl[2], "background_interior_knots": spl[3]},
+                             "stages_ms": bst, "solve": info_from_bytes(ib.cpu().numpy()),
+                             "api": "sfft_run_pair, one pair at a time, same inputs as the headline"}
+        pb.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

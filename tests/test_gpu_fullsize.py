@@ -120,3 +120,51 @@ def test_fp64_path_sampled_parity_4096():
     # D is written as float32 (the image type): compare within its rounding too
     assert np.sqrt(np.mean((D.ravel()[pix] - De) ** 2)) <= 1e-6 * spec.sigma + 1e-7 * np.sqrt(np.mean(De ** 2))
     plan.close()
+
+
+# The 4096^2 pair with tensor-product B-splines (Eq. 7-9): piecewise-linear
+# kernel variation with one interior knot (K = 3), quadratic background with
+# one interior knot (K' = 4), w = 8, constant ratio: 2609 unknowns.
+BSPLINE_4096 = (1, 1, 2, 1)
+
+
+def test_bspline_sampled_parity_4096():
+    """Mixed path, B-spline basis, 4096^2: the sampled checks of test_sampled_parity."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, info_from_bytes
+    from paper_2109_09334_gb300.build import build
+    build()
+    spec = synth.PAIR4096
+    f = spec.fit
+    R, S = synth.make_pair(spec, seed=6)
+    R32, S32 = R.astype(np.float32), S.astype(np.float32)
+    plan = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, 0, 0, True, dtype="float32", precision="mixed",
+                    spline=BSPLINE_4096)
+    D, x, info, M, rhs = plan.run_pair(torch.from_numpy(R32).cuda(), torch.from_numpy(S32).cuda(),
+                                       keep_system=True)
+    torch.cuda.synchronize()
+    M, rhs, x, D = M.cpu().numpy(), rhs.cpu().numpy(), x.cpu().numpy(), D.cpu().numpy().astype(np.float64)
+    inf = info_from_bytes(info.cpu().numpy())
+    assert inf["status"] == 0, inf
+    n = rhs.shape[0]
+    c = oracle.OracleConfig(spec.n0, spec.n1, f.w0, f.w1, 0, 0, True, "bspline", *BSPLINE_4096)
+    assert n == oracle.num_unknowns(c) == 2609
+    rng = np.random.default_rng(17)
+    rows = np.concatenate([rng.integers(0, n, 300), np.arange(0, n, max(1, n // 100))[:100]])
+    cols = np.concatenate([rng.integers(0, n, 300), np.arange(0, n, max(1, n // 100))[:100]])
+    Me = oracle.system_entries(R32, S32, c, rows, cols)
+    Mg = M[rows, cols]
+    d = np.sqrt(np.abs(np.diag(M)))
+    assert np.sqrt(np.mean((Mg - Me) ** 2)) <= 1e-5 * np.sqrt(np.mean(Me ** 2))
+    assert np.max(np.abs(Mg - Me) / (d[rows] * d[cols])) <= 1e-4
+    rr = rng.integers(0, n, 150)
+    re = oracle.system_entries(R32, S32, c, rr, -np.ones_like(rr))
+    assert np.sqrt(np.mean((rhs[rr] - re) ** 2)) <= 1e-5 * np.sqrt(np.mean(re ** 2))
+    assert np.max(np.abs(rhs[rr] - re)) <= 1e-4 * np.sqrt(np.mean(re ** 2))
+    xs = np.linalg.solve(M, rhs)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    pix = rng.integers(0, spec.n0 * spec.n1, 2000)
+    De = oracle.subtract_pixels(R32, S32, x, c, pix)
+    assert np.sqrt(np.mean((D.ravel()[pix] - De) ** 2)) <= 1e-3 * spec.sigma
+    plan.close()
