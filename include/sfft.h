@@ -215,6 +215,32 @@ int sfft_decorrelate(sfft_plan_t plan, const double *d_x, double xt0, double yt0
                      double sigma_sci, const void *d_diff, void *d_out, sfft_stream_t stream);
 
 /*
+ * Noise decorrelation in the co-added form of App. C (Eq. 21-24 in full):
+ * the difference image was made as D = sum_j S_j (*) G_j - [sum_i R_i (*) H_i] (*) K
+ * from M science and N reference exposures with white noise sigma_Sj,
+ * sigma_Ri, homogenised by the kernels G_j, H_i (divided by M and N, as
+ * Eq. 21 states) and co-added.  The real filter
+ *     Q^ = sqrt(s_D^2 / (sum_j s_Sj^2 |G^_j|^2 + |K^|^2 sum_i s_Ri^2 |H^_i|^2)),
+ * normalised to unit kernel sum (s_D^2 = the denominator at frequency 0),
+ * is applied as in sfft_decorrelate, with K the kernel of this plan's
+ * coefficients d_x at (xt0, yt0).
+ *   n_sci, n_ref     : M and N, each 1..16.
+ *   d_G, d_H         : device FP64 kernel images, centred, [n_sci][2g0+1][2g1+1]
+ *                      and [n_ref][2g0+1][2g1+1] (row-major, offset a = -g0 first).
+ *   h_sigma_sci/_ref : host arrays of the noise levels (>= 0; not all science ones 0).
+ *   g0, g1           : half-widths of G and H, 0..32, 2g+1 at most the image size.
+ * Where the denominator vanishes (every G^_j and H^_i zero at a frequency)
+ * the output is not finite.  Allocates the plan's table of the kernels' row
+ * spectra on first use (or when larger kernels are given); otherwise as
+ * sfft_decorrelate (asynchronous on `stream`, d_out may equal d_diff).
+ */
+int sfft_decorrelate_coadd(sfft_plan_t plan, const double *d_x, double xt0, double yt0,
+                           int32_t n_sci, const double *d_G, const double *h_sigma_sci,
+                           int32_t n_ref, const double *d_H, const double *h_sigma_ref,
+                           int32_t g0, int32_t g1, const void *d_diff, void *d_out,
+                           sfft_stream_t stream);
+
+/*
  * One whole pair on device buffers: build, solve and subtract.  d_M, d_rhs,
  * d_x and d_info may be NULL, in which case plan-owned buffers are used.
  */

@@ -1,5 +1,8 @@
 """Noise decorrelation of the difference image (App. C, Eq. 21-24), FP64.
 
+Two forms: one pair (below) and the co-added form of Eq. 21-24 in full
+(decorrelate_coadd).
+
 TEST INFRASTRUCTURE ONLY (see the package header): imported by the tests.
 
 For one pair with no co-addition (M = N = 1 and G = H = delta in Eq. 21),
@@ -70,4 +73,37 @@ def decorrelate(D, k, sigma_ref, sigma_sci):
     """D (*) Q, circular, with Q from filter_spectrum."""
     D = np.asarray(D, np.float64)
     q = filter_spectrum(k, D.shape[0], D.shape[1], sigma_ref, sigma_sci)
+    return np.real(np.fft.ifft2(np.fft.fft2(D) * q))
+
+
+def kernel_spectrum(k, n0, n1):
+    """2-D DFT of a centred kernel image k (half-widths k.shape // 2) placed
+    circularly on the n0 x n1 grid."""
+    w0, w1 = k.shape[0] // 2, k.shape[1] // 2
+    full = np.zeros((n0, n1))
+    for a in range(-w0, w0 + 1):
+        for b in range(-w1, w1 + 1):
+            full[a % n0, b % n1] += k[a + w0, b + w1]
+    return np.fft.fft2(full)
+
+
+def coadd_filter(k, n0, n1, sigma_sci, G, sigma_ref, H):
+    """Q0 of Eq. 24 for D = sum_j S_j (*) G_j - [sum_i R_i (*) H_i] (*) K (Eq. 21):
+    sqrt(s_D^2 / (sum_j s_Sj^2 |G^_j|^2 + |K^|^2 sum_i s_Ri^2 |H^_i|^2)),
+    with s_D^2 the denominator at frequency 0 (unit kernel sum)."""
+    kh = kernel_spectrum(k, n0, n1)
+    den = np.zeros((n0, n1))
+    for s, g in zip(sigma_sci, G):
+        den += s ** 2 * np.abs(kernel_spectrum(g, n0, n1)) ** 2
+    dh = np.zeros((n0, n1))
+    for s, h in zip(sigma_ref, H):
+        dh += s ** 2 * np.abs(kernel_spectrum(h, n0, n1)) ** 2
+    den = den + np.abs(kh) ** 2 * dh
+    return np.sqrt(den[0, 0] / den)
+
+
+def decorrelate_coadd(D, k, sigma_sci, G, sigma_ref, H):
+    """D (*) Q, circular, with Q from coadd_filter."""
+    D = np.asarray(D, np.float64)
+    q = coadd_filter(k, D.shape[0], D.shape[1], sigma_sci, G, sigma_ref, H)
     return np.real(np.fft.ifft2(np.fft.fft2(D) * q))

@@ -129,6 +129,15 @@ class SfftPlan:
         binding.sfft_decorrelate(self.handle, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, self.stream)
         return out
 
+    def decorrelate_coadd(self, x, diff, G, sigma_sci, H, sigma_ref, xt0=0.0, yt0=0.0, out=None):
+        """Noise decorrelation in the co-added form of App. C (sfft_decorrelate_coadd):
+        G, H: FP64 CUDA tensors [n, 2g0+1, 2g1+1] of the homogenisation kernels."""
+        torch = _torch()
+        out = out if out is not None else torch.empty_like(diff)
+        binding.sfft_decorrelate_coadd(self.handle, x, xt0, yt0, G.contiguous(), sigma_sci, H.contiguous(),
+                                       sigma_ref, diff, out, self.stream)
+        return out
+
     def run_pair(self, ref, sci, mask=None, out=None, keep_system=False):
         torch = _torch()
         self._check_img(ref), self._check_img(sci)

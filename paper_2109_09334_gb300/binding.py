@@ -108,6 +108,8 @@ def library():
         lib.sfft_pool_wait.argtypes = [vp, ptk, ctypes.c_int64]
         lib.sfft_pool_usage.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32)]
         lib.sfft_plan_autotune.argtypes = [vp, vp, vp, vp, vp]
+        dbl = ctypes.c_double
+        lib.sfft_decorrelate_coadd.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, i32, vp, vp, i32, i32, vp, vp, vp]
         lib.sfft_plan_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.sfft_plan_set_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
@@ -211,6 +213,19 @@ def sfft_solve_static(d_M, d_rhs, n, precision, d_x, d_info=None, stream=None):
 def sfft_decorrelate(plan, d_x, xt0, yt0, sigma_ref, sigma_sci, d_diff, d_out, stream=None):
     _check(library().sfft_decorrelate(plan, _p(d_x), float(xt0), float(yt0), float(sigma_ref), float(sigma_sci),
                                       _p(d_diff), _p(d_out), _s(stream)), "sfft_decorrelate")
+
+
+def sfft_decorrelate_coadd(plan, d_x, xt0, yt0, d_G, sigma_sci, d_H, sigma_ref, d_diff, d_out, stream=None):
+    """d_G: [n_sci, 2g0+1, 2g1+1] and d_H: [n_ref, 2g0+1, 2g1+1] FP64 device tensors; sigma_*: sequences."""
+    n_sci, n_ref = int(d_G.shape[0]), int(d_H.shape[0])
+    g0, g1 = int(d_G.shape[1]) // 2, int(d_G.shape[2]) // 2
+    if tuple(d_H.shape[1:]) != tuple(d_G.shape[1:]) or len(sigma_sci) != n_sci or len(sigma_ref) != n_ref:
+        raise ValueError("sfft_decorrelate_coadd: kernel shapes and noise levels do not match")
+    ss = (ctypes.c_double * n_sci)(*[float(v) for v in sigma_sci])
+    sr = (ctypes.c_double * n_ref)(*[float(v) for v in sigma_ref])
+    _check(library().sfft_decorrelate_coadd(plan, _p(d_x), float(xt0), float(yt0), n_sci, _p(d_G), ss, n_ref,
+                                            _p(d_H), sr, g0, g1, _p(d_diff), _p(d_out), _s(stream)),
+           "sfft_decorrelate_coadd")
 
 
 def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):

@@ -133,7 +133,7 @@ void plan_free(Plan *p) {
                     p->twpm0, p->kimg, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->lag, p->A,
                     p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own, p->x_own, p->info_own,
                     p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap, p->d_int, p->ftab, p->ftab64,
-                    p->bxy64, p->d_zdesc, p->d_rdesc, p->z0, p->cmat, p->unk};
+                    p->bxy64, p->d_zdesc, p->d_rdesc, p->z0, p->cmat, p->unk, p->gam};
     for (void *b : bufs)
         if (b) cudaFree(b);
     free(p->h_int);
@@ -619,7 +619,50 @@ int sfft_decorrelate(sfft_plan_t plan, const double *d_x, double xt0, double yt0
     if (!(xt0 >= -1.0 && xt0 <= 1.0) || !(yt0 >= -1.0 && yt0 <= 1.0)) return SFFT_ERR_INVALID;
     Plan *p = (Plan *)plan;
     p->last_stream = (cudaStream_t)stream;
-    return status_of(decorrelate(p, d_x, xt0, yt0, sigma_ref, sigma_sci, d_diff, d_out, (cudaStream_t)stream));
+    return status_of(
+        decorrelate(p, d_x, xt0, yt0, sigma_ref, sigma_sci, d_diff, d_out, nullptr, (cudaStream_t)stream));
+}
+
+int sfft_decorrelate_coadd(sfft_plan_t plan, const double *d_x, double xt0, double yt0, int32_t n_sci,
+                           const double *d_G, const double *h_sigma_sci, int32_t n_ref, const double *d_H,
+                           const double *h_sigma_ref, int32_t g0, int32_t g1, const void *d_diff, void *d_out,
+                           sfft_stream_t stream) {
+    if (!plan || !d_x || !d_diff || !d_out || !d_G || !d_H || !h_sigma_sci || !h_sigma_ref) return SFFT_ERR_INVALID;
+    if (!(xt0 >= -1.0 && xt0 <= 1.0) || !(yt0 >= -1.0 && yt0 <= 1.0)) return SFFT_ERR_INVALID;
+    if (n_sci < 1 || n_ref < 1 || n_sci > kMaxCoadd || n_ref > kMaxCoadd) return SFFT_ERR_INVALID;
+    Plan *p = (Plan *)plan;
+    if (g0 < 0 || g1 < 0 || g0 > 32 || g1 > 32 || 2 * g0 + 1 > p->n0 || 2 * g1 + 1 > p->n1) return SFFT_ERR_INVALID;
+    Coadd co{};
+    co.ns = n_sci;
+    co.nr = n_ref;
+    co.g0 = g0;
+    co.g1 = g1;
+    co.G = d_G;
+    co.H = d_H;
+    double ssum = 0.0;
+    for (int j = 0; j < n_sci; ++j) {
+        if (!(h_sigma_sci[j] >= 0.0)) return SFFT_ERR_INVALID;
+        co.sigma2[j] = h_sigma_sci[j] * h_sigma_sci[j];
+        ssum += co.sigma2[j];
+    }
+    for (int i = 0; i < n_ref; ++i) {
+        if (!(h_sigma_ref[i] >= 0.0)) return SFFT_ERR_INVALID;
+        co.sigma2[n_sci + i] = h_sigma_ref[i] * h_sigma_ref[i];
+    }
+    if (!(ssum > 0.0)) return SFFT_ERR_INVALID;
+    const size_t need = (size_t)(n_sci + n_ref) * (2 * g0 + 1) * p->h1c * p->csz;
+    if (need > p->gam_bytes) {  // plan-owned table, grown on demand
+        if (p->gam) cudaFree(p->gam);
+        p->gam = nullptr;
+        p->gam_bytes = 0;
+        if (cudaMalloc(&p->gam, need) != cudaSuccess) {
+            cudaGetLastError();
+            return SFFT_ERR_OOM;
+        }
+        p->gam_bytes = need;
+    }
+    p->last_stream = (cudaStream_t)stream;
+    return status_of(decorrelate(p, d_x, xt0, yt0, 0.0, 1.0, d_diff, d_out, &co, (cudaStream_t)stream));
 }
 
 int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask, double *d_M,

@@ -75,6 +75,8 @@ struct FTab {
 constexpr int kMaxKTerms = 40;
 constexpr int kMaxBTerms = 36;
 constexpr int kMaxFun = 8;
+// Largest number of science (and of reference) images in the co-added form of the decorrelation.
+constexpr int kMaxCoadd = 16;
 
 struct Plan {
     sfft_config cfg;
@@ -138,6 +140,8 @@ struct Plan {
     void *img_ref, *img_sci, *img_diff;
     uint8_t *img_mask;
     void *kap;             // [nk][L0][m] kernel row spectra (compute type)
+    void *gam;             // co-added decorrelation: row spectra of the homogenisation kernels
+    size_t gam_bytes;
     size_t ws_bytes;
     uint64_t launches;     // kernels this plan has enqueued
     // buffers of the most recent run_pair (for sfft_replay_stage)
@@ -203,8 +207,16 @@ struct SolveBuffers {
 };
 cudaError_t solve_on_buffers(const SolveBuffers &b, const double *M, const double *rhs, double *x,
                              sfft_solve_info *info, cudaStream_t s);
+// The co-added form of App. C (Eq. 21): ns science and nr reference
+// homogenisation kernels (FP64 device images, half-widths g0, g1) and their
+// noise variances sigma2[0 .. ns+nr).  Null: the one-pair form.
+struct Coadd {
+    int ns, nr, g0, g1;
+    const double *G, *H;
+    double sigma2[2 * kMaxCoadd];
+};
 cudaError_t decorrelate(Plan *p, const double *x, double xt0, double yt0, double sigma_ref, double sigma_sci,
-                        const void *diff, void *out, cudaStream_t s);
+                        const void *diff, void *out, const Coadd *co, cudaStream_t s);
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s);
 cudaError_t plan_tables(Plan *p, cudaStream_t s);
 

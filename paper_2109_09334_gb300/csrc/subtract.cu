@@ -382,17 +382,29 @@ __global__ void k_kernel_image(BasisView bv, TermWeights tw, const double *__res
 }
 
 // kap[a + w0][m] = sum_b K(a, b) exp(-2 pi i m b / N1)
+// for nkern centred kernels of half-widths w0, w1 (kernel c at kimg_a for
+// c < na, else kimg_b): kap[c][a + w0][m] = sum_b k_c(a, b) exp(-2 pi i m b / N1)
 template <typename T>
-__global__ void k_decorr_kappa(int n1, int w0, int w1, const double *__restrict__ kimg,
-                               const cpx<T> *__restrict__ tw1, cpx<T> *__restrict__ kap) {
+__global__ void k_decorr_kappa(int n1, int nkern, int na, int w0, int w1, const double *__restrict__ kimg_a,
+                               const double *__restrict__ kimg_b, const cpx<T> *__restrict__ tw1,
+                               cpx<T> *__restrict__ kap) {
     const int h1c = n1 / 2 + 1, L0 = 2 * w0 + 1, L1 = 2 * w1 + 1;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L0 * h1c; e += gridDim.x * blockDim.x) {
-        const int a = e / h1c, m = e - a * h1c;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nkern * L0 * h1c; e += gridDim.x * blockDim.x) {
+        const int ca = e / h1c, m = e - ca * h1c;
+        const int c = ca / L0, a = ca - c * L0;
+        const double *k = c < na ? kimg_a + (size_t)c * L0 * L1 : kimg_b + (size_t)(c - na) * L0 * L1;
         cpx<T> v = mk((T)0, (T)0);
-        for (int bi = 0; bi < L1; ++bi) v = v + scale(tw1[imod(m * (bi - w1), n1)], (T)kimg[a * L1 + bi]);
+        for (int bi = 0; bi < L1; ++bi) v = v + scale(tw1[imod(m * (bi - w1), n1)], (T)k[a * L1 + bi]);
         kap[e] = v;
     }
 }
+
+// The co-added form of Eq. 21: ns science kernels G_j then nr reference
+// kernels H_i (half-widths g0 along x), their noise variances s2[0 .. ns+nr).
+struct CoaddDesc {
+    int ns, nr, g0;
+    double s2[2 * kMaxCoadd];
+};
 
 // Forward real transform of the rows of D, two rows per complex transform,
 // written as Dt[m][x] (m < N1/2 + 1): pow2 n1 by the radix-16 FFT, other n1
@@ -437,18 +449,22 @@ __global__ void __launch_bounds__(512) k_decorr_cols(int n0, int n1, int mlen, i
                                                       double sigma_ref, double sigma_sci,
                                                       const cpx<T> *__restrict__ kap, const cpx<T> *__restrict__ tw0,
                                                       const cpx<T> *__restrict__ twg, const cpx<T> *__restrict__ chirp,
-                                                      const cpx<T> *__restrict__ bfilt, cpx<T> *__restrict__ Dt) {
+                                                      const cpx<T> *__restrict__ bfilt, cpx<T> *__restrict__ Dt,
+                                                      CoaddDesc cd, const cpx<T> *__restrict__ gam) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = mlen / 16;
     const int ntw = BLU ? 0 : pass_table_len(n0);
     const int L0 = 2 * w0 + 1;
+    const int nc = cd.ns + cd.nr, Lg = 2 * cd.g0 + 1;  // nc = 0: the one-pair form
     cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // pass table (pow2)
     cpx<T> *kp = tw + ntw;                               // L0: kappa(a, m)
-    cpx<T> *zr = kp + L0;                                // padded mlen
+    cpx<T> *gp = kp + L0;                                // nc * Lg: gamma_c(a, m)
+    cpx<T> *zr = gp + nc * Lg;                           // padded mlen
     const int tid = threadIdx.x, m = blockIdx.x;
     const int h1c = n1 / 2 + 1;
     for (int q = tid; q < ntw; q += G) tw[q] = twg[q];
     for (int a = tid; a < L0; a += G) kp[a] = kap[(size_t)a * h1c + m];
+    for (int e = tid; e < nc * Lg; e += G) gp[e] = gam[(size_t)e * h1c + m];
     double k00 = 0.0;  // K^(0, 0): the kernel sum
     for (int a = 0; a < L0; ++a) k00 += (double)kap[(size_t)a * h1c].re;
     cpx<T> *col = Dt + (size_t)m * n0;
@@ -456,13 +472,39 @@ __global__ void __launch_bounds__(512) k_decorr_cols(int n0, int n1, int mlen, i
     __syncthreads();
     if (BLU) bluestein(zr, n0, mlen, -1, chirp, bfilt, twg, tid, G);
     else group_fft(zr, n0, -1, tw, tid, G);
-    const double ss2 = sigma_sci * sigma_sci, sr2 = sigma_ref * sigma_ref;
-    const T num = (T)(ss2 + sr2 * k00 * k00);
-    for (int l = tid; l < n0; l += G) {
-        cpx<T> kh = mk((T)0, (T)0);
-        for (int a = 0; a < L0; ++a) kh = kh + cmul(kp[a], tw0[imod(l * (a - w0), n0)]);
-        const T q = sqrt(num / ((T)ss2 + (T)sr2 * (kh.re * kh.re + kh.im * kh.im)));
-        zr[pad16(l)] = scale(zr[pad16(l)], q);
+    if (nc == 0) {
+        const double ss2 = sigma_sci * sigma_sci, sr2 = sigma_ref * sigma_ref;
+        const T num = (T)(ss2 + sr2 * k00 * k00);
+        for (int l = tid; l < n0; l += G) {
+            cpx<T> kh = mk((T)0, (T)0);
+            for (int a = 0; a < L0; ++a) kh = kh + cmul(kp[a], tw0[imod(l * (a - w0), n0)]);
+            const T q = sqrt(num / ((T)ss2 + (T)sr2 * (kh.re * kh.re + kh.im * kh.im)));
+            zr[pad16(l)] = scale(zr[pad16(l)], q);
+        }
+    } else {
+        // Eq. 23-24 in full: den = sum_j s_Sj^2 |G^_j|^2 + |K^|^2 sum_i s_Ri^2 |H^_i|^2,
+        // normalised by its value at frequency 0 (unit kernel sum)
+        double ds = 0.0, dr = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            double g00 = 0.0;
+            for (int a = 0; a < Lg; ++a) g00 += (double)gam[((size_t)c * Lg + a) * h1c].re;
+            (c < cd.ns ? ds : dr) += cd.s2[c] * g00 * g00;
+        }
+        const T num = (T)(ds + k00 * k00 * dr);
+        for (int l = tid; l < n0; l += G) {
+            cpx<T> kh = mk((T)0, (T)0);
+            for (int a = 0; a < L0; ++a) kh = kh + cmul(kp[a], tw0[imod(l * (a - w0), n0)]);
+            T es = (T)0, er = (T)0;
+            for (int c = 0; c < nc; ++c) {
+                cpx<T> gh = mk((T)0, (T)0);
+                for (int a = 0; a < Lg; ++a) gh = gh + cmul(gp[c * Lg + a], tw0[imod(l * (a - cd.g0), n0)]);
+                const T e2 = (T)cd.s2[c] * (gh.re * gh.re + gh.im * gh.im);
+                if (c < cd.ns) es += e2;
+                else er += e2;
+            }
+            const T q = sqrt(num / (es + (kh.re * kh.re + kh.im * kh.im) * er));
+            zr[pad16(l)] = scale(zr[pad16(l)], q);
+        }
     }
     __syncthreads();
     if (BLU) bluestein(zr, n0, mlen, 1, chirp, bfilt, twg, tid, G);
@@ -473,16 +515,28 @@ __global__ void __launch_bounds__(512) k_decorr_cols(int n0, int n1, int mlen, i
 
 template <typename T>
 static cudaError_t decorr_t(Plan *p, const double *x, double xt0, double yt0, double sr, double ss,
-                            const void *diff, void *out, cudaStream_t s) {
+                            const void *diff, void *out, const Coadd *co, cudaStream_t s) {
     cudaError_t err;
     const int w0 = p->cfg.w0, w1 = p->cfg.w1;
     TermWeights tw;
     basis_term_weights(p, xt0, yt0, tw.w);
     k_kernel_image<<<1, 256, 0, s>>>(p->bv, tw, x, p->kimg);
     const int tot = p->L0 * p->h1c;
-    k_decorr_kappa<T><<<(tot + 255) / 256, 256, 0, s>>>(p->n1, w0, w1, p->kimg, (const cpx<T> *)p->tw1,
-                                                        (cpx<T> *)p->kap);
+    k_decorr_kappa<T><<<(tot + 255) / 256, 256, 0, s>>>(p->n1, 1, 1, w0, w1, p->kimg, nullptr,
+                                                        (const cpx<T> *)p->tw1, (cpx<T> *)p->kap);
     p->launches += 2;
+    CoaddDesc cd{};
+    if (co) {  // row spectra of the homogenisation kernels, science then reference
+        cd.ns = co->ns;
+        cd.nr = co->nr;
+        cd.g0 = co->g0;
+        for (int c = 0; c < co->ns + co->nr; ++c) cd.s2[c] = co->sigma2[c];
+        const int totc = (co->ns + co->nr) * (2 * co->g0 + 1) * p->h1c;
+        k_decorr_kappa<T><<<(totc + 255) / 256, 256, 0, s>>>(p->n1, co->ns + co->nr, co->ns, co->g0, co->g1,
+                                                             co->G, co->H, (const cpx<T> *)p->tw1,
+                                                             (cpx<T> *)p->gam);
+        p->launches++;
+    }
     if ((err = cudaGetLastError())) return err;
     {  // rows
         const int G = p->m1 / 16;
@@ -518,12 +572,13 @@ static cudaError_t decorr_t(Plan *p, const double *x, double xt0, double yt0, do
     {  // columns
         const int G = p->m0 / 16;
         const int ntw = p->gen0 ? 0 : pass_table_len(p->n0);
-        const size_t smem = ((size_t)ntw + p->L0 + padded_len(p->m0)) * sizeof(cpx<T>);
+        const int ncg = (cd.ns + cd.nr) * (2 * cd.g0 + 1);
+        const size_t smem = ((size_t)ntw + p->L0 + ncg + padded_len(p->m0)) * sizeof(cpx<T>);
         auto kern = p->gen0 ? k_decorr_cols<T, true> : k_decorr_cols<T, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<p->h1c, G, smem, s>>>(p->n0, p->n1, p->m0, w0, sr, ss, (const cpx<T> *)p->kap, (const cpx<T> *)p->tw0,
                                      (const cpx<T> *)(p->gen0 ? p->twpm0 : p->twp0), (const cpx<T> *)p->chirp0,
-                                     (const cpx<T> *)p->bfilt0, (cpx<T> *)p->U);
+                                     (const cpx<T> *)p->bfilt0, (cpx<T> *)p->U, cd, (const cpx<T> *)p->gam);
         p->launches++;
         if ((err = cudaGetLastError())) return err;
     }
@@ -532,9 +587,9 @@ static cudaError_t decorr_t(Plan *p, const double *x, double xt0, double yt0, do
 }
 
 cudaError_t decorrelate(Plan *p, const double *x, double xt0, double yt0, double sigma_ref, double sigma_sci,
-                        const void *diff, void *out, cudaStream_t s) {
-    return p->fp64 ? decorr_t<double>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, s)
-                   : decorr_t<float>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, s);
+                        const void *diff, void *out, const Coadd *co, cudaStream_t s) {
+    return p->fp64 ? decorr_t<double>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, co, s)
+                   : decorr_t<float>(p, x, xt0, yt0, sigma_ref, sigma_sci, diff, out, co, s);
 }
 
 cudaError_t subtract_from_rows(Plan *p, const double *x, void *diff, cudaStream_t s) {

@@ -71,3 +71,52 @@ def test_whitens_the_difference_noise():
     # each averaged bin has a relative error of about 1/sqrt(trials) = 5 %
     assert np.abs(dec / flat - 1).max() < 0.3
     assert abs(dec.mean() / flat - 1) < 0.02
+
+
+def _blur(rng, w0, w1, spread=0.1):
+    k = np.abs(rng.standard_normal((2 * w0 + 1, 2 * w1 + 1))) * spread
+    k[w0, w1] += 1.0
+    return k / k.sum()
+
+
+def test_coadd_form_with_delta_kernels_is_the_pair_form():
+    """M = N = 1 and G = H = delta reduce Eq. 21 to D = S - R (*) K."""
+    rng = np.random.default_rng(3)
+    k = _blur(rng, 2, 2)
+    d = np.zeros((3, 3))
+    d[1, 1] = 1.0
+    D = random_field(20, 16, 4)
+    a = decorr.decorrelate_coadd(D, k, [6.0], [d], [4.0], [d])
+    b = decorr.decorrelate(D, k, 4.0, 6.0)
+    assert np.allclose(a, b, rtol=0, atol=1e-10 * np.abs(D).max())
+
+
+def test_coadd_filter_whitens_coadded_noise():
+    """White noise in M = 3 science and N = 2 reference exposures, homogenised
+    by G_j, H_i, co-added (Eq. 21) and subtracted through K: after the filter
+    of Eq. 24 the power spectrum is flat (Monte Carlo, 400 realisations)."""
+    rng = np.random.default_rng(11)
+    n0, n1 = 20, 24
+    k = _blur(rng, 2, 2, 0.3)
+    G = [_blur(rng, 1, 1, 0.4) / 3 for _ in range(3)]
+    H = [_blur(rng, 2, 1, 0.4) / 2 for _ in range(2)]
+    ss, sr = [2.0, 3.0, 2.5], [1.5, 4.0]
+    kh = decorr.kernel_spectrum(k, n0, n1)
+    gh = [decorr.kernel_spectrum(g, n0, n1) for g in G]
+    hh = [decorr.kernel_spectrum(h, n0, n1) for h in H]
+    raw = np.zeros((n0, n1))
+    dec = np.zeros((n0, n1))
+    trials = 400
+    for _ in range(trials):
+        Sf = sum(np.fft.fft2(rng.normal(0, s, (n0, n1))) * g for s, g in zip(ss, gh))
+        Rf = sum(np.fft.fft2(rng.normal(0, s, (n0, n1))) * h for s, h in zip(sr, hh))
+        D = np.real(np.fft.ifft2(Sf - Rf * kh))
+        raw += np.abs(np.fft.fft2(D)) ** 2
+        dec += np.abs(np.fft.fft2(decorr.decorrelate_coadd(D, k, ss, G, sr, H))) ** 2
+    raw /= trials * n0 * n1
+    dec /= trials * n0 * n1
+    flat = sum(s ** 2 * abs(g[0, 0]) ** 2 for s, g in zip(ss, gh)) + abs(kh[0, 0]) ** 2 * sum(
+        s ** 2 * abs(h[0, 0]) ** 2 for s, h in zip(sr, hh))
+    assert raw.max() / raw.min() > 2.0
+    assert np.abs(dec / flat - 1).max() < 0.3
+    assert abs(dec.mean() / flat - 1) < 0.02
