@@ -241,6 +241,22 @@ int sfft_decorrelate_coadd(sfft_plan_t plan, const double *d_x, double xt0, doub
                            sfft_stream_t stream);
 
 /*
+ * Crowded-flavor mask (Sec. 3.1): the pixels affected by saturated sources,
+ * for the d_mask argument of sfft_build_system / sfft_run_pair.  A pixel is
+ * masked (0) when R reaches sat_ref or S reaches sat_sci anywhere within the
+ * square of half-width `grow` around it (Chebyshev distance, clipped at the
+ * image edges), or when d_mask_in (NULL: none) masks it; else 1.  Needs no
+ * plan.
+ *   n0, n1        : image size (>= 1); dtype: sfft_dtype of d_ref, d_sci.
+ *   grow          : 0..16.
+ *   d_mask_out    : n0*n1 bytes, device; may equal d_mask_in.
+ * Asynchronous on `stream`; SFFT_ERR_INVALID for bad arguments.
+ */
+int sfft_saturation_mask(int32_t n0, int32_t n1, int32_t dtype, const void *d_ref, const void *d_sci,
+                         double sat_ref, double sat_sci, int32_t grow, const uint8_t *d_mask_in,
+                         uint8_t *d_mask_out, sfft_stream_t stream);
+
+/*
  * One whole pair on device buffers: build, solve and subtract.  d_M, d_rhs,
  * d_x and d_info may be NULL, in which case plan-owned buffers are used.
  */

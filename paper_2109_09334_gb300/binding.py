@@ -111,6 +111,7 @@ def library():
         dbl = ctypes.c_double
         lib.sfft_decorrelate_coadd.argtypes = [vp, vp, dbl, dbl, i32, vp, vp, i32, vp, vp, i32, i32, vp, vp, vp]
         lib.sfft_plan_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.sfft_saturation_mask.argtypes = [i32, i32, i32, vp, vp, dbl, dbl, i32, vp, vp, vp]
         lib.sfft_plan_set_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.sfft_plan_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_replay_stage.argtypes = [vp, ctypes.c_int, vp]
@@ -226,6 +227,15 @@ def sfft_decorrelate_coadd(plan, d_x, xt0, yt0, d_G, sigma_sci, d_H, sigma_ref, 
     _check(library().sfft_decorrelate_coadd(plan, _p(d_x), float(xt0), float(yt0), n_sci, _p(d_G), ss, n_ref,
                                             _p(d_H), sr, g0, g1, _p(d_diff), _p(d_out), _s(stream)),
            "sfft_decorrelate_coadd")
+
+
+def sfft_saturation_mask(d_ref, d_sci, sat_ref, sat_sci, grow, d_mask_out, d_mask_in=None, stream=None):
+    """Crowded-flavor mask of a pair of 2-D float32/float64 CUDA tensors into a uint8 tensor."""
+    n0, n1 = int(d_ref.shape[0]), int(d_ref.shape[1])
+    dt = SFFT_F64 if d_ref.element_size() == 8 else SFFT_F32
+    _check(library().sfft_saturation_mask(n0, n1, dt, _p(d_ref), _p(d_sci), float(sat_ref), float(sat_sci),
+                                          int(grow), _p(d_mask_in), _p(d_mask_out), _s(stream)),
+           "sfft_saturation_mask")
 
 
 def sfft_subtract(plan, d_ref, d_sci, d_x, d_diff, stream=None):

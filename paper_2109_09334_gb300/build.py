@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfft.so")
-SOURCES = ["api.cu", "basis.cu", "build.cu", "server.cu", "solve.cu", "solve_static.cu", "subtract.cu"]
+SOURCES = ["api.cu", "basis.cu", "build.cu", "mask.cu", "server.cu", "solve.cu", "solve_static.cu", "subtract.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

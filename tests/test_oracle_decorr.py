@@ -120,3 +120,21 @@ def test_coadd_filter_whitens_coadded_noise():
     assert raw.max() / raw.min() > 2.0
     assert np.abs(dec / flat - 1).max() < 0.3
     assert abs(dec.mean() / flat - 1) < 0.02
+
+
+def test_saturation_mask_matches_binary_dilation():
+    """The crowded-flavor mask against scipy's binary dilation with a square
+    structuring element (a library routine the oracle does not use)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    from oracle import masking
+    rng = np.random.default_rng(5)
+    for n0, n1, grow in ((17, 23, 0), (32, 32, 2), (20, 13, 4)):
+        R = rng.uniform(0, 100, (n0, n1))
+        S = rng.uniform(0, 100, (n0, n1))
+        sat = (R >= 97.0) | (S >= 98.5)
+        want = ~ndimage.binary_dilation(sat, structure=np.ones((2 * grow + 1, 2 * grow + 1), bool)) if grow else ~sat
+        got = masking.saturation_mask(R, S, 97.0, 98.5, grow)
+        assert np.array_equal(got.astype(bool), want)
+        m_in = (rng.random((n0, n1)) > 0.1).astype(np.uint8)
+        got2 = masking.saturation_mask(R, S, 97.0, 98.5, grow, m_in)
+        assert np.array_equal(got2.astype(bool), want & (m_in != 0))
