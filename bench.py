@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--no-bspline", action="store_true", help="skip the B-spline basis measurement")
     ap.add_argument("--mode", default="full", choices=["full", "pair"],
                     help="pair: only warmup + steps pairs through sfft_run_pair (for profiler captures)")
-    ap.add_argument("--depth", type=int, default=4, help="pairs in flight in the serving path (1..8)")
-    ap.add_argument("--batch", type=int, default=4, help="systems solved per launch in the serving path")
+    ap.add_argument("--depth", type=int, default=8, help="pairs in flight in the serving path (1..8)")
+    ap.add_argument("--batch", type=int, default=8, help="systems solved per launch in the serving path")
     ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
                     help="sectors64: solve the sectors' systems eight per launch, or one per pair")
     return ap.parse_args()

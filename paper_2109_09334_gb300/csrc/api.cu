@@ -133,7 +133,7 @@ void plan_free(Plan *p) {
                     p->twpm0, p->kimg, p->xhat, p->yhat, p->F, p->U, p->Q, p->pairs, p->rowmom, p->lag, p->A,
                     p->Wm, p->dscale, p->r, p->xw, p->zv, p->flag, p->M_own, p->rhs_own, p->x_own, p->info_own,
                     p->img_ref, p->img_sci, p->img_diff, p->img_mask, p->kap, p->d_int, p->ftab, p->ftab64,
-                    p->bxy64, p->d_zdesc, p->d_rdesc, p->z0, p->cmat, p->unk, p->gam};
+                    p->bxy64, p->d_zdesc, p->d_rdesc, p->z0, p->cmat, p->unk, p->gam, p->bnd};
     for (void *b : bufs)
         if (b) cudaFree(b);
     free(p->h_int);
@@ -250,8 +250,9 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     };
     for (int a = 0; a < p->nk; ++a)
         for (int b = a; b < p->nk; ++b) push(PK_OMEGA, a, b, 2 * cfg->w0);
-    for (int a = 0; a < p->nk; ++a)
-        for (int q = 0; q < p->nbx; ++q) push(PK_LAMBDA, a, q, cfg->w0);
+    if (!p->lam_closed)  // otherwise Lambda is evaluated in closed form (k_lambda_closed)
+        for (int a = 0; a < p->nk; ++a)
+            for (int q = 0; q < p->nbx; ++q) push(PK_LAMBDA, a, q, cfg->w0);
     for (int a = 0; a < p->nk; ++a) push(PK_THETA, a, p->nk, cfg->w0);
     p->npairs = np;
     p->nrows = rows;

@@ -305,6 +305,12 @@ int basis_build(Plan *p, cudaStream_t s) {
     // ---- row moments and zero-lag descriptors -------------------------------
     const int npo = nk * (nk + 1) / 2;
     p->nzm = npo + nk * nb + nk + nb;
+    // polynomial basis: Lambda in closed form from the 2-D moments
+    // mu(u, v) = sum x^u y^v Rm, u, v <= dk + db, appended to z0
+    const int Dm = c.dk + c.db;
+    p->lam_closed = poly ? 1 : 0;
+    p->z_mu = p->nzm;
+    if (poly) p->nzm += (Dm + 1) * (Dm + 1);
     std::vector<int> zd((size_t)p->nzm * 3);
     std::vector<int> rd;
     // row-moment indices
@@ -376,6 +382,14 @@ int basis_build(Plan *p, cudaStream_t s) {
         const int pp = h[bv.o_sp + sidx], qq = h[bv.o_sq + sidx];
         if (poly) put(e++, fS + qq, pp, -1);
         else put(e++, nrr + nrb + nfy + qq, nfx + pp, -1);
+    }
+    if (poly)
+        for (int u = 0; u <= Dm; ++u)
+            for (int v = 0; v <= Dm; ++v) put(e++, fR + v, u, -1);
+    if (poly) {
+        const size_t nbnd = (size_t)2 * c.w1 * (Dm + 1) + (size_t)4 * c.w0 * c.w1 + 1;
+        if (cudaMalloc((void **)&p->bnd, nbnd * sizeof(double)) != cudaSuccess) return SFFT_ERR_OOM;
+        p->ws_bytes += nbnd * sizeof(double);
     }
     if (cudaMalloc((void **)&p->d_zdesc, zd.size() * sizeof(int)) != cudaSuccess) return SFFT_ERR_OOM;
     if (cudaMalloc((void **)&p->z0, (size_t)p->nzm * sizeof(double)) != cudaSuccess) return SFFT_ERR_OOM;

@@ -289,6 +289,140 @@ __global__ void k_row_moments_tab(int n1, int nmom, const int *__restrict__ rdes
 }
 
 // ---------------------------------------------------------------------------
+// Boundary data of the closed-form Lambda (polynomial basis), FP64:
+//   bnd[c * (D+1) + u] = sum_x xt^u Rm(x, y_c)  for the 2 w1 boundary columns
+//                        y_c = c (c < w1) or n1 - 2 w1 + c,
+//   bnd[2 w1 (D+1) + r * 2 w1 + c] = Rm(x_r, y_c) for the 2 w0 boundary rows
+//                        x_r = r (r < w0) or n0 - 2 w0 + r.
+// Blocks 0 .. 2 w1 - 1: one column each; block 2 w1: the corner pixels.
+constexpr int kMaxDm = 6;  // dk + db
+
+template <typename I>
+__global__ void k_boundary(int n0, int n1, int w0, int w1, int D, const I *__restrict__ R,
+                           const uint8_t *__restrict__ mask, double *__restrict__ bnd) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nbc = 2 * w1;
+    if ((int)blockIdx.x == nbc) {
+        for (int e = tid; e < 2 * w0 * nbc; e += nthr) {
+            const int r = e / nbc, c = e - r * nbc;
+            const int x = r < w0 ? r : n0 - 2 * w0 + r, y = c < w1 ? c : n1 - 2 * w1 + c;
+            const size_t k = (size_t)x * n1 + y;
+            bnd[(size_t)nbc * (D + 1) + e] = (mask == nullptr || mask[k] != 0) ? (double)R[k] : 0.0;
+        }
+        return;
+    }
+    const int c = blockIdx.x;
+    const int y = c < w1 ? c : n1 - 2 * w1 + c;
+    double acc[kMaxDm + 1];
+#pragma unroll
+    for (int u = 0; u <= kMaxDm; ++u) acc[u] = 0.0;
+#pragma unroll 4
+    for (int x = tid; x < n0; x += nthr) {
+        const size_t k = (size_t)x * n1 + y;
+        const double v = (mask == nullptr || mask[k] != 0) ? (double)R[k] : 0.0;
+        const double xt = coord<double>(x, n0);
+        double pw = v;
+#pragma unroll
+        for (int u = 0; u <= kMaxDm; ++u) {
+            if (u <= D) acc[u] += pw;
+            pw *= xt;
+        }
+    }
+    __shared__ double red[32][kMaxDm + 1];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int u = 0; u <= kMaxDm; ++u) {
+        double a = acc[u];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) red[warp][u] = a;
+    }
+    __syncthreads();
+    if (tid <= D) {
+        double a = 0.0;
+        for (int w = 0; w < (nthr >> 5); ++w) a += red[w][tid];
+        bnd[(size_t)c * (D + 1) + tid] = a;
+    }
+}
+
+// Lambda_ts(rho) = sum_x g_t(x) T_s((x + rho) mod N) in closed form for the
+// polynomial basis, g_t = xt^i yt^j Rm, T_s = xt^p yt^q (Eq. B8), FP64.
+// With X_e(x) = (xt + 2 rho0/(N0-1))^p, the shifted monomial as if it did not
+// wrap, and dX = X_wrapped - X_e (non-zero only on the |rho0| rows where x +
+// rho0 wraps), likewise Y_e, dY along y:
+//   Lambda = sum g X_e Y_e + sum g dX Y_e + sum g X_e dY + sum g dX dY,
+// the first term by binomial expansion over the 2-D moments mu(u, v), the
+// second from the per-row moments of the wrapping rows, the third from the
+// column moments of the wrapping columns, the last over the corner pixels.
+__device__ __forceinline__ double binom(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+// One warp per value: the lanes share the wrapping rows, columns and corner
+// pixels and sum their parts in a fixed order (warp shuffle).
+__global__ void k_lambda_closed(int n0, int n1, int w0, int w1, int D, BasisView bv,
+                                const double *__restrict__ rowmom, int nmom, int fR,
+                                const double *__restrict__ mu, const double *__restrict__ bnd,
+                                double *__restrict__ lagla) {
+    const int L0 = 2 * w0 + 1, L1 = 2 * w1 + 1;
+    const int total = bv.nk * bv.nb * L0 * L1;
+    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (e >= total) return;  // whole warps
+    const int r1i = e % L1, r0i = (e / L1) % L0, ts = e / (L0 * L1);
+    const int t = ts / bv.nb, s = ts - t * bv.nb;
+    const int rho0 = r0i - w0, rho1 = r1i - w1;
+    const int i = bv.ti(t), j = bv.tj(t), p = bv.sp(s), q = bv.sq(s);
+    const double h0 = 2.0 * rho0 / (double)(n0 - 1), h1 = 2.0 * rho1 / (double)(n1 - 1);
+    const int nbc = 2 * w1;
+    const double *colm = bnd, *corner = bnd + (size_t)nbc * (D + 1);
+    // the weights C(p,k) h0^(p-k) and C(q,l) h1^(q-l)
+    double bx[kMaxDm + 1], by[kMaxDm + 1];
+#pragma unroll
+    for (int k = 0; k <= kMaxDm; ++k) {
+        bx[k] = k <= p ? binom(p, k) * ipow(h0, p - k) : 0.0;
+        by[k] = k <= q ? binom(q, k) * ipow(h1, q - k) : 0.0;
+    }
+    // rows where x + rho0 wraps, columns where y + rho1 wraps
+    const int xa = rho0 > 0 ? n0 - rho0 : 0, nx = rho0 > 0 ? rho0 : -rho0;
+    const int ya = rho1 > 0 ? n1 - rho1 : 0, ny = rho1 > 0 ? rho1 : -rho1;
+    auto dxf = [&](int x) {
+        const int xw = x + rho0 >= n0 ? x + rho0 - n0 : (x + rho0 < 0 ? x + rho0 + n0 : x + rho0);
+        return ipow(coord<double>(xw, n0), p) - ipow(coord<double>(x, n0) + h0, p);
+    };
+    auto dyf = [&](int y) {
+        const int yw = y + rho1 >= n1 ? y + rho1 - n1 : (y + rho1 < 0 ? y + rho1 + n1 : y + rho1);
+        return ipow(coord<double>(yw, n1), q) - ipow(coord<double>(y, n1) + h1, q);
+    };
+    double part = 0.0;
+    for (int k = lane; k < nx; k += 32) {  // sum g dX Y_e over the wrapping rows
+        const int x = xa + k;
+        double ysum = 0.0;
+        for (int l = 0; l <= q; ++l) ysum += by[l] * rowmom[(size_t)x * nmom + fR + j + l];
+        part += dxf(x) * ipow(coord<double>(x, n0), i) * ysum;
+    }
+    for (int k = lane; k < ny; k += 32) {  // sum g X_e dY over the wrapping columns
+        const int y = ya + k;
+        const int c = y < w1 ? y : y - (n1 - nbc);
+        double xsum = 0.0;
+        for (int kk = 0; kk <= p; ++kk) xsum += bx[kk] * colm[(size_t)c * (D + 1) + i + kk];
+        part += dyf(y) * ipow(coord<double>(y, n1), j) * xsum;
+    }
+    for (int k = lane; k < nx * ny; k += 32) {  // sum g dX dY over the corner pixels
+        const int x = xa + k / ny, y = ya + k % ny;
+        const int r = x < w0 ? x : x - (n0 - 2 * w0), c = y < w1 ? y : y - (n1 - nbc);
+        part += ipow(coord<double>(x, n0), i) * ipow(coord<double>(y, n1), j) * corner[r * nbc + c] * dxf(x) * dyf(y);
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) {
+        double A = 0.0;  // sum g X_e Y_e by binomial expansion over mu
+        for (int k = 0; k <= p; ++k)
+            for (int l = 0; l <= q; ++l) A += bx[k] * by[l] * mu[(i + k) * (D + 1) + (j + l)];
+        lagla[(size_t)ts * L0 * L1 + (size_t)r0i * L1 + r1i] = A + part;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Zero-lag values (FP64): z0[e] = sum_x xtab[xa](x) (xtab[xb](x) if xb >= 0)
 // rowmom[x][d] for descriptor e = (d, xa, xb).
 __global__ void k_zero_lag(int n0, int nmom, const int *__restrict__ zdesc, const double *__restrict__ xtab,
@@ -945,6 +1079,11 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
         k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
                                                   p->rowmom);
         p->launches++;
+        if (p->lam_closed) {
+            k_boundary<I><<<2 * p->cfg.w1 + 1, 1024, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1,
+                                                            p->cfg.dk + p->cfg.db, (const I *)ref, mask, p->bnd);
+            p->launches++;
+        }
     } else if (moments) {  // ytab = fy | by
         dim3 grid(p->n0, (p->nmom + kMomChunk - 1) / kMomChunk);
         k_row_moments_tab<T, I><<<grid, 256, 0, s>>>(p->n1, p->nmom, p->d_rdesc, ft.fy, (const I *)ref,
@@ -996,7 +1135,7 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int G = p->na / 8;
-    const int nimg = p->nimg, nxp = p->nbx;
+    const int nimg = p->nimg, nxp = p->lam_closed ? 0 : p->nbx;
     // one group of G lanes per product, whole warps, at most 384 threads per
     // block; more products go to further blocks along y
     const int max_groups = 384 / G;
@@ -1017,7 +1156,7 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
     if (!kern) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(p->h1c, nchunks);
-    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, p->nbx, p->nbk, p->npairs, hmax, p->pairs,
+    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, nxp, p->nbk, p->npairs, hmax, p->pairs,
                                   (const cpx<T> *)p->U, (const cpx<T> *)p->xhat, (const cpx<T> *)p->tw0,
                                   (cpx<T> *)p->Q);
     p->launches++;
@@ -1041,6 +1180,15 @@ static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) 
     lv.w1 = p->cfg.w1;
     lv.nk = p->nk;
     lv.nbt = p->nb;
+    if (p->lam_closed) {
+        const int nla = p->nk * p->nb * p->L0 * p->L1;
+        const int fR = 2 * p->cfg.dk + 1;  // row moments sum_y Rm yt^v (k_row_moments layout)
+        k_lambda_closed<<<(nla + 7) / 8, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk + p->cfg.db,
+                                                          p->bv, p->rowmom, p->nmom, fR, p->z0 + p->z_mu, p->bnd,
+                                                          p->lag + p->lag_la);
+        p->launches++;
+        if ((err = cudaGetLastError())) return err;
+    }
     const size_t total = (size_t)p->n * p->n + p->n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;

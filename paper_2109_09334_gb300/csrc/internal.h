@@ -117,6 +117,12 @@ struct Plan {
     double *z0;            // [nzm] zero-lag values (FP64)
     double *cmat;          // C of Eq. B11, [nb][nb] (FP64, depends on the basis only)
     int4 *unk;             // [n] decoded unknowns: (kernel term?, term, alpha, beta)
+    // Polynomial basis: Lambda in closed form (k_lambda_closed) instead of the
+    // gather; z_mu: offset of the 2-D moments mu(u, v), u, v <= dk + db, in z0;
+    // bnd: FP64 column moments of the 2 w1 boundary columns and the masked R
+    // in the 2 w0 x 2 w1 corner pixels.
+    int lam_closed, z_mu;
+    double *bnd;
     void *xhat;            // [p][lb][r] 1-D spectra of the background x-functions, permuted (compute type)
     void *yhat;            // [q][m] 1-D spectra of the background y-functions, m < h1c (compute type)
     void *F;               // [(nfy+1)][m][x] row transforms (compute type)
