@@ -308,7 +308,7 @@ int basis_build(Plan *p, cudaStream_t s) {
     // polynomial basis: Lambda in closed form from the 2-D moments
     // mu(u, v) = sum x^u y^v Rm, u, v <= dk + db, appended to z0
     const int Dm = c.dk + c.db;
-    p->lam_closed = poly ? 1 : 0;
+    p->lam_closed = (poly && c.w0 <= 16 && c.w1 <= 16) ? 1 : 0;  // half-widths of k_lambda_closed's tables
     p->z_mu = p->nzm;
     if (poly) p->nzm += (Dm + 1) * (Dm + 1);
     std::vector<int> zd((size_t)p->nzm * 3);
@@ -386,8 +386,8 @@ int basis_build(Plan *p, cudaStream_t s) {
     if (poly)
         for (int u = 0; u <= Dm; ++u)
             for (int v = 0; v <= Dm; ++v) put(e++, fR + v, u, -1);
-    if (poly) {
-        const size_t nbnd = (size_t)2 * c.w1 * (Dm + 1) + (size_t)4 * c.w0 * c.w1 + 1;
+    if (p->lam_closed) {  // 16 row-chunk partial sums of the boundary column moments, then the corners
+        const size_t nbnd = (size_t)16 * 2 * c.w1 * (Dm + 1) + (size_t)4 * c.w0 * c.w1 + 1;
         if (cudaMalloc((void **)&p->bnd, nbnd * sizeof(double)) != cudaSuccess) return SFFT_ERR_OOM;
         p->ws_bytes += nbnd * sizeof(double);
     }

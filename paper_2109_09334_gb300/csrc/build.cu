@@ -289,35 +289,41 @@ __global__ void k_row_moments_tab(int n1, int nmom, const int *__restrict__ rdes
 }
 
 // ---------------------------------------------------------------------------
-// Boundary data of the closed-form Lambda (polynomial basis), FP64:
-//   bnd[c * (D+1) + u] = sum_x xt^u Rm(x, y_c)  for the 2 w1 boundary columns
-//                        y_c = c (c < w1) or n1 - 2 w1 + c,
-//   bnd[2 w1 (D+1) + r * 2 w1 + c] = Rm(x_r, y_c) for the 2 w0 boundary rows
-//                        x_r = r (r < w0) or n0 - 2 w0 + r.
-// Blocks 0 .. 2 w1 - 1: one column each; block 2 w1: the corner pixels.
+// Boundary data of the closed-form Lambda (polynomial basis), FP64, in
+// kBndChunks partial sums over row chunks (added in order by the consumer):
+//   bnd[(h * 2 w1 + c) * (D+1) + u] = sum over rows x of chunk h of xt^u Rm(x, y_c)
+//       for the 2 w1 boundary columns y_c = c (c < w1) or n1 - 2 w1 + c,
+//   bnd[kBndChunks * 2 w1 (D+1) + r * 2 w1 + c] = Rm(x_r, y_c) for the
+//       2 w0 boundary rows x_r = r (r < w0) or n0 - 2 w0 + r.
+// Grid (2 w1 + 1, kBndChunks): block (c, h) one column and row chunk; blocks
+// (2 w1, 0) the corner pixels.
 constexpr int kMaxDm = 6;  // dk + db
+constexpr int kBndChunks = 16;
+constexpr int kMaxWClosed = 16;  // kernel half-widths of the closed-form Lambda
 
 template <typename I>
-__global__ void k_boundary(int n0, int n1, int w0, int w1, int D, const I *__restrict__ R,
-                           const uint8_t *__restrict__ mask, double *__restrict__ bnd) {
+__global__ void __launch_bounds__(256) k_boundary(int n0, int n1, int w0, int w1, int D, const I *__restrict__ R,
+                                                  const uint8_t *__restrict__ mask, double *__restrict__ bnd) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int nbc = 2 * w1;
-    if ((int)blockIdx.x == nbc) {
+    const int c = blockIdx.x, h = blockIdx.y;
+    if (c == nbc) {
+        if (h != 0) return;
         for (int e = tid; e < 2 * w0 * nbc; e += nthr) {
-            const int r = e / nbc, c = e - r * nbc;
-            const int x = r < w0 ? r : n0 - 2 * w0 + r, y = c < w1 ? c : n1 - 2 * w1 + c;
+            const int r = e / nbc, cc = e - r * nbc;
+            const int x = r < w0 ? r : n0 - 2 * w0 + r, y = cc < w1 ? cc : n1 - 2 * w1 + cc;
             const size_t k = (size_t)x * n1 + y;
-            bnd[(size_t)nbc * (D + 1) + e] = (mask == nullptr || mask[k] != 0) ? (double)R[k] : 0.0;
+            bnd[(size_t)kBndChunks * nbc * (D + 1) + e] = (mask == nullptr || mask[k] != 0) ? (double)R[k] : 0.0;
         }
         return;
     }
-    const int c = blockIdx.x;
     const int y = c < w1 ? c : n1 - 2 * w1 + c;
+    const int per = (n0 + kBndChunks - 1) / kBndChunks;
+    const int xa = h * per, xb = min(n0, xa + per);
     double acc[kMaxDm + 1];
 #pragma unroll
     for (int u = 0; u <= kMaxDm; ++u) acc[u] = 0.0;
-#pragma unroll 4
-    for (int x = tid; x < n0; x += nthr) {
+    for (int x = xa + tid; x < xb; x += nthr) {
         const size_t k = (size_t)x * n1 + y;
         const double v = (mask == nullptr || mask[k] != 0) ? (double)R[k] : 0.0;
         const double xt = coord<double>(x, n0);
@@ -328,19 +334,19 @@ __global__ void k_boundary(int n0, int n1, int w0, int w1, int D, const I *__res
             pw *= xt;
         }
     }
-    __shared__ double red[32][kMaxDm + 1];
+    __shared__ double red[8][kMaxDm + 1];
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int u = 0; u <= kMaxDm; ++u) {
-        double a = acc[u];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) red[warp][u] = a;
+        double v = acc[u];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][u] = v;
     }
     __syncthreads();
     if (tid <= D) {
-        double a = 0.0;
-        for (int w = 0; w < (nthr >> 5); ++w) a += red[w][tid];
-        bnd[(size_t)c * (D + 1) + tid] = a;
+        double v = 0.0;
+        for (int w = 0; w < (nthr >> 5); ++w) v += red[w][tid];
+        bnd[((size_t)h * nbc + c) * (D + 1) + tid] = v;
     }
 }
 
@@ -353,72 +359,116 @@ __global__ void k_boundary(int n0, int n1, int w0, int w1, int D, const I *__res
 // the first term by binomial expansion over the 2-D moments mu(u, v), the
 // second from the per-row moments of the wrapping rows, the third from the
 // column moments of the wrapping columns, the last over the corner pixels.
+// One block per (t, s): the per-row and per-column pieces that do not depend
+// on both lags are built once in shared memory; thread e then takes lag e.
 __device__ __forceinline__ double binom(int n, int k) {
     double r = 1.0;
     for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
     return r;
 }
 
-// One warp per value: the lanes share the wrapping rows, columns and corner
-// pixels and sum their parts in a fixed order (warp shuffle).
-__global__ void k_lambda_closed(int n0, int n1, int w0, int w1, int D, BasisView bv,
-                                const double *__restrict__ rowmom, int nmom, int fR,
-                                const double *__restrict__ mu, const double *__restrict__ bnd,
-                                double *__restrict__ lagla) {
+__global__ void __launch_bounds__(256) k_lambda_closed(int n0, int n1, int w0, int w1, int D, BasisView bv,
+                                                       const double *__restrict__ rowmom, int nmom, int fR,
+                                                       const double *__restrict__ mu, const double *__restrict__ bnd,
+                                                       double *__restrict__ lagla) {
+    constexpr int W = kMaxWClosed, NR = 2 * W + 1;
+    __shared__ double sbx[NR][kMaxDm + 1], sby[NR][kMaxDm + 1];  // C(p,k) h0^(p-k), C(q,l) h1^(q-l)
+    __shared__ double sdx[NR][W], sdy[NR][W];                    // dX(rho0, k-th wrapping row), dY
+    __shared__ double srow[NR][2 * W];  // [rho1][r]: sum_y (Y_e Rm yt^j)(x_r) + sum over wrapping y of Rm yt^j dY
+    __shared__ double scol[NR][2 * W];  // [rho0][c]: sum_x X_e Rm xt^i at boundary column c
+    __shared__ double sxi[2 * W], syj[2 * W];  // xt^i at the boundary rows, yt^j at the boundary columns
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int L0 = 2 * w0 + 1, L1 = 2 * w1 + 1;
-    const int total = bv.nk * bv.nb * L0 * L1;
-    const int e = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (e >= total) return;  // whole warps
-    const int r1i = e % L1, r0i = (e / L1) % L0, ts = e / (L0 * L1);
-    const int t = ts / bv.nb, s = ts - t * bv.nb;
-    const int rho0 = r0i - w0, rho1 = r1i - w1;
+    const int ts = blockIdx.x, t = ts / bv.nb, s = ts - t * bv.nb;
     const int i = bv.ti(t), j = bv.tj(t), p = bv.sp(s), q = bv.sq(s);
-    const double h0 = 2.0 * rho0 / (double)(n0 - 1), h1 = 2.0 * rho1 / (double)(n1 - 1);
-    const int nbc = 2 * w1;
-    const double *colm = bnd, *corner = bnd + (size_t)nbc * (D + 1);
-    // the weights C(p,k) h0^(p-k) and C(q,l) h1^(q-l)
-    double bx[kMaxDm + 1], by[kMaxDm + 1];
-#pragma unroll
-    for (int k = 0; k <= kMaxDm; ++k) {
-        bx[k] = k <= p ? binom(p, k) * ipow(h0, p - k) : 0.0;
-        by[k] = k <= q ? binom(q, k) * ipow(h1, q - k) : 0.0;
+    const int nbc = 2 * w1, nbr = 2 * w0;
+    const double *corner = bnd + (size_t)kBndChunks * nbc * (D + 1);
+    auto xrow = [&](int r) { return r < w0 ? r : n0 - 2 * w0 + r; };
+    auto ycol = [&](int c) { return c < w1 ? c : n1 - 2 * w1 + c; };
+    // rows (columns) where x + rho0 (y + rho1) wraps: k-th of them
+    auto wrow = [&](int rho0, int k) { return rho0 > 0 ? n0 - rho0 + k : k; };
+    auto wcol = [&](int rho1, int k) { return rho1 > 0 ? n1 - rho1 + k : k; };
+    for (int e = tid; e < L0 * (kMaxDm + 1); e += nthr) {
+        const int a = e / (kMaxDm + 1), k = e - a * (kMaxDm + 1);
+        const double h0 = 2.0 * (a - w0) / (double)(n0 - 1);
+        sbx[a][k] = k <= p ? binom(p, k) * ipow(h0, p - k) : 0.0;
     }
-    // rows where x + rho0 wraps, columns where y + rho1 wraps
-    const int xa = rho0 > 0 ? n0 - rho0 : 0, nx = rho0 > 0 ? rho0 : -rho0;
-    const int ya = rho1 > 0 ? n1 - rho1 : 0, ny = rho1 > 0 ? rho1 : -rho1;
-    auto dxf = [&](int x) {
-        const int xw = x + rho0 >= n0 ? x + rho0 - n0 : (x + rho0 < 0 ? x + rho0 + n0 : x + rho0);
-        return ipow(coord<double>(xw, n0), p) - ipow(coord<double>(x, n0) + h0, p);
-    };
-    auto dyf = [&](int y) {
-        const int yw = y + rho1 >= n1 ? y + rho1 - n1 : (y + rho1 < 0 ? y + rho1 + n1 : y + rho1);
-        return ipow(coord<double>(yw, n1), q) - ipow(coord<double>(y, n1) + h1, q);
-    };
-    double part = 0.0;
-    for (int k = lane; k < nx; k += 32) {  // sum g dX Y_e over the wrapping rows
-        const int x = xa + k;
-        double ysum = 0.0;
-        for (int l = 0; l <= q; ++l) ysum += by[l] * rowmom[(size_t)x * nmom + fR + j + l];
-        part += dxf(x) * ipow(coord<double>(x, n0), i) * ysum;
+    for (int e = tid; e < L1 * (kMaxDm + 1); e += nthr) {
+        const int b = e / (kMaxDm + 1), l = e - b * (kMaxDm + 1);
+        const double h1 = 2.0 * (b - w1) / (double)(n1 - 1);
+        sby[b][l] = l <= q ? binom(q, l) * ipow(h1, q - l) : 0.0;
     }
-    for (int k = lane; k < ny; k += 32) {  // sum g X_e dY over the wrapping columns
-        const int y = ya + k;
-        const int c = y < w1 ? y : y - (n1 - nbc);
-        double xsum = 0.0;
-        for (int kk = 0; kk <= p; ++kk) xsum += bx[kk] * colm[(size_t)c * (D + 1) + i + kk];
-        part += dyf(y) * ipow(coord<double>(y, n1), j) * xsum;
+    for (int e = tid; e < L0 * w0; e += nthr) {
+        const int a = e / max(w0, 1), k = e - a * max(w0, 1);
+        const int rho0 = a - w0, nx = rho0 > 0 ? rho0 : -rho0;
+        double d = 0.0;
+        if (k < nx) {
+            const int x = wrow(rho0, k);
+            const int xw = x + rho0 >= n0 ? x + rho0 - n0 : (x + rho0 < 0 ? x + rho0 + n0 : x + rho0);
+            d = ipow(coord<double>(xw, n0), p) - ipow(coord<double>(x, n0) + 2.0 * rho0 / (double)(n0 - 1), p);
+        }
+        sdx[a][k] = d;
     }
-    for (int k = lane; k < nx * ny; k += 32) {  // sum g dX dY over the corner pixels
-        const int x = xa + k / ny, y = ya + k % ny;
-        const int r = x < w0 ? x : x - (n0 - 2 * w0), c = y < w1 ? y : y - (n1 - nbc);
-        part += ipow(coord<double>(x, n0), i) * ipow(coord<double>(y, n1), j) * corner[r * nbc + c] * dxf(x) * dyf(y);
+    for (int e = tid; e < L1 * w1; e += nthr) {
+        const int b = e / max(w1, 1), k = e - b * max(w1, 1);
+        const int rho1 = b - w1, ny = rho1 > 0 ? rho1 : -rho1;
+        double d = 0.0;
+        if (k < ny) {
+            const int y = wcol(rho1, k);
+            const int yw = y + rho1 >= n1 ? y + rho1 - n1 : (y + rho1 < 0 ? y + rho1 + n1 : y + rho1);
+            d = ipow(coord<double>(yw, n1), q) - ipow(coord<double>(y, n1) + 2.0 * rho1 / (double)(n1 - 1), q);
+        }
+        sdy[b][k] = d;
     }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) {
+    for (int r = tid; r < nbr; r += nthr) sxi[r] = ipow(coord<double>(xrow(r), n0), i);
+    for (int c = tid; c < nbc; c += nthr) syj[c] = ipow(coord<double>(ycol(c), n1), j);
+    __syncthreads();
+    // srow[rho1][r] = sum_l by[l] rowmom(x_r, j + l) + sum_(wrapping y) Rm(x_r, y) yt^j dY(y)
+    for (int e = tid; e < L1 * nbr; e += nthr) {
+        const int b = e / nbr, r = e - b * nbr;
+        const int rho1 = b - w1, ny = rho1 > 0 ? rho1 : -rho1;
+        const int x = xrow(r);
+        double v = 0.0;
+        for (int l = 0; l <= q; ++l) v += sby[b][l] * rowmom[(size_t)x * nmom + fR + j + l];
+        for (int k = 0; k < ny; ++k) {
+            const int y = wcol(rho1, k);
+            const int c = y < w1 ? y : y - (n1 - nbc);
+            v += corner[r * nbc + c] * syj[c] * sdy[b][k];
+        }
+        srow[b][r] = v;
+    }
+    // scol[rho0][c] = sum_k bx[k] (column moment of y_c at i + k), chunks added in order
+    for (int e = tid; e < L0 * nbc; e += nthr) {
+        const int a = e / nbc, c = e - a * nbc;
+        double v = 0.0;
+        for (int k = 0; k <= p; ++k) {
+            double cm = 0.0;
+            for (int h = 0; h < kBndChunks; ++h) cm += bnd[((size_t)h * nbc + c) * (D + 1) + i + k];
+            v += sbx[a][k] * cm;
+        }
+        scol[a][c] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < L0 * L1; e += nthr) {
+        const int a = e / L1, b = e - a * L1;
+        const int rho0 = a - w0, rho1 = b - w1;
+        const int nx = rho0 > 0 ? rho0 : -rho0, ny = rho1 > 0 ? rho1 : -rho1;
         double A = 0.0;  // sum g X_e Y_e by binomial expansion over mu
         for (int k = 0; k <= p; ++k)
-            for (int l = 0; l <= q; ++l) A += bx[k] * by[l] * mu[(i + k) * (D + 1) + (j + l)];
-        lagla[(size_t)ts * L0 * L1 + (size_t)r0i * L1 + r1i] = A + part;
+            for (int l = 0; l <= q; ++l) A += sbx[a][k] * sby[b][l] * mu[(i + k) * (D + 1) + (j + l)];
+        double BD = 0.0;  // wrapping rows: sum dX xt^i (Y_e-weighted row sums + corner dY part)
+        for (int k = 0; k < nx; ++k) {
+            const int x = wrow(rho0, k);
+            const int r = x < w0 ? x : x - (n0 - nbr);
+            BD += sdx[a][k] * sxi[r] * srow[b][r];
+        }
+        double Cc = 0.0;  // wrapping columns: sum dY yt^j (X_e-weighted column sums)
+        for (int k = 0; k < ny; ++k) {
+            const int y = wcol(rho1, k);
+            const int c = y < w1 ? y : y - (n1 - nbc);
+            Cc += sdy[b][k] * syj[c] * scol[a][c];
+        }
+        lagla[(size_t)ts * L0 * L1 + e] = A + BD + Cc;
     }
 }
 
@@ -1080,7 +1130,7 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
                                                   p->rowmom);
         p->launches++;
         if (p->lam_closed) {
-            k_boundary<I><<<2 * p->cfg.w1 + 1, 1024, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1,
+            k_boundary<I><<<dim3(2 * p->cfg.w1 + 1, kBndChunks), 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1,
                                                             p->cfg.dk + p->cfg.db, (const I *)ref, mask, p->bnd);
             p->launches++;
         }
@@ -1181,9 +1231,8 @@ static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) 
     lv.nk = p->nk;
     lv.nbt = p->nb;
     if (p->lam_closed) {
-        const int nla = p->nk * p->nb * p->L0 * p->L1;
         const int fR = 2 * p->cfg.dk + 1;  // row moments sum_y Rm yt^v (k_row_moments layout)
-        k_lambda_closed<<<(nla + 7) / 8, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk + p->cfg.db,
+        k_lambda_closed<<<p->nk * p->nb, 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1, p->cfg.dk + p->cfg.db,
                                                           p->bv, p->rowmom, p->nmom, fR, p->z0 + p->z_mu, p->bnd,
                                                           p->lag + p->lag_la);
         p->launches++;
