@@ -456,7 +456,9 @@ int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes);
 
 /*
  * Set the plan's launch shapes (SFFT_TUNING_LEN values, read), e.g. to
- * reproduce an earlier sfft_plan_autotune.  Results do not depend on them.
+ * reproduce an earlier sfft_plan_autotune; like the autotuner, this also
+ * sets the shapes later plans (server slots, pool lanes) of the same
+ * configuration start with in this process.  Results do not depend on them.
  * SFFT_ERR_INVALID for a value outside the ranges above (nothing changed).
  */
 int sfft_plan_set_tuning(sfft_plan_t plan, const int32_t *shapes);

@@ -610,6 +610,7 @@ int sfft_plan_set_tuning(sfft_plan_t plan, const int32_t *shapes) {
     if (shapes[1] < 0 || shapes[1] > 4 || shapes[2] < 0 || shapes[2] > 4) return SFFT_ERR_INVALID;
     if (shapes[3] < 0 || shapes[3] > kMaxSolveGrid) return SFFT_ERR_INVALID;
     set_shapes((Plan *)plan, shapes);
+    tune_store((Plan *)plan);  // later plans of this configuration start with them
     return SFFT_OK;
 }
 
