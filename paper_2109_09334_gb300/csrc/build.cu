@@ -509,17 +509,17 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n0 / 16;
     const int np = padded_len(n0);
-    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n0
-    cpx<T> *Z = tw + n0;                                 // GI * np
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // GI * np
+    const int tid = threadIdx.x;
     const int grp = tid / G, gt = tid - grp * G;
     const int m = blockIdx.y;
     const int h1c = n1 / 2 + 1;
     const int nk = bv.nk;
     const int t = blockIdx.x * GI + grp;
     const bool act = t <= nk;
-    const int ntw = pass_table_len(n0);
-    for (int q = tid; q < ntw; q += nthr) tw[q] = tw0g[q];
+    // the pass-ordered twiddles are read through L1 (the whole table is
+    // 8 n0 bytes and every block of the launch reads it)
+    const cpx<T> *tw = tw0g;
     cpx<T> *zr = Z + (size_t)grp * np;
     if (act) {
         // thread gt loads elements gt + G c, c < 16: coalesced, all in flight
@@ -1155,14 +1155,14 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     if (GI > 4) GI = 4;
     const int nimg = p->nk + 1;
     if (GI > nimg) GI = nimg;
-    size_t smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+    size_t smem = (size_t)GI * padded_len(p->n0) * sizeof(cpx<T>);
     while (GI > 1 && smem > 110 * 1024) {
         --GI;
-        smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+        smem = (size_t)GI * padded_len(p->n0) * sizeof(cpx<T>);
     }
     if (p->tune_gi > 0 && p->tune_gi < GI) {
         GI = p->tune_gi;
-        smem = ((size_t)p->n0 + (size_t)GI * padded_len(p->n0)) * sizeof(cpx<T>);
+        smem = (size_t)GI * padded_len(p->n0) * sizeof(cpx<T>);
     }
     auto kern = k_cols<T>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -168,15 +168,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_rows_inv(int n0,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
     const int np = padded_len(n1);
-    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n1
-    cpx<T> *Z = tw + n1;                                 // NG * np
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // NG * np
+    const int tid = threadIdx.x;
     const int grp = tid / G, gt = tid - grp * G;
     const int half = n1 / 2;
     const T inv = (T)1 / (T)n1;
     const int xa = (blockIdx.x * NG + grp) * 2, xb = xa + 1;
-    const int ntw = pass_table_len(n1);
-    for (int q = tid; q < ntw; q += nthr) tw[q] = tw1g[q];
+    const cpx<T> *tw = tw1g;  // pass-ordered twiddles, read through L1
     cpx<T> *zr = Z + (size_t)grp * np;
     {
         // 16 frequencies per thread, all loads in flight
@@ -280,14 +278,14 @@ static cudaError_t launch_rows_inv(Plan *p, void *diff, cudaStream_t s) {
         if (NG < 1) NG = 1;
         if (NG > 4) NG = 4;
         if (NG > (p->n0 + 1) / 2) NG = (p->n0 + 1) / 2;
-        size_t smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+        size_t smem = (size_t)NG * padded_len(p->n1) * sizeof(cpx<T>);
         while (NG > 1 && smem > 110 * 1024) {
             NG /= 2;
-            smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+            smem = (size_t)NG * padded_len(p->n1) * sizeof(cpx<T>);
         }
         if (p->tune_ng > 0 && p->tune_ng < NG) {
             NG = p->tune_ng;
-            smem = ((size_t)p->n1 + (size_t)NG * padded_len(p->n1)) * sizeof(cpx<T>);
+            smem = (size_t)NG * padded_len(p->n1) * sizeof(cpx<T>);
         }
         const int blocks = (p->n0 + 2 * NG - 1) / (2 * NG);
         if (p->cfg.dtype == SFFT_F64) {
