@@ -50,6 +50,8 @@ def parse():
                     help="pair: only warmup + steps pairs through sfft_run_pair (for profiler captures)")
     ap.add_argument("--depth", type=int, default=8, help="pairs in flight in the serving path (1..8)")
     ap.add_argument("--batch", type=int, default=8, help="systems solved per launch in the serving path")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch shapes (for launch lists without the tuning replays)")
     ap.add_argument("--solve-grid", type=int, default=0,
                     help="blocks of the cooperative solve (0: two per SM in FP32, one in FP64)")
     ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
@@ -310,7 +312,7 @@ def run_ours(args):
         binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, x, info, D, stream)
 
     # launch shapes picked by timing (kept for the server's plans below)
-    tuning = plan.autotune(*dev_pairs[0])
+    tuning = binding.sfft_plan_tuning(plan.handle) if args.no_autotune else plan.autotune(*dev_pairs[0])
     if args.solve_grid:  # set by hand; the server's slots (created below) start with it
         tuning["solve_grid"] = args.solve_grid
         binding.sfft_plan_set_tuning(plan.handle, tuning)

@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0
 //   RR_v = sum_y Rm^2 yt^v (v <= 2dk), R_v = sum_y Rm yt^v (v <= dk+db),
 //   RS_v = sum_y Rm Sm yt^v (v <= dk), S_v = sum_y Sm yt^v (v <= db).
 template <typename T, typename I>
-__global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, const I *__restrict__ S,
-                              const uint8_t *__restrict__ mask, double *__restrict__ rowmom) {
-    __shared__ Acc<T> red[32][kMaxMom];
+__global__ void __launch_bounds__(256) k_row_moments(int n1, int dk, int db, const I *__restrict__ R,
+                                                     const I *__restrict__ S, const uint8_t *__restrict__ mask,
+                                                     double *__restrict__ rowmom) {
+    __shared__ T part_s[kMaxMom][256];  // plain per-thread partials, transposed for the reduction
     const int x0 = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
     const size_t rowoff = (size_t)x0 * n1;
     const MomLayout ml = mom_layout(dk, db);
@@ -209,7 +210,7 @@ __global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, c
             p *= yt;
         }
     }
-    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    // the partials that are needed, at their moment index
 #pragma unroll
     for (int k = 0; k < 22; ++k) {
         T val;
@@ -218,19 +219,18 @@ __global__ void k_row_moments(int n1, int dk, int db, const I *__restrict__ R, c
         else if (k < 14) { val = pR[k - 7]; dst = (k - 7 <= dk + db) ? ml.fR + k - 7 : -1; }
         else if (k < 18) { val = pRS[k - 14]; dst = (k - 14 <= dk) ? ml.fRS + k - 14 : -1; }
         else { val = pS[k - 18]; dst = (k - 18 <= db) ? ml.fS + k - 18 : -1; }
-        if (dst >= 0) {
-            Acc<T> a;
-            a.zero();
-            a.add(val);
-            for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
-            if (lane == 0) red[warp][dst] = a;
-        }
+        if (dst >= 0) part_s[dst][tid] = val;
     }
     __syncthreads();
-    if (tid < ml.n) {
-        Acc<T> a = red[0][tid];
-        for (int w = 1; w < nw; ++w) a.add(red[w][tid]);
-        rowmom[(size_t)x0 * ml.n + tid] = a.wide();
+    // warp w reduces moments w, w + nw, ...: each lane a two-sum over its
+    // threads' partials, then across the warp, in a fixed order
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    for (int d = warp; d < ml.n; d += nw) {
+        Acc<T> a;
+        a.zero();
+        for (int k = lane; k < nthr; k += 32) a.add(part_s[d][k]);
+        for (int o = 16; o > 0; o >>= 1) shfl_add(a, o);
+        if (lane == 0) rowmom[(size_t)x0 * ml.n + d] = a.wide();
     }
 }
 
@@ -1149,9 +1149,10 @@ static cudaError_t launch_cols(Plan *p, cudaStream_t s) {
     p->launches++;
     if (p->gen0) return cudaGetLastError();  // the lag sums along x need no column spectra
     const int G = p->n0 / 16;
-    // at most 512 (FP32) / 256 (FP64) threads and about 100 KB of shared
-    // memory per block, so that two blocks share an SM
-    int GI = (sizeof(T) == 4 ? 512 : 256) / G;
+    // about 256 threads per block (one 4096-point transform; the twiddles
+    // come through L1, so small blocks cost no table copies), at most 4 images
+    int GI = 256 / G;
+    if (GI < 1) GI = 1;
     if (GI > 4) GI = 4;
     const int nimg = p->nk + 1;
     if (GI > nimg) GI = nimg;
