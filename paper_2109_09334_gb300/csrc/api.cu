@@ -275,7 +275,7 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     SFFT_ALLOC(p->tw1, p->n1 * csz);
     SFFT_ALLOC(p->twp0, p->n0 * csz);
     SFFT_ALLOC(p->twp1, p->n1 * csz);
-    SFFT_ALLOC(p->xhat, (size_t)p->nbx * p->n0 * csz);
+    if (!p->lam_closed) SFFT_ALLOC(p->xhat, (size_t)p->nbx * p->n0 * csz);
     SFFT_ALLOC(p->yhat, (size_t)p->nby * p->h1c * csz);
     SFFT_ALLOC(p->F, (size_t)(p->nfy + 1) * half * csz);
     // the column spectra (power-of-two n0); the subtraction reuses U for D~
@@ -330,23 +330,25 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     k_twiddle64<<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a);
     k_twiddle64<<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b);
     const int bx = (p->nbx * p->n0 + 127) / 128, by = (p->nby * p->h1c + 127) / 128;
-    // background functions: powers computed in the kernel, or the B-spline tables
-    const double *tbx = p->bxy64, *tby = p->bxy64 ? p->bxy64 + (size_t)p->nbx * p->n0 : nullptr;
+    // the tabulated background functions (FP64)
+    const double *tbx = p->bxy64, *tby = p->bxy64 + (size_t)p->nbx * p->n0;
     if (p->fp64) {
         k_round<double><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<double> *)p->tw0);
         k_round<double><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<double> *)p->tw1);
         if (!p->gen0) pass_tables<double>(p->n0, t64a, (cpx<double> *)p->twp0, s);
         if (!p->gen1) pass_tables<double>(p->n1, t64b, (cpx<double> *)p->twp1, s);
-        k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
-                                              (cpx<double> *)p->xhat);
+        if (p->xhat)
+            k_poly_dft<double><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
+                                                  (cpx<double> *)p->xhat);
         k_poly_dft<double><<<by, 128, 0, s>>>(p->n1, p->h1c, p->nby, t64b, 0, 1, 0, tby, (cpx<double> *)p->yhat);
     } else {
         k_round<float><<<(p->n0 + 255) / 256, 256, 0, s>>>(p->n0, t64a, (cpx<float> *)p->tw0);
         k_round<float><<<(p->n1 + 255) / 256, 256, 0, s>>>(p->n1, t64b, (cpx<float> *)p->tw1);
         if (!p->gen0) pass_tables<float>(p->n0, t64a, (cpx<float> *)p->twp0, s);
         if (!p->gen1) pass_tables<float>(p->n1, t64b, (cpx<float> *)p->twp1, s);
-        k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
-                                             (cpx<float> *)p->xhat);
+        if (p->xhat)
+            k_poly_dft<float><<<bx, 128, 0, s>>>(p->n0, p->n0, p->nbx, t64a, p->na, p->nbk, 1, tbx,
+                                                 (cpx<float> *)p->xhat);
         k_poly_dft<float><<<by, 128, 0, s>>>(p->n1, p->h1c, p->nby, t64b, 0, 1, 0, tby, (cpx<float> *)p->yhat);
     }
     for (int ax = 0; ax < 2; ++ax) {  // Bluestein tables of the axes that are not powers of two

@@ -276,7 +276,8 @@ int basis_build(Plan *p, cudaStream_t s) {
             e = cudaMemcpy(p->ftab, f32.data(), nft * sizeof(float), cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) return SFFT_ERR_CUDA;
-        // FP64 background functions, bx then by, for their 1-D spectra
+    }
+    {  // FP64 background functions, bx then by, for their 1-D spectra (both bases)
         const size_t nbg = tbx.size() + tby.size();
         if (cudaMalloc((void **)&p->bxy64, nbg * sizeof(double)) != cudaSuccess) return SFFT_ERR_OOM;
         p->ws_bytes += nbg * sizeof(double);

@@ -109,7 +109,7 @@ struct Plan {
     int *h_int, *d_int;    // int tables (host copy, device copy)
     void *ftab;            // B-spline function tables, compute type: fx | fy | bx | by
     double *ftab64;        // FP64 x-functions for the zero-lag sums: [nallx][n0]
-    double *bxy64;         // B-spline: FP64 background functions bx [nbx][n0] then by [nby][n1]
+    double *bxy64;         // FP64 background functions bx [nbx][n0] then by [nby][n1] (for their spectra)
     int nallx;
     int nzm;               // zero-lag values: Omega(0,0) of each pair, Lambda(0,0), Theta(0,0), E
     int *d_zdesc;          // [nzm][3] (row moment, x-function a, x-function b or -1)
@@ -123,7 +123,8 @@ struct Plan {
     // in the 2 w0 x 2 w1 corner pixels.
     int lam_closed, z_mu;
     double *bnd;
-    void *xhat;            // [p][lb][r] 1-D spectra of the background x-functions, permuted (compute type)
+    void *xhat;            // [p][lb][r] 1-D spectra of the background x-functions, permuted (compute
+                           // type); only where Lambda goes through the gather (not lam_closed)
     void *yhat;            // [q][m] 1-D spectra of the background y-functions, m < h1c (compute type)
     void *F;               // [(nfy+1)][m][x] row transforms (compute type)
     void *U;               // [nimg][m][lb][r] full spectra, permuted (compute type); reused for Dt
