@@ -177,7 +177,9 @@ def stage_bytes(spec, n):
     b = 4 if spec.dtype == "float32" else 8
     nk = (f.dk + 1) * (f.dk + 2) // 2
     nimg = nk + 1
-    nrows = (nk * (nk + 1) // 2) * (4 * f.w0 + 1) + nk * (f.db + 1) * (2 * f.w0 + 1) + nk * (2 * f.w0 + 1)
+    # stage-1 rows of the Omega and Theta products (Lambda is evaluated in
+    # closed form for the polynomial basis, outside the gather)
+    nrows = (nk * (nk + 1) // 2) * (4 * f.w0 + 1) + nk * (2 * f.w0 + 1)
     h1c = spec.n1 // 2 + 1
     return {
         "rows": 2 * P * b + (f.dk + 2) * H * c,
@@ -200,7 +202,7 @@ def stage_flops(spec, n):
     na = min(64, n0)
     units = h1c * (n0 // na)
     n_om = nk * (nk + 1) // 2
-    n_other = nk * (f.db + 1) + nk
+    n_other = nk  # Theta; Lambda is in closed form for the polynomial basis (not in the gather)
     # per pair and residue class: products, two 8-point DFTs, twiddles, compensated outer sums
     per_unit = lambda lags: na * 6 + 2 * 60 * (na // 8) + 7 * 6 * (na // 8) + lags * 18
     nfft_rows = (f.dk + 3) // 2
