@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
     const int L0 = 2 * w0 + 1;
     cpx<T> *kp = reinterpret_cast<cpx<T> *>(smem_raw);  // nk * L0
     constexpr int Q = sub_q<T>();
-    cpx<T> *W = kp + nk * L0;  // n0 + n0 / Q (padded)
+    cpx<T> *Wb = kp + nk * L0;  // two buffers of n0 + n0 / Q (padded), alternating by term
     auto padq = [](int v) { return v + v / Q; };
     const int m = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
     const int h1c = n1 / 2 + 1;
@@ -120,7 +120,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
             }
         }
     }
-    // terms grouped by their y-function j: F_j is loaded once per group
+    // terms grouped by their y-function j: F_j is loaded once per group.  The
+    // weighted columns alternate between two buffers, so one barrier per term
+    // separates a buffer's fill from its reads and from its refill two terms on.
+    const int wlen = n0 + (n0 + Q - 1) / Q;
+    int nterm = 0;
     for (int j = 0; j < bv.nfy; ++j) {
         const int ncj = bv.jcnt(j);
         if (ncj == 0) continue;
@@ -130,14 +134,14 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
         for (int q = 0; q < Q; ++q) f[q] = (P2 || x0 + q < n0) ? Fj[q] : mk((T)0, (T)0);
         for (int k = 0; k < ncj; ++k) {
             const int t = bv.jterm(j, k), i = bv.ti(t);
-            __syncthreads();  // previous term's window reads are done
+            cpx<T> *W = Wb + (size_t)(nterm++ & 1) * wlen;
 #pragma unroll
             for (int q = 0; q < Q; ++q)
                 if (P2 || x0 + q < n0) {
                     const T wx = ft.fx ? ft.fx[(size_t)i * n0 + x0 + q] : ipow(xt[q], i);
                     W[padq(x0 + q)] = scale(f[q], wx);
                 }
-            __syncthreads();
+            __syncthreads();  // this buffer is filled; the other one's reads (two terms ago) are done
             const cpx<T> *kt = kp + t * L0;
             cpx<T> win[Q];
 #pragma unroll
@@ -314,7 +318,8 @@ static cudaError_t sub_t(Plan *p, const double *x, void *diff, cudaStream_t s) {
     if ((err = cudaGetLastError())) return err;
     {
         const int nthr = (p->n0 + sub_q<T>() - 1) / sub_q<T>();
-        const size_t smem = ((size_t)p->nk * p->L0 + (size_t)(p->n0 + nthr)) * sizeof(cpx<T>);
+        const size_t smem = ((size_t)p->nk * p->L0 + 2 * (size_t)(p->n0 + (p->n0 + sub_q<T>() - 1) / sub_q<T>())) *
+                            sizeof(cpx<T>);
         const int nbkg_off = p->n - p->nb;
         auto kern = p->gen0 ? k_sub_cols<T, false, -1> : k_sub_cols<T, true, -1>;
         switch (p->cfg.w0) {  // the half-widths of the workloads, unrolled
