@@ -5,8 +5,9 @@
 // host memory, and three streams:
 //   sc  copies of host requests' inputs to the slot's staging buffers;
 //   sb  the build of each pair (row/column FFTs, gather, lag sums, assembly);
-//   ss  (highest priority) the solves, the subtractions and the copies of
-//       the results back to host requests.
+//   ss  (highest priority) the solves and the subtractions;
+//   so  the copies of the results back to host requests, so that they
+//       overlap the next group's solve and subtractions.
 // Request s uses slot s mod depth.  Its build is enqueued at once; the
 // requests are grouped `batch` at a time (batch <= depth), and when a group
 // is complete (or on sfft_flush, or when a caller waits for one of its
@@ -15,16 +16,18 @@
 // grid-wide steps, so solving several systems in one launch costs little
 // more than solving one.  Events order the streams:
 //   built[i]: sb -> ss (M, rhs of the slot ready);
-//   done[i]:  ss -> sb, sc (the slot's previous pair is finished, so its
-//             workspace and staging buffers may be overwritten).
+//   done[i]:  ss or so -> sb, sc (the slot's previous pair is finished, so
+//             its workspace and staging buffers may be overwritten);
+//   subtracted[i]: ss -> so (a host request's results are ready to copy).
 // A slot is reused only by a request of a later group, whose predecessor's
 // group is complete and therefore flushed, so `done` is always recorded
 // before anything waits on it.  Every pair runs the kernels of
 // sfft_run_pair on its own slot, so its results are the same.
 //
-// Completion: every request records an event on ss after its last
-// operation.  ss is in order, so requests complete in submission order and
-// a watermark (all requests below it are complete) answers sfft_poll.
+// Completion: every request records an event after its last operation (on
+// ss, or on so for a host request).  The watermark (all requests below it
+// are complete) advances over these events in submission order, so requests
+// complete in submission order; it answers sfft_poll.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -46,7 +49,7 @@ struct Slot {
     Plan *plan = nullptr;
     void *ref = nullptr, *sci = nullptr, *diff = nullptr;  // staging for host requests
     uint8_t *mask = nullptr;
-    cudaEvent_t built = nullptr, done = nullptr, copied = nullptr;
+    cudaEvent_t built = nullptr, done = nullptr, copied = nullptr, subtracted = nullptr;
     // the request built in this slot and not yet flushed
     bool host = false;
     const void *in_ref = nullptr, *in_sci = nullptr;  // device images the build read
@@ -64,7 +67,7 @@ struct Server {
     int depth = 0, batch = 1;
     size_t img_bytes = 0, pixels = 0;
     Slot slots[kMaxDepth];
-    cudaStream_t sc = nullptr, sb = nullptr, ss = nullptr;
+    cudaStream_t sc = nullptr, sb = nullptr, ss = nullptr, so = nullptr;
     cudaEvent_t input_ready = nullptr;
     cudaEvent_t ring[kRing] = {};
     uint64_t next_seq = 0;   // sequence number of the next request
@@ -83,14 +86,14 @@ void server_free(Server *v) {
         void *bufs[] = {s.ref, s.sci, s.diff, s.mask};
         for (void *b : bufs)
             if (b) cudaFree(b);
-        cudaEvent_t evs[] = {s.built, s.done, s.copied};
+        cudaEvent_t evs[] = {s.built, s.done, s.copied, s.subtracted};
         for (cudaEvent_t e : evs)
             if (e) cudaEventDestroy(e);
     }
     for (cudaEvent_t e : v->ring)
         if (e) cudaEventDestroy(e);
     if (v->input_ready) cudaEventDestroy(v->input_ready);
-    cudaStream_t sts[] = {v->sc, v->sb, v->ss};
+    cudaStream_t sts[] = {v->sc, v->sb, v->ss, v->so};
     for (cudaStream_t s : sts)
         if (s) cudaStreamDestroy(s);
     delete v;
@@ -123,6 +126,7 @@ int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->sc, cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->sb, cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->ss, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->so, cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->input_ready, cudaEventDisableTiming);
     for (int k = 0; k < kRing && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&v->ring[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -144,6 +148,7 @@ int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.built, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.subtracted, cudaEventDisableTiming);
         // a fresh slot is free: let the first waits on `done` pass at once
         if (e == cudaSuccess) e = cudaEventRecord(s.done, v->ss);
         if (e != cudaSuccess) {
@@ -188,16 +193,20 @@ int flush(Server *v) {
         Plan *p = s.plan;
         if (s.in_mask) e = row_transform(p, s.in_ref, s.in_sci, nullptr, false, v->ss);
         if (e == cudaSuccess) e = subtract_from_rows(p, s.x, s.diff_out, v->ss);
-        if (s.host) {
+        cudaStream_t last = v->ss;  // the stream of this request's last operation
+        if (s.host) {  // results back to the host on so, overlapping the next group's work on ss
             const sfft_request &r = s.req;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r.diff, s.diff, v->img_bytes, cudaMemcpyDeviceToHost, v->ss);
+            last = v->so;
+            if (e == cudaSuccess) e = cudaEventRecord(s.subtracted, v->ss);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(v->so, s.subtracted, 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.diff, s.diff, v->img_bytes, cudaMemcpyDeviceToHost, v->so);
             if (e == cudaSuccess && r.x)
-                e = cudaMemcpyAsync(r.x, p->x_own, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost, v->ss);
+                e = cudaMemcpyAsync(r.x, p->x_own, (size_t)p->n * sizeof(double), cudaMemcpyDeviceToHost, v->so);
             if (e == cudaSuccess && r.info)
-                e = cudaMemcpyAsync(r.info, p->info_own, sizeof(sfft_solve_info), cudaMemcpyDeviceToHost, v->ss);
+                e = cudaMemcpyAsync(r.info, p->info_own, sizeof(sfft_solve_info), cudaMemcpyDeviceToHost, v->so);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(s.done, v->ss);
-        if (e == cudaSuccess) e = cudaEventRecord(v->ring[seq % kRing], v->ss);
+        if (e == cudaSuccess) e = cudaEventRecord(s.done, last);
+        if (e == cudaSuccess) e = cudaEventRecord(v->ring[seq % kRing], last);
     }
     if (e != cudaSuccess) return status_of(e);
     v->flushed = end;
@@ -360,6 +369,7 @@ int sfft_server_destroy(sfft_server_t server) {
     cudaStreamSynchronize(v->sc);
     cudaStreamSynchronize(v->sb);
     cudaStreamSynchronize(v->ss);
+    cudaStreamSynchronize(v->so);
     server_free(v);
     return SFFT_OK;
 }
