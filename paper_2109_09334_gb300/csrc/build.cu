@@ -589,6 +589,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // shared table.  Each output keeps a plain FP32 partial over kFold residue
 // classes that is folded into a two-sum accumulator.
 constexpr int kPad = 8;   // complex elements of padding per image tile / transpose region
+// threads per block of the gather: the FP32 lag-range-16 variant keeps four
+// blocks of 28 product groups resident per SM; the others take up to 48 groups
+template <typename T, int NS>
+__host__ __device__ constexpr int kGatherThreads() { return (sizeof(T) == 4 && NS == 5) ? 224 : 384; }
 constexpr int kFold = 4;  // residue classes per plain partial sum
 
 // NS output slots per lane: 8 in general; 5 when every lag half-range is at most
@@ -600,7 +604,7 @@ __device__ __forceinline__ int out_slot(int c, int s1) {
 }
 
 template <typename T, int G, int NS>
-__global__ void __launch_bounds__(384, (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_gather(int n0, int n1, int nk, int nxp, int nbk, int npairs, int hmax,
+__global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS == 5) ? 4 : 1) k_gather(int n0, int n1, int nk, int nxp, int nbk, int npairs, int hmax,
                                                 const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
                                                 const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
                                                 cpx<T> *__restrict__ Q) {
@@ -1187,25 +1191,27 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
     }
     const int G = p->na / 8;
     const int nimg = p->nimg, nxp = p->lam_closed ? 0 : p->nbx;
-    // one group of G lanes per product, whole warps, at most 384 threads per
-    // block; more products go to further blocks along y
-    const int max_groups = 384 / G;
+    const int hmax = 2 * p->cfg.w0;
+    const bool ns5 = G == 8 && hmax <= 16;
+    // one group of G lanes per product, whole warps, at most kGatherThreads
+    // threads per block; more products go to further blocks along y
+    const int max_groups = (ns5 ? kGatherThreads<T, 5>() : kGatherThreads<T, 8>()) / G;
     const int nchunks = (p->npairs + max_groups - 1) / max_groups;
     const int per_chunk = (p->npairs + nchunks - 1) / nchunks;
     int nthr = per_chunk * G;
     nthr = ((nthr + 31) / 32) * 32;
     const int ngroups = nthr / G;
-    const int hmax = 2 * p->cfg.w0;
     const int nap = p->na + kPad;
     size_t smem = (2 * (size_t)(nimg + nxp) * nap + (size_t)ngroups * nap + (size_t)p->nbk * (2 * hmax + 1)) *
                   sizeof(cpx<T>);
     void (*kern)(int, int, int, int, int, int, int, const PairDesc *, const cpx<T> *, const cpx<T> *,
                  const cpx<T> *, cpx<T> *) = nullptr;
-    if (G == 8) kern = (hmax <= 16) ? k_gather<T, 8, 5> : k_gather<T, 8, 8>;
+    if (G == 8) kern = ns5 ? k_gather<T, 8, 5> : k_gather<T, 8, 8>;
     if (G == 4) kern = k_gather<T, 4, 8>;
     if (G == 2) kern = k_gather<T, 2, 8>;
     if (!kern) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     dim3 grid(p->h1c, nchunks);
     kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, nxp, p->nbk, p->npairs, hmax, p->pairs,
                                   (const cpx<T> *)p->U, (const cpx<T> *)p->xhat, (const cpx<T> *)p->tw0,
