@@ -922,6 +922,7 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, BasisView 
 // ---------------------------------------------------------------------------
 // Stage 2: sum over m.  One block per stage-1 row.
 constexpr int kS2Out = 8;  // lag outputs per warp task in k_stage2
+constexpr int kS2Fold = 8;  // frequencies per plain partial sum in k_stage2
 
 template <typename T>
 __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npairs,
@@ -956,12 +957,19 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
         const int nsp = nw / nchr;
         const int ch = c0 + warp % nchr, sp = warp / nchr;
         const bool act = sp < nsp;
+        // each lane: plain partial sums over kS2Fold of its frequencies, folded
+        // into two-sum accumulators (one rounding per term, compensated sums)
         Acc<T> a[kS2Out];
+        T pl[kS2Out];
 #pragma unroll
-        for (int k = 0; k < kS2Out; ++k) a[k].zero();
+        for (int k = 0; k < kS2Out; ++k) {
+            a[k].zero();
+            pl[k] = (T)0;
+        }
         const int qi = ch / cpq, roff = (ch - qi * cpq) * kS2Out;
         const int r0 = roff - h1;  // first rho1 of the chunk
         if (act) {
+            int cnt = 0;
             for (int mm = sp * 32 + lane; mm < h1c; mm += nsp * 32) {
                 cpx<T> v = q[mm];
                 if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)bv.lamq(pd.b, qi) * h1c + mm]);
@@ -972,12 +980,22 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
                 for (int k = 0; k < kS2Out; ++k) {
                     if (roff + k < nr1) {
                         const cpx<T> e = conj(tw1[idx]);
-                        a[k].add(v.re * e.re - v.im * e.im);
+                        pl[k] += v.re * e.re - v.im * e.im;
                     }
                     idx += mm;
                     if (idx >= n1) idx -= n1;
                 }
+                if (++cnt == kS2Fold) {
+#pragma unroll
+                    for (int k = 0; k < kS2Out; ++k) {
+                        a[k].add(pl[k]);
+                        pl[k] = (T)0;
+                    }
+                    cnt = 0;
+                }
             }
+#pragma unroll
+            for (int k = 0; k < kS2Out; ++k) a[k].add(pl[k]);
         }
 #pragma unroll
         for (int k = 0; k < kS2Out; ++k)
