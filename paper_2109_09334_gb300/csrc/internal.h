@@ -71,9 +71,8 @@ struct FTab {
     const T *fx, *fy, *bx, *by;
 };
 
-// Largest basis sizes (kernel terms, background terms, functions per axis).
+// Largest basis sizes (kernel terms, functions per axis).
 constexpr int kMaxKTerms = 40;
-constexpr int kMaxBTerms = 36;
 constexpr int kMaxFun = 8;
 // Largest number of science (and of reference) images in the co-added form of the decorrelation.
 constexpr int kMaxCoadd = 16;
