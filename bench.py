@@ -221,7 +221,7 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def survey_alg_bytes(spec):
+def pair_alg_bytes(spec):
     """Bytes the method itself must move per pair: read R, S once, write and read
     each forward spectrum once, read the R and S spectra again, write D."""
     f = spec.fit
@@ -486,7 +486,7 @@ def run_ours(args):
                                   "frac": ach / alu_peak, "traffic": load_traffic(kern) if kern.startswith("k_") and " " not in kern else None, "kernel": kern,
                                   "stage": top, "alg_flops_per_launch": sf[top], "alg_bytes_per_launch": sb[top],
                                   "peak_source": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {clk:.0f} MHz"}
-        ba = survey_alg_bytes(spec)
+        ba = pair_alg_bytes(spec)
         result["pair_roofline"] = {"alg_bytes_per_pair": ba, "achieved_GBs": ba / (ms_step / 1e3) / 1e9,
                                    "frac": ba / (ms_step / 1e3) / 1e9 / peak}
 
