@@ -38,6 +38,10 @@
  *
  * Memory: every pointer named d_* is device memory owned by the caller; h_*
  * is host memory owned by the caller (page-locked for asynchronous copies).
+ * Device images R, S and masks are read with 16-byte vector loads: d_ref,
+ * d_sci and d_mask must be 16-byte aligned (cudaMalloc and PyTorch
+ * allocations are); the calls return SFFT_ERR_INVALID before any launch
+ * otherwise.
  * A plan owns its workspace; it is not thread-safe and serves one pair at a
  * time on the stream it is used with.
  *

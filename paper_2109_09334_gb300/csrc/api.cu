@@ -513,6 +513,7 @@ int sfft_replay_stage(sfft_plan_t plan, int stage, sfft_stream_t stream) {
 int sfft_build_system(sfft_plan_t plan, const void *d_ref, const void *d_sci, const uint8_t *d_mask,
                       double *d_M, double *d_rhs, sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_M || !d_rhs) return SFFT_ERR_INVALID;
+    if (!images_aligned(d_ref, d_sci, d_mask)) return SFFT_ERR_INVALID;
     Plan *p = (Plan *)plan;
     p->last_stream = (cudaStream_t)stream;
     return status_of(build_system(p, d_ref, d_sci, d_mask, d_M, d_rhs, (cudaStream_t)stream));
@@ -530,6 +531,7 @@ int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
                   sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_x || !d_diff) return SFFT_ERR_INVALID;
     if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    if (!images_aligned(d_ref, d_sci, nullptr)) return SFFT_ERR_INVALID;
     Plan *p = (Plan *)plan;
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
@@ -542,6 +544,7 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
                        sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
     if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    if (!images_aligned(d_ref, d_sci, nullptr)) return SFFT_ERR_INVALID;
     Plan *p = (Plan *)plan;
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_pair(p, d_ref, d_sci, nullptr, nullptr, nullptr, nullptr, nullptr, d_diff, s);
@@ -673,6 +676,8 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
                   double *d_rhs, double *d_x, sfft_solve_info *d_info, void *d_diff, sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
     if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
+    if (!images_aligned(d_ref, d_sci, nullptr)) return SFFT_ERR_INVALID;
+    if (!images_aligned(d_ref, d_sci, d_mask)) return SFFT_ERR_INVALID;
     return run_pair((Plan *)plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, (cudaStream_t)stream);
 }
 
@@ -683,6 +688,7 @@ int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !d_refs[i] || !d_scis[i] || !d_diffs[i]) return SFFT_ERR_INVALID;
         if (d_diffs[i] == d_refs[i] || d_diffs[i] == d_scis[i]) return SFFT_ERR_INVALID;
+        if (!images_aligned(d_refs[i], d_scis[i], d_masks ? d_masks[i] : nullptr)) return SFFT_ERR_INVALID;
         if (((Plan *)plans[i])->fp64 != ((Plan *)plans[0])->fp64) return SFFT_ERR_INVALID;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return SFFT_ERR_INVALID;  // one workspace per pair

@@ -160,6 +160,13 @@ struct Plan {
     PairDesc *host_pairs;  // [npairs]
 };
 
+// Device images and masks are read with 16-byte vector loads: every entry
+// point checks their alignment before any launch.
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+inline bool images_aligned(const void *ref, const void *sci, const void *mask) {
+    return aligned16(ref) && aligned16(sci) && (mask == nullptr || aligned16(mask));
+}
+
 // plans (api.cu): validation, allocation + tables, release
 int plan_validate(const sfft_config *c);
 int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out);  // cfg already validated

@@ -379,6 +379,7 @@ int sfft_submit(sfft_server_t server, const sfft_request *req, sfft_ticket *tick
     if (!req->ref || !req->sci || !req->diff) return SFFT_ERR_INVALID;
     if (req->memory != SFFT_REQ_DEVICE && req->memory != SFFT_REQ_HOST) return SFFT_ERR_INVALID;
     if (req->diff == req->ref || req->diff == req->sci) return SFFT_ERR_INVALID;
+    if (req->memory == SFFT_REQ_DEVICE && !images_aligned(req->ref, req->sci, req->mask)) return SFFT_ERR_INVALID;
     Server *v = (Server *)server;
     std::lock_guard<std::mutex> lock(v->mu);
     uint64_t seq = 0;
@@ -493,6 +494,7 @@ int sfft_pool_submit(sfft_pool_t pool, const sfft_config *cfg, const sfft_reques
     if (!pool || !cfg || !req || !ticket) return SFFT_ERR_INVALID;
     if (!req->ref || !req->sci || !req->diff) return SFFT_ERR_INVALID;
     if (req->memory != SFFT_REQ_DEVICE && req->memory != SFFT_REQ_HOST) return SFFT_ERR_INVALID;
+    if (req->memory == SFFT_REQ_DEVICE && !images_aligned(req->ref, req->sci, req->mask)) return SFFT_ERR_INVALID;
     const int v = plan_validate(cfg);
     if (v) return v;
     Pool *pl = (Pool *)pool;

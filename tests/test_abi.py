@@ -95,3 +95,19 @@ def test_set_tuning_checks_before_use(lib):
     for bad in ((3, 0, 0, 0), (32, 0, 0, 0), (-1, 0, 0, 0), (0, 5, 0, 0), (0, 0, -1, 0), (0, 0, 0, 513)):
         assert lib.sfft_plan_set_tuning(fake, arr(*bad)) == binding.SFFT_ERR_INVALID
     assert lib.sfft_plan_tuning(None, arr(0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
+
+
+def test_misaligned_images_rejected(lib):
+    """Images and masks must be 16-byte aligned (vector loads); checked before any use."""
+    fake = ctypes.c_void_p(4096)  # never dereferenced: every call below is rejected first
+    odd = ctypes.c_void_p(4096 + 4)
+    ok = ctypes.c_void_p(8192)
+    assert lib.sfft_build_system(fake, odd, ok, None, ok, ok, None) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_build_system(fake, ok, odd, None, ok, ok, None) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_build_system(fake, ok, ok, ctypes.c_void_p(4096 + 8), ok, ok, None) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_run_pair(fake, odd, ok, None, None, None, None, None, ctypes.c_void_p(12288), None) == \
+        binding.SFFT_ERR_INVALID
+    assert lib.sfft_subtract(fake, ok, odd, ok, ctypes.c_void_p(12288), None) == binding.SFFT_ERR_INVALID
+    req = binding.make_request(odd.value, ok.value, ctypes.c_void_p(12288).value)
+    t = binding.sfft_ticket()
+    assert lib.sfft_submit(fake, ctypes.byref(req), ctypes.byref(t)) == binding.SFFT_ERR_INVALID
