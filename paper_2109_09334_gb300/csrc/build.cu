@@ -192,12 +192,10 @@ __global__ void __launch_bounds__(256) k_row_moments(int n1, int dk, int db, con
     for (int v = 0; v < 7; ++v) pRR[v] = pR[v] = (T)0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) pRS[v] = pS[v] = (T)0;
-#pragma unroll 4
-    for (int y = tid; y < n1; y += nthr) {
-        const T keep = (mask == nullptr || mask[rowoff + y] != 0) ? (T)1 : (T)0;
-        const T rv = (T)R[rowoff + y] * keep;
-        const T sv = (T)S[rowoff + y] * keep;
-        const T yt = coord<T>(y, n1);
+    const T inv = (T)1 / (T)(n1 - 1);  // yt = (2y - (n1 - 1)) / (n1 - 1)
+    auto accum = [&](int y, T r, T sval, bool keep) {
+        const T rv = keep ? r : (T)0, sv = keep ? sval : (T)0;
+        const T yt = (T)(2 * y - (n1 - 1)) * inv;
         T p = (T)1;
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
@@ -209,6 +207,26 @@ __global__ void __launch_bounds__(256) k_row_moments(int n1, int dk, int db, con
             }
             p *= yt;
         }
+    };
+    if (sizeof(I) == 4 && (n1 & 3) == 0) {
+        // rows of 16-byte-aligned float images: four pixels per load, all of a
+        // thread's loads in flight
+        const float4 *R4 = reinterpret_cast<const float4 *>(R + rowoff);
+        const float4 *S4 = reinterpret_cast<const float4 *>(S + rowoff);
+        const uchar4 *M4 = mask ? reinterpret_cast<const uchar4 *>(mask + rowoff) : nullptr;
+#pragma unroll 4
+        for (int c = tid; c < (n1 >> 2); c += nthr) {
+            const float4 r = __ldg(R4 + c), sv = __ldg(S4 + c);
+            const uchar4 m = M4 ? M4[c] : make_uchar4(1, 1, 1, 1);
+            accum(4 * c, (T)r.x, (T)sv.x, m.x != 0);
+            accum(4 * c + 1, (T)r.y, (T)sv.y, m.y != 0);
+            accum(4 * c + 2, (T)r.z, (T)sv.z, m.z != 0);
+            accum(4 * c + 3, (T)r.w, (T)sv.w, m.w != 0);
+        }
+    } else {
+#pragma unroll 4
+        for (int y = tid; y < n1; y += nthr)
+            accum(y, (T)R[rowoff + y], (T)S[rowoff + y], mask == nullptr || mask[rowoff + y] != 0);
     }
     // the partials that are needed, at their moment index
 #pragma unroll
