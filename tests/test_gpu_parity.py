@@ -72,6 +72,8 @@ SMALL = [
     (37, 41, 2, 1, 0, 1, 1, True),
     (17, 19, 1, 1, 1, 0, 0, False),
     (100, 96, 4, 4, 2, 2, 1, False),
+    # a half-width above 16: Lambda through the gather, not in closed form
+    (64, 96, 2, 20, 1, 1, 1, False),
 ]
 
 

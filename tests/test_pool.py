@@ -128,3 +128,34 @@ def test_admission_by_memory_budget(lib):
     assert pool.wait(ta[0], timeout_us=0)  # a released lane's requests have completed
     assert pool.wait(tb[0], timeout_us=60_000_000)
     pool.close()
+
+
+@pytest.mark.gpu
+def test_pool_mixes_polynomial_and_bspline_configurations(lib):
+    """A B-spline configuration is its own lane; results equal sfft_run_pair's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, SfftPool, info_from_bytes
+    cases = [(64, 64, 2, 1, 1, 1, None), (64, 64, 2, 0, 0, 1, (2, 1, 1, 0)), (48, 64, 2, 0, 0, 0, (1, 0, 1, 1))]
+    expected, inputs = [], []
+    for k, (n0, n1, w, dk, db, cpr, spline) in enumerate(cases):
+        R, S = pair(n0, n1, 70 + k)
+        plan = SfftPlan(n0, n1, w, w, dk, db, cpr, spline=spline)
+        D, x, info, _, _ = plan.run_pair(torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda())
+        torch.cuda.synchronize()
+        expected.append((D.cpu().numpy(), x.cpu().numpy()))
+        inputs.append((R, S))
+        plan.close()
+    pool = SfftPool(64 << 30, depth=2, batch=1)
+    handles = []
+    for (n0, n1, w, dk, db, cpr, spline), (R, S) in zip(cases, inputs):
+        got = pool.submit(torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda(), w, w, dk, db, cpr, spline=spline)
+        assert got is not None
+        handles.append(got)
+    assert pool.usage[1] == len(cases)
+    for k, (t, D, x, info) in enumerate(handles):
+        assert pool.wait(t, timeout_us=60_000_000)
+        assert info_from_bytes(info.cpu().numpy())["status"] == 0
+        assert np.array_equal(D.cpu().numpy(), expected[k][0]), k
+        assert np.array_equal(x.cpu().numpy(), expected[k][1]), k
+    pool.close()
