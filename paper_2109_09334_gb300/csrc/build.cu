@@ -988,12 +988,17 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
         const int r0 = roff - h1;  // first rho1 of the chunk
         if (act) {
             int cnt = 0;
-            for (int mm = sp * 32 + lane; mm < h1c; mm += nsp * 32) {
+            const int mstep = nsp * 32;
+            const int dstep = imod(mstep * r0, n1);  // change of (mm r0) mod n1 per step of mm
+            int idx0 = imod((sp * 32 + lane) * r0, n1);
+            for (int mm = sp * 32 + lane; mm < h1c; mm += mstep) {
                 cpx<T> v = q[mm];
                 if (pd.kind == PK_LAMBDA) v = cmul(v, yhat[(size_t)bv.lamq(pd.b, qi) * h1c + mm]);
                 const T wm = (mm == 0 || (2 * mm == n1)) ? (T)1 : (T)2;
                 v = scale(v, wm);
-                int idx = imod(mm * r0, n1);  // (mm rho1) mod n1, stepped by mm
+                int idx = idx0;  // (mm rho1) mod n1, stepped by mm over the chunk's lags
+                idx0 += dstep;
+                if (idx0 >= n1) idx0 -= n1;
 #pragma unroll
                 for (int k = 0; k < kS2Out; ++k) {
                     if (roff + k < nr1) {

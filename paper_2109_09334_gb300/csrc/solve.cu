@@ -581,8 +581,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     }
     __syncthreads();
     int wofs[kMaxBatch + 1];  // flat W^T y tasks of all systems
-    wofs[0] = 0;
-    for (int b = 0; b < nsys; ++b) wofs[b + 1] = wofs[b] + ((ba.sys[b].n + 31) / 32) * kSeg;
+    int yofs[kMaxBatch + 1];  // flat W z tasks (row pairs) of all systems
+    wofs[0] = yofs[0] = 0;
+    for (int b = 0; b < nsys; ++b) {
+        wofs[b + 1] = wofs[b] + ((ba.sys[b].n + 31) / 32) * kSeg;
+        yofs[b + 1] = yofs[b] + (ba.sys[b].n + 1) / 2;
+    }
     for (int it = 0; it <= kMaxIters && done != all; ++it) {
         // r = rhs - M x (FP64); z = D r
         for (int row = bid * nw + warp; row < nrows_all; row += nbk * nw) {
@@ -621,13 +625,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             }
         }
         if (done == all) break;
-        // y = W z  (W lower triangular)
-        for (int row = bid * nw + warp; row < nrows_all; row += nbk * nw) {
-            const int b = sys_of(nrow, nsys, row), i = row - nrow[b];
+        // y = W z  (W lower triangular; row i has i + 1 entries).  A warp task
+        // takes rows k and n - 1 - k, n + 1 entries together, so that every
+        // task has the same length.
+        for (int task = bid * nw + warp; task < yofs[nsys]; task += nbk * nw) {
+            const int b = sys_of(yofs, nsys, task), k = task - yofs[b];
             if (done & (1u << b)) continue;
             const SolveArgs<T> &s = ba.sys[b];
-            const T a = dot_warp<T>(s.W + (size_t)i * s.n, s.z, lane, i + 1);
-            if (lane == 0) s.y[i] = a;
+            const int i2 = s.n - 1 - k;
+            const T a = dot_warp<T>(s.W + (size_t)k * s.n, s.z, lane, k + 1);
+            if (lane == 0) s.y[k] = a;
+            if (i2 != k) {
+                const T a2 = dot_warp<T>(s.W + (size_t)i2 * s.n, s.z, lane, i2 + 1);
+                if (lane == 0) s.y[i2] = a2;
+            }
         }
         grid.sync();
         // w = W^T y in kSeg row segments (coalesced rows of W), summed in a fixed order
