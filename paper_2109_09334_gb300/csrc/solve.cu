@@ -68,24 +68,40 @@ struct TileSmem {
 template <typename T>
 __device__ void tile_gemm(T (&acc)[4][4], TileSmem<T> &sm, const T *Ag, int lda, int arow0, int arows,
                           const T *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
+    constexpr int kLd = kTile * kNB / kThreads;  // elements of each operand per thread
     const int tid = threadIdx.x;
     const int tr = tid / 16, tc = tid % 16;
     for (int kk = k0; kk < k1; kk += kNB) {
         const int kn = min(kNB, k1 - kk);
-        for (int e = tid; e < kTile * kNB; e += kThreads) {
-            const int i = e / kNB, p = e % kNB;
-            sm.a[i][p] = (i < arows && p < kn) ? Ag[(size_t)(arow0 + i) * lda + kk + p] : (T)0;
+        // all loads of the chunk are issued before the first store to shared
+        // memory, so that their latencies overlap
+        T ra[kLd], rb[kLd];
+#pragma unroll
+        for (int q = 0; q < kLd; ++q) {
+            const int e = tid + q * kThreads, i = e / kNB, p = e % kNB;
+            ra[q] = (i < arows && p < kn) ? Ag[(size_t)(arow0 + i) * lda + kk + p] : (T)0;
         }
         if (transB) {
-            for (int e = tid; e < kTile * kNB; e += kThreads) {
-                const int j = e / kNB, p = e % kNB;
-                sm.b[p][j] = (j < bcols && p < kn) ? Bg[(size_t)(bcol0 + j) * ldb + kk + p] : (T)0;
+#pragma unroll
+            for (int q = 0; q < kLd; ++q) {
+                const int e = tid + q * kThreads, j = e / kNB, p = e % kNB;
+                rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(bcol0 + j) * ldb + kk + p] : (T)0;
             }
         } else {
-            for (int e = tid; e < kTile * kNB; e += kThreads) {
-                const int p = e / kTile, j = e % kTile;
-                sm.b[p][j] = (j < bcols && p < kn) ? Bg[(size_t)(kk + p) * ldb + bcol0 + j] : (T)0;
+#pragma unroll
+            for (int q = 0; q < kLd; ++q) {
+                const int e = tid + q * kThreads, p = e / kTile, j = e % kTile;
+                rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(kk + p) * ldb + bcol0 + j] : (T)0;
             }
+        }
+#pragma unroll
+        for (int q = 0; q < kLd; ++q) {
+            const int e = tid + q * kThreads;
+            sm.a[e / kNB][e % kNB] = ra[q];
+            if (transB)
+                sm.b[e % kNB][e / kNB] = rb[q];
+            else
+                sm.b[e / kTile][e % kTile] = rb[q];
         }
         __syncthreads();
 #pragma unroll 8
