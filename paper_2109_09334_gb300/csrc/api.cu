@@ -676,7 +676,6 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
                   double *d_rhs, double *d_x, sfft_solve_info *d_info, void *d_diff, sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_diff) return SFFT_ERR_INVALID;
     if (d_diff == d_ref || d_diff == d_sci) return SFFT_ERR_INVALID;
-    if (!images_aligned(d_ref, d_sci, nullptr)) return SFFT_ERR_INVALID;
     if (!images_aligned(d_ref, d_sci, d_mask)) return SFFT_ERR_INVALID;
     return run_pair((Plan *)plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, (cudaStream_t)stream);
 }

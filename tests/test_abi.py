@@ -111,3 +111,56 @@ def test_misaligned_images_rejected(lib):
     req = binding.make_request(odd.value, ok.value, ctypes.c_void_p(12288).value)
     t = binding.sfft_ticket()
     assert lib.sfft_submit(fake, ctypes.byref(req), ctypes.byref(t)) == binding.SFFT_ERR_INVALID
+
+
+def test_header_serves_a_plain_c_program(lib, tmp_path):
+    """include/sfft.h compiles as C99 with warnings as errors, and a C program
+    linked against libsfft.so (no torch, no CUDA headers) calls the entry
+    points that need no GPU: the unknown count of a polynomial and a B-spline
+    configuration equals the oracle's, destroying a NULL plan is a no-op, and
+    invalid arguments come back as status codes."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(binding.LIB)
+    src = tmp_path / "use_sfft.c"
+    src.write_text(r"""
+#include "sfft.h"
+#include <stdio.h>
+#include <string.h>
+
+static int count(int basis, int cpr, int32_t *n) {
+    sfft_config c;
+    memset(&c, 0, sizeof c);
+    c.n0 = 4096; c.n1 = 4096; c.w0 = 8; c.w1 = 8; c.const_phot_ratio = cpr;
+    c.dtype = SFFT_F32; c.precision = SFFT_PREC_MIXED; c.basis = basis;
+    if (basis == SFFT_BASIS_POLY) { c.dk = 2; c.db = 2; }
+    else { c.kdeg = 1; c.kint = 1; c.bdeg = 2; c.bint = 1; }
+    return sfft_num_unknowns(&c, n);
+}
+
+int main(void) {
+    int32_t np = 0, nb = 0;
+    if (count(SFFT_BASIS_POLY, 1, &np) != SFFT_OK) return 2;
+    if (count(SFFT_BASIS_BSPLINE, 0, &nb) != SFFT_OK) return 3;
+    if (sfft_num_unknowns(NULL, &np) != SFFT_ERR_INVALID) return 4;
+    if (sfft_plan_destroy(NULL) != SFFT_OK) return 5;          /* documented no-op */
+    uint64_t bytes = 0;
+    if (sfft_plan_workspace_bytes(NULL, &bytes) != SFFT_ERR_INVALID) return 6;
+    printf("%d %d %s\n", (int)np, (int)nb, sfft_status_string(SFFT_ERR_SINGULAR));
+    return 0;
+}
+""")
+    exe = tmp_path / "use_sfft"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(root, "include"),
+                    str(src), "-L", libdir, "-lsfft", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split(None, 2)
+    poly = oracle.OracleConfig(4096, 4096, 8, 8, 2, 2, True)
+    spl = oracle.OracleConfig(4096, 4096, 8, 8, 0, 0, False, "bspline", 1, 1, 2, 1)
+    assert int(out[0]) == oracle.num_unknowns(poly) == 1735
+    assert int(out[1]) == oracle.num_unknowns(spl)
+    assert out[2].strip() == binding.status_string(-4)
