@@ -164,3 +164,52 @@ int main(void) {
     assert int(out[0]) == oracle.num_unknowns(poly) == 1735
     assert int(out[1]) == oracle.num_unknowns(spl)
     assert out[2].strip() == binding.status_string(-4)
+
+
+def test_create_rejects_configurations_before_device_use(lib):
+    """Plan, server and pool creation check their arguments before any CUDA
+    call (so this runs without a GPU): sizes outside [16, 4096], lag ranges
+    that do not fit one period (4w + 1 <= n, and <= 64 along a power-of-two
+    x axis), degrees above 3, B-spline limits, unknown enums and NULL outputs
+    each return their status, and the output handle is left NULL."""
+    INV, UNS = binding.SFFT_ERR_INVALID, -8
+    base = dict(n0=64, n1=64, w0=2, w1=2, dk=1, db=1, cpr=1)
+
+    def cfg(spline=None, dtype="float32", precision="mixed", **kw):
+        a = dict(base, **kw)
+        return binding.make_config(a["n0"], a["n1"], a["w0"], a["w1"], a["dk"], a["db"], a["cpr"],
+                                   dtype, precision, spline)
+
+    def bad(c, field, value):
+        setattr(c, field, value)
+        return c
+
+    cases = [
+        (cfg(n0=15), UNS), (cfg(n1=15), UNS), (cfg(n0=4097), UNS), (cfg(n1=4097), UNS), (cfg(n0=0), UNS),
+        (cfg(n0=4096, w0=16), UNS),           # 4 w0 + 1 = 65 > 64 along a power-of-two x axis
+        (cfg(n0=100, n1=100, w0=25), UNS),    # 4 w0 + 1 = 101 > n0
+        (cfg(n1=64, w1=16), UNS),             # 4 w1 + 1 = 65 > n1
+        (cfg(w0=-1), INV), (cfg(w1=-1), INV),
+        (cfg(dk=4), UNS), (cfg(db=4), UNS), (cfg(dk=-1), INV),
+        (bad(cfg(), "dtype", 2), INV), (bad(cfg(), "precision", 5), INV), (bad(cfg(), "basis", 7), INV),
+        (cfg(spline=(1, 1, 1, 1)), INV),                  # B-splines need dk = db = 0
+        (cfg(spline=(4, 0, 1, 0), dk=0, db=0), UNS),      # degree above 3
+        (cfg(spline=(3, 3, 1, 0), dk=0, db=0), UNS),      # 7 functions per axis
+        (cfg(spline=(1, -1, 1, 0), dk=0, db=0), INV),
+    ]
+    for c, want in cases:
+        h = ctypes.c_void_p(1234)
+        assert lib.sfft_plan_create(ctypes.byref(c), None, ctypes.byref(h)) == want, c
+        assert h.value is None
+        h = ctypes.c_void_p(1234)
+        assert lib.sfft_server_create(ctypes.byref(c), 2, 1, ctypes.byref(h)) == want, c
+        assert h.value is None
+    good = cfg()
+    h = ctypes.c_void_p()
+    assert lib.sfft_plan_create(None, None, ctypes.byref(h)) == INV
+    assert lib.sfft_plan_create(ctypes.byref(good), None, None) == INV
+    for depth, batch in [(0, 1), (9, 1), (2, 0), (2, 3)]:
+        assert lib.sfft_server_create(ctypes.byref(good), depth, batch, ctypes.byref(h)) == INV
+        assert lib.sfft_pool_create(ctypes.c_uint64(1 << 30), depth, batch, ctypes.byref(h)) == INV
+    assert lib.sfft_pool_create(ctypes.c_uint64(0), 2, 1, ctypes.byref(h)) == INV
+    assert lib.sfft_pool_create(ctypes.c_uint64(1 << 30), 2, 1, None) == INV
