@@ -276,3 +276,46 @@ def test_flux_conservation_physical_psf():
     assert abs(a00_00 - 1.05) < 0.01
     assert abs(a01_00 - 0.05) < 0.01
     assert abs(a10_00) < 0.01
+
+
+@pytest.mark.parametrize("n0,n1", [(13, 11), (16, 16)])
+def test_lambda_lag_sums_against_moment_closed_form(n0, n1):
+    """Lambda_ts(rho) = sum_x g_t(x) T_s((x + rho) mod N) for g_t = x^i y^j R and
+    T_s = x^p y^q (App. B, Eq. B8) against its closed form: on rows whose
+    shifted index stays inside the image the shifted coordinate is
+    x + 2 rho0/(n0-1); on the rows that wrap it moves by a further
+    -/+ 2 n0/(n0-1) (likewise along y).  So Lambda is a sum over four
+    row/column blocks of binomial expansions in the blocks' 2-D moments
+    mu_B(u, v) = sum_B x^u y^v R, with no circular index anywhere."""
+    from math import comb
+    R = random_field(n0, n1, seed=17)
+    xt = bruteforce.coords(n0)
+    yt = bruteforce.coords(n1)
+
+    def classes(n, rho):
+        """Index sets and coordinate offsets: the rows that stay inside and those that wrap."""
+        idx = np.arange(n)
+        wraps = (idx + rho >= n) | (idx + rho < 0)
+        d = 2.0 * rho / (n - 1)
+        dw = d - np.sign(rho) * 2.0 * n / (n - 1)
+        return [(idx[~wraps], d), (idx[wraps], dw)]
+
+    for (i, j) in [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1)]:
+        g = np.outer(xt ** i, yt ** j) * R
+        for (p, q) in [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]:
+            T = np.outer(xt ** p, yt ** q)
+            for r0 in range(-3, 4):
+                for r1 in range(-3, 4):
+                    closed = 0.0
+                    for rows, d0 in classes(n0, r0):
+                        for cols, d1 in classes(n1, r1):
+                            if rows.size == 0 or cols.size == 0:
+                                continue
+                            blk = R[np.ix_(rows, cols)]
+                            xs, ys = xt[rows], yt[cols]
+                            for a in range(p + 1):
+                                for b in range(q + 1):
+                                    mu = xs ** (i + a) @ blk @ ys ** (j + b)
+                                    closed += comb(p, a) * comb(q, b) * d0 ** (p - a) * d1 ** (q - b) * mu
+                    lag = oracle.lag_sum(g, T, r0, r1)
+                    assert abs(lag - closed) <= 1e-12 * max(1.0, np.abs(R).sum()), (i, j, p, q, r0, r1)
