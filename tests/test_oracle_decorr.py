@@ -138,3 +138,25 @@ def test_saturation_mask_matches_binary_dilation():
         m_in = (rng.random((n0, n1)) > 0.1).astype(np.uint8)
         got2 = masking.saturation_mask(R, S, 97.0, 98.5, grow, m_in)
         assert np.array_equal(got2.astype(bool), want & (m_in != 0))
+
+
+def test_saturation_mask_edge_cases():
+    """Closed expectations: a pixel exactly at its level counts as saturated;
+    nothing saturated keeps everything; a window wider than the image masks
+    every pixel once anything saturates; a saturated corner pixel masks exactly
+    the (grow + 1)^2 pixels of the clipped square at that corner."""
+    from oracle import masking
+    n0, n1 = 24, 19
+    R = np.zeros((n0, n1))
+    S = np.zeros((n0, n1))
+    assert masking.saturation_mask(R, S, 1.0, 1.0, 3).all()
+    R[5, 7] = 1.0                                   # exactly at the level
+    m = masking.saturation_mask(R, S, 1.0, 2.0, 0)
+    assert m[5, 7] == 0 and m.sum() == n0 * n1 - 1
+    assert not masking.saturation_mask(R, S, 1.0, 2.0, 30).any()
+    R[5, 7] = 0.0
+    S[n0 - 1, 0] = 5.0                              # a saturated corner of S
+    for grow in (0, 1, 16):
+        m = masking.saturation_mask(R, S, 1.0, 5.0, grow)
+        assert (m == 0).sum() == (grow + 1) ** 2
+        assert (m[n0 - 1 - grow:, :grow + 1] == 0).all()
