@@ -184,7 +184,10 @@ int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double 
  * one stream, or make one wait for the other.  The first call on each device
  * (made with that device current) does one-time setup.  It looks up the
  * array's address and sizes the cooperative grid, checking both results.
- * Make that call before any stream capture begins.
+ * Make that call before any stream capture begins.  The setup is kept for
+ * the life of the process and belongs to the device's context at that time:
+ * calls must not span a cudaDeviceReset of the device (or any other end of
+ * its primary context), after which the recorded address is stale.
  */
 #define SFFT_SOLVE_STATIC_MAX_N 1024
 int sfft_solve_static(const double *d_M, const double *d_rhs, int32_t n, int32_t precision,
@@ -361,15 +364,30 @@ int sfft_submit(sfft_server_t server, const sfft_request *req, sfft_ticket *tick
 /* Enqueue the solves and subtractions of an incomplete batch now. */
 int sfft_flush(sfft_server_t server);
 
-/* SFFT_OK if the ticket's request has completed, SFFT_ERR_BUSY if not yet. */
+/*
+ * SFFT_OK if the ticket's request has completed, SFFT_ERR_BUSY if not yet,
+ * SFFT_ERR_CUDA if a completion query reported a CUDA error (sticky: every
+ * later submit, poll and wait on this server returns it; destroy it).
+ */
 int sfft_poll(sfft_server_t server, const sfft_ticket *ticket);
 
 /*
  * Wait until the ticket's request has completed: SFFT_OK, or
- * SFFT_ERR_TIMEOUT after timeout_us microseconds (timeout_us < 0: no limit).
- * Numerical failures are reported in the request's info, as for sfft_solve.
+ * SFFT_ERR_TIMEOUT after timeout_us microseconds (timeout_us < 0: no limit),
+ * or SFFT_ERR_CUDA as soon as a completion query reports a CUDA error (as
+ * for sfft_poll; the wait never spins on a failed query).  Numerical
+ * failures are reported in the request's info, as for sfft_solve.
  */
 int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_us);
+
+/*
+ * Testing hook, off by default: with enable != 0 the server's completion
+ * queries report a CUDA error (as a failed device would) without asking the
+ * device, so that the error paths of sfft_poll, sfft_wait and sfft_submit can
+ * be exercised with no fault on the GPU.  The work already enqueued still
+ * runs; sfft_server_destroy waits for it as usual.
+ */
+int sfft_server_debug_fail_queries(sfft_server_t server, int32_t enable);
 
 /*
  * Make `stream` wait (on the device, without blocking the host) until the

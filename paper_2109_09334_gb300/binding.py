@@ -100,6 +100,7 @@ def library():
         lib.sfft_wait.argtypes = [vp, tkp, ctypes.c_int64]
         lib.sfft_stream_wait_ticket.argtypes = [vp, tkp, vp]
         lib.sfft_server_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sfft_server_debug_fail_queries.argtypes = [vp, i32]
         ptk = ctypes.POINTER(sfft_pool_ticket)
         lib.sfft_pool_create.argtypes = [ctypes.c_uint64, i32, i32, ctypes.POINTER(vp)]
         lib.sfft_pool_destroy.argtypes = [vp]
@@ -330,6 +331,11 @@ def sfft_server_launch_count(server):
     c = ctypes.c_uint64()
     _check(library().sfft_server_launch_count(server, ctypes.byref(c)), "sfft_server_launch_count")
     return c.value
+
+
+def sfft_server_debug_fail_queries(server, enable):
+    """Testing hook: make the server's completion queries report a CUDA error."""
+    _check(library().sfft_server_debug_fail_queries(server, int(bool(enable))), "sfft_server_debug_fail_queries")
 
 
 def sfft_pool_create(budget_bytes, depth=2, batch=1):

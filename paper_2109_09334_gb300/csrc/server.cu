@@ -75,6 +75,13 @@ struct Server {
     uint64_t watermark = 0;  // every request below it has completed
     std::mutex mu;
     int refs = 0;  // callers waiting on it through a pool (guarded by the pool's lock)
+    // Sticky failure: once a completion query reports a CUDA error, every
+    // later submit, poll and wait returns it (the requests in flight can no
+    // longer be known to complete).
+    int err = SFFT_OK;
+    // testing hook (sfft_server_debug_fail_queries): completion queries
+    // report a CUDA error without asking the device
+    bool fail_queries = false;
 };
 
 namespace {
@@ -99,18 +106,28 @@ void server_free(Server *v) {
     delete v;
 }
 
+// Completion query of one request's event (through the testing hook).
+cudaError_t query_done(Server *v, cudaEvent_t ev, bool block) {
+    if (v->fail_queries) return cudaErrorLaunchFailure;
+    return block ? cudaEventSynchronize(ev) : cudaEventQuery(ev);
+}
+
 // Advance the watermark over completed requests (caller holds mu).  Only
-// flushed requests have their completion event recorded.
-void advance(Server *v) {
+// flushed requests have their completion event recorded.  Returns SFFT_OK,
+// or SFFT_ERR_CUDA (sticky) if a query reported an error.
+int advance(Server *v) {
+    if (v->err != SFFT_OK) return v->err;
     while (v->watermark < v->flushed) {
-        const cudaError_t e = cudaEventQuery(v->ring[v->watermark % kRing]);
-        if (e == cudaErrorNotReady) return;
+        const cudaError_t e = query_done(v, v->ring[v->watermark % kRing], false);
+        if (e == cudaErrorNotReady) return SFFT_OK;
         if (e != cudaSuccess) {
-            cudaGetLastError();
-            return;
+            if (!v->fail_queries) cudaGetLastError();
+            v->err = SFFT_ERR_CUDA;
+            return v->err;
         }
         ++v->watermark;
     }
+    return SFFT_OK;
 }
 
 int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
@@ -215,15 +232,20 @@ int flush(Server *v) {
 
 int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
     const bool host = r->memory == SFFT_REQ_HOST;
+    if (v->err != SFFT_OK) return v->err;
     // keep at most kRing requests in flight: the ring slot must be free
     while (v->next_seq - v->watermark >= (uint64_t)kRing) {
         if (v->watermark >= v->flushed) {
             const int rc = flush(v);
             if (rc != SFFT_OK) return rc;
         }
-        const cudaError_t e = cudaEventSynchronize(v->ring[v->watermark % kRing]);
-        if (e != cudaSuccess) return status_of(e);
-        advance(v);
+        const cudaError_t e = query_done(v, v->ring[v->watermark % kRing], true);
+        if (e != cudaSuccess) {
+            v->err = SFFT_ERR_CUDA;
+            return v->err;
+        }
+        const int rc = advance(v);
+        if (rc != SFFT_OK) return rc;
     }
     const uint64_t seq = v->next_seq;
     // the request that used this slot before belongs to an earlier, full,
@@ -286,7 +308,9 @@ bool same_config(const sfft_config &a, const sfft_config &b) { return memcmp(&a,
 // every request of the lane has completed (caller holds the pool's lock)
 bool lane_idle(Lane &l) {
     std::lock_guard<std::mutex> lock(l.srv->mu);
-    advance(l.srv);
+    // a lane whose completion query failed is never idle: its memory may
+    // still be in use on the device
+    if (advance(l.srv) != SFFT_OK) return false;
     return l.srv->flushed == l.srv->next_seq && l.srv->watermark == l.srv->next_seq;
 }
 
@@ -359,6 +383,14 @@ int sfft_server_create(const sfft_config *cfg, int32_t depth, int32_t batch, sff
     return rc;
 }
 
+int sfft_server_debug_fail_queries(sfft_server_t server, int32_t enable) {
+    if (!server) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    v->fail_queries = enable != 0;
+    return SFFT_OK;
+}
+
 int sfft_server_destroy(sfft_server_t server) {
     if (!server) return SFFT_OK;
     Server *v = (Server *)server;
@@ -397,7 +429,8 @@ int sfft_poll(sfft_server_t server, const sfft_ticket *ticket) {
         const int rc = flush(v);
         if (rc != SFFT_OK) return rc;
     }
-    advance(v);
+    const int rc = advance(v);
+    if (rc != SFFT_OK) return rc;
     return ticket->seq < v->watermark ? SFFT_OK : SFFT_ERR_BUSY;
 }
 
@@ -413,7 +446,8 @@ int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_u
                 const int rc = flush(v);
                 if (rc != SFFT_OK) return rc;
             }
-            advance(v);
+            const int rc = advance(v);
+            if (rc != SFFT_OK) return rc;
             if (ticket->seq < v->watermark) return SFFT_OK;
         }
         if (timeout_us >= 0) {

@@ -181,8 +181,10 @@ def _sky(kind, n0, n1):
     return 100.0 + 20.0 * xt * xt + 10.0 * yt * yt + 5.0 * xt * yt
 
 
-def make_pair(spec: PairSpec, seed: int = 0):
-    """Return (R, S) as C-contiguous arrays of spec.dtype."""
+def make_pair(spec: PairSpec, seed: int = 0, return_transients: bool = False):
+    """Return (R, S) as C-contiguous arrays of spec.dtype; with
+    return_transients also the (x, y) positions of the transients injected
+    into S (empty arrays when the spec has none)."""
     rng = np.random.default_rng(seed)
     n0, n1 = spec.n0, spec.n1
     xs = rng.uniform(0, n0, spec.n_src)
@@ -201,6 +203,7 @@ def make_pair(spec: PairSpec, seed: int = 0):
     S = _sky(spec.sky_sci, n0, n1)
     _render(R, xs, ys, flux, fr, el, spec.pa_deg, half)
     _render(S, xs, ys, flux * scale, fs, el, spec.pa_deg, half)
+    tx = ty = np.zeros(0)
     if spec.n_transients:
         tx = rng.uniform(0, n0, spec.n_transients)
         ty = rng.uniform(0, n1, spec.n_transients)
@@ -215,7 +218,23 @@ def make_pair(spec: PairSpec, seed: int = 0):
         R = R + rng.normal(0, spec.sigma, R.shape)
         S = S + rng.normal(0, spec.sigma, S.shape)
     dt = np.dtype(spec.dtype)
-    return np.ascontiguousarray(R, dtype=dt), np.ascontiguousarray(S, dtype=dt)
+    R, S = np.ascontiguousarray(R, dtype=dt), np.ascontiguousarray(S, dtype=dt)
+    if return_transients:
+        return R, S, (tx, ty)
+    return R, S
+
+
+def transient_mask(shape, positions, half: int):
+    """uint8 mask of an image of `shape`: 0 on the square of half-width
+    `half` around each (x, y) position (clipped at the edges), 1 elsewhere.
+    The masked squares are where a caller hides known variable sources from
+    the fit (the build sees zeros there; the subtraction is unmasked)."""
+    n0, n1 = shape
+    mask = np.ones((n0, n1), dtype=np.uint8)
+    for x, y in zip(*positions):
+        xi, yi = int(np.floor(x)), int(np.floor(y))
+        mask[max(0, xi - half):min(n0, xi + half + 1), max(0, yi - half):min(n1, yi + half + 1)] = 0
+    return mask
 
 
 def random_field(n0, n1, seed, n_src=None, sky=100.0, sigma=5.0, fwhm=2.0):

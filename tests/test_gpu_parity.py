@@ -7,6 +7,19 @@ Tolerances (stated per result):
     refinement): rel. error of M and rhs <= 1e-5; the solver is checked
     against an FP64 solve of the same GPU-built system (<= 1e-8); the
     difference image RMS deviation from the oracle's is <= 1e-3 sigma.
+
+Beyond the norms, every small case checks each block of Eq. 18 on its own
+(the kernel-kernel block A of Eq. B5, the kernel-background block B of
+Eq. B7/B9, the background block C of Eq. B11, the rhs parts D of Eq. B13 and
+E of Eq. B15), since C, B and E are orders of magnitude smaller than A and a
+wrong one could hide under a norm of the whole matrix:
+  * per block, rel. Frobenius error <= the tolerance of the whole matrix;
+  * per entry, |dM_ij| <= tol_e * sqrt(M_ii M_jj) (Cauchy-Schwarz bounds
+    |M_ij| by that product, so this is a relative error on the scale the
+    entry can reach), and |drhs_i| <= tol_e * sqrt(M_ii) * ||S_masked||;
+    tol_e = 1e-4 mixed, 1e-9 FP64;
+  * D: the largest pixel deviation <= 1e-2 sigma (mixed) or 1e-5 sigma
+    (FP64), so that one wrong pixel cannot hide in the RMS.
 """
 import numpy as np
 import pytest
@@ -88,6 +101,42 @@ SPLINE = [
 ]
 
 
+def kernel_unknowns(c):
+    """Boolean mask over the unknowns: True for kernel coefficients (the
+    oracle's own decoding of the unknown order), False for background ones."""
+    return np.array([oracle.decode_unknown(c, u)[0] for u in range(oracle.num_unknowns(c))])
+
+
+def block_errors(Mg, rg, Mo, ro, c, S, mask):
+    """Relative Frobenius error of each block of Eq. 18 and the largest
+    per-entry errors on the Cauchy-Schwarz scale (module docstring)."""
+    k = kernel_unknowns(c)
+    b = ~k
+    out = {}
+    for name, (ri, ci) in {"A": (k, k), "B": (k, b), "C": (b, b)}.items():
+        if ri.any() and ci.any():
+            out[name] = rel(Mg[np.ix_(ri, ci)], Mo[np.ix_(ri, ci)])
+    out["rhs_D"] = rel(rg[k], ro[k])
+    out["rhs_E"] = rel(rg[b], ro[b])
+    d = np.sqrt(np.abs(np.diag(Mo)))
+    out["entry_M"] = float(np.max(np.abs(Mg - Mo) / np.maximum(np.outer(d, d), 1e-300)))
+    Sm = S if mask is None else S * (mask != 0)
+    out["entry_rhs"] = float(np.max(np.abs(rg - ro) / np.maximum(d * np.linalg.norm(Sm), 1e-300)))
+    return out
+
+
+def check_system(Mg, rg, Mo, ro, c, S, mask, tol, tol_e):
+    assert rel(Mg, Mo) <= tol
+    assert rel(rg, ro) <= tol
+    e = block_errors(Mg, rg, Mo, ro, c, S, mask)
+    print("block errors", {k: f"{v:.1e}" for k, v in e.items()})
+    for name in ("A", "B", "C", "rhs_D", "rhs_E"):
+        if name in e:
+            assert e[name] <= tol, (name, e)
+    assert e["entry_M"] <= tol_e, e
+    assert e["entry_rhs"] <= tol_e, e
+
+
 def check_against_oracle(R, S, c, precision, mask, g):
     """The tolerances of the module docstring, oracle config c vs GPU result g."""
     Mo, ro = oracle.build_system(R, S, c, mask=mask)
@@ -95,20 +144,20 @@ def check_against_oracle(R, S, c, precision, mask, g):
     Do = oracle.subtract(R, S, xo, c)
     assert g["info"]["status"] == 0, g["info"]
     if precision == "fp64":
-        assert rel(g["M"], Mo) <= 1e-10
-        assert rel(g["rhs"], ro) <= 1e-10
+        check_system(g["M"], g["rhs"], Mo, ro, c, S, mask, 1e-10, 1e-9)
         assert rel(g["x"], xo) <= 1e-8
         assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
+        assert np.max(np.abs(g["D"] - Do)) <= 1e-5 * SIGMA
     else:
         # inputs rounded to float32 on both sides for the system check
         R32, S32 = R.astype(np.float32).astype(np.float64), S.astype(np.float32).astype(np.float64)
         Mo32, ro32 = oracle.build_system(R32, S32, c, mask=mask)
-        assert rel(g["M"], Mo32) <= 1e-5
-        assert rel(g["rhs"], ro32) <= 1e-5
+        check_system(g["M"], g["rhs"], Mo32, ro32, c, S32, mask, 1e-5, 1e-4)
         xs = np.linalg.solve(g["M"], g["rhs"])
         assert rel(g["x"], xs) <= 1e-8
         Do32 = oracle.subtract(R32, S32, oracle.cholesky_solve(Mo32, ro32), c)
         assert np.sqrt(np.mean((g["D"] - Do32) ** 2)) <= 1e-3 * SIGMA
+        assert np.max(np.abs(g["D"] - Do32)) <= 1e-2 * SIGMA
 
 
 @pytest.mark.parametrize("case", SPLINE)
@@ -136,27 +185,9 @@ def test_small_cases_against_oracle(case, precision):
     if masked:
         mask = (np.random.default_rng(n0).random((n0, n1)) > 0.15).astype(np.uint8)
     c = oracle.OracleConfig(n0, n1, w0, w1, dk, db, bool(cpr))
-    Mo, ro = oracle.build_system(R, S, c, mask=mask)
-    xo = oracle.cholesky_solve(Mo, ro)
-    Do = oracle.subtract(R, S, xo, c)
     dtype = "float64" if precision == "fp64" else "float32"
     g = gpu_run(R, S, w0, w1, dk, db, cpr, precision, dtype, mask)
-    assert g["info"]["status"] == 0, g["info"]
-    if precision == "fp64":
-        assert rel(g["M"], Mo) <= 1e-10
-        assert rel(g["rhs"], ro) <= 1e-10
-        assert rel(g["x"], xo) <= 1e-8
-        assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
-    else:
-        # inputs rounded to float32 on both sides for the system check
-        R32, S32 = R.astype(np.float32).astype(np.float64), S.astype(np.float32).astype(np.float64)
-        Mo32, ro32 = oracle.build_system(R32, S32, c, mask=mask)
-        assert rel(g["M"], Mo32) <= 1e-5
-        assert rel(g["rhs"], ro32) <= 1e-5
-        xs = np.linalg.solve(g["M"], g["rhs"])
-        assert rel(g["x"], xs) <= 1e-8
-        Do32 = oracle.subtract(R32, S32, oracle.cholesky_solve(Mo32, ro32), c)
-        assert np.sqrt(np.mean((g["D"] - Do32) ** 2)) <= 1e-3 * SIGMA
+    check_against_oracle(R, S, c, precision, mask, g)
     g["plan"].close()
 
 
@@ -172,9 +203,10 @@ def test_pair256_fp64_full():
     g = gpu_run(R, S, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, "fp64", "float64")
     assert g["M"].shape == (82, 82)
     assert g["info"]["status"] == 0
-    assert rel(g["M"], Mo) <= 1e-10 and rel(g["rhs"], ro) <= 1e-10
+    check_system(g["M"], g["rhs"], Mo, ro, c, S, None, 1e-10, 1e-9)
     assert rel(g["x"], xo) <= 1e-8
     assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-6 * SIGMA
+    assert np.max(np.abs(g["D"] - Do)) <= 1e-5 * SIGMA
     g["plan"].close()
 
 
@@ -191,10 +223,10 @@ def test_pair1024_mixed_full():
     g = gpu_run(R, S, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, "mixed", "float32")
     assert g["M"].shape == (510, 510)
     assert g["info"]["status"] == 0, g["info"]
-    assert rel(g["M"], Mo) <= 1e-5
-    assert rel(g["rhs"], ro) <= 1e-5
+    check_system(g["M"], g["rhs"], Mo, ro, c, S64, None, 1e-5, 1e-4)
     assert rel(g["x"], np.linalg.solve(g["M"], g["rhs"])) <= 1e-8
     assert np.sqrt(np.mean((g["D"] - Do) ** 2)) <= 1e-3 * SIGMA
+    assert np.max(np.abs(g["D"] - Do)) <= 1e-2 * SIGMA
     g["plan"].close()
 
 

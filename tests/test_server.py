@@ -162,3 +162,47 @@ def test_batch_with_a_singular_system(lib):
             assert np.array_equal(D.cpu().numpy(), expected[k][0])
     srv.close()
     plan.close()
+
+
+@pytest.mark.gpu
+def test_failed_completion_query_ends_wait_with_error(lib):
+    """A completion query that reports a CUDA error ends sfft_wait with
+    SFFT_ERR_CUDA instead of spinning (timeout -1 included), and the error
+    is sticky for poll, wait and submit.  The failure is made on the host by
+    the server's testing hook: no fault on the GPU, and the enqueued work
+    runs to completion (destroy waits for it)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import threading
+    from paper_2109_09334_gb300 import SfftServer, binding as B
+    n0 = n1 = 64
+    R, S, _ = make_pairs(n0, n1, 1, seed=41)[0]
+    srv = SfftServer(n0, n1, 2, 2, 1, 1, 1, dtype="float32", precision="mixed", depth=2, batch=2)
+    Rt = torch.from_numpy(R.astype(np.float32)).cuda()
+    St = torch.from_numpy(S.astype(np.float32)).cuda()
+    t0 = srv.submit(Rt, St)[0]
+    t1 = srv.submit(Rt, St)[0]
+    assert srv.wait(t0)  # the server works before the hook is set
+    B.sfft_server_debug_fail_queries(srv.handle, True)
+    rc = {}
+
+    def waiter():
+        rc["wait"] = lib.sfft_wait(srv.handle, ctypes.byref(t1), -1)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    th.join(timeout=30)
+    assert not th.is_alive(), "sfft_wait kept spinning after a failed completion query"
+    assert rc["wait"] == B.SFFT_ERR_CUDA
+    assert lib.sfft_poll(srv.handle, ctypes.byref(t1)) == B.SFFT_ERR_CUDA
+    assert lib.sfft_wait(srv.handle, ctypes.byref(t1), 1000) == B.SFFT_ERR_CUDA
+    req = B.make_request(Rt, St, torch.empty_like(Rt))
+    t = B.sfft_ticket()
+    assert lib.sfft_submit(srv.handle, ctypes.byref(req), ctypes.byref(t)) == B.SFFT_ERR_CUDA
+    with pytest.raises(B.SfftError):
+        srv.wait(t1)
+    # the hook only fakes the queries: the device finished the work
+    B.sfft_server_debug_fail_queries(srv.handle, False)
+    torch.cuda.synchronize()
+    srv.close()
+    assert lib.sfft_server_debug_fail_queries(None, 1) == B.SFFT_ERR_INVALID

@@ -1,11 +1,18 @@
 """sfft_solve_static (the solve on the library's static device workspace)
-against sfft_solve on a plan.
+against sfft_solve on a plan, and against the oracle's Cholesky solve.
 
 The file name sorts last so that it runs after every other test has used the
-library, and it needs nothing from them: it also passes alone.  Tolerance:
-both entry points run the same kernels on the same system, so the
-coefficients agree to within 1e-12 of max |theta| (they are expected to be
-bitwise equal; the bound leaves room for nothing but rounding).
+library, and it needs nothing from them: it also passes alone.  Tolerances:
+both entry points run the same kernel with the same (default) grid on the
+same system, and the solve's reductions run in a fixed order, so the
+coefficients and the iteration counts are bitwise equal.  Against the
+oracle's FP64 Cholesky solve of the same GPU-built system: the plain FP64
+path within 1e-8 relative; the mixed path stops refining at
+||rhs - M x|| <= 1e-12 ||rhs||, which bounds its distance from the exact
+solution by cond(M) * 1e-12 (relative), so it must agree with the oracle
+within max(1e-8, cond(M) * 1e-12).  These systems sit near the size limit on
+small images, so cond(M) reaches 1e8 (measured 4.6e7 and 1.5e8): there the
+bound, not 1e-8, is what refinement to 1e-12 can promise.
 """
 import ctypes
 import re
@@ -90,12 +97,16 @@ def test_static_solve_matches_plan_solve(lib, case, precision):
     xr = x_ref.cpu().numpy()
     ir = info_from_bytes(info_ref.cpu().numpy())
     assert ir["status"] == B.SFFT_OK
-    scale = float(np.abs(xr).max())
+    import oracle
+    Mh = M.cpu().numpy()
+    xo = oracle.cholesky_solve(Mh, rhs.cpu().numpy())
+    tol = 1e-8 if precision == "fp64" else max(1e-8, float(np.linalg.cond(Mh)) * 1e-12)
     for x, info in zip(xs, infos):
         xv = x.cpu().numpy()
         iv = info_from_bytes(info.cpu().numpy())
         assert iv["status"] == B.SFFT_OK, iv
         assert iv["iters"] == ir["iters"]
         assert np.all(np.isfinite(xv))
-        assert float(np.abs(xv - xr).max()) <= 1e-12 * scale
+        np.testing.assert_array_equal(xv, xr)
+        assert np.linalg.norm(xv - xo) <= tol * np.linalg.norm(xo)
     plan.close()
