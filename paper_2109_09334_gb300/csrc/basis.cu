@@ -251,7 +251,11 @@ int basis_build(Plan *p, cudaStream_t s) {
     if (cudaMalloc((void **)&p->unk, (size_t)p->n * sizeof(int4)) != cudaSuccess) return SFFT_ERR_OOM;
     p->ws_bytes += (size_t)p->n * sizeof(int4);
 
-    // ---- function tables (B-spline: compute type, x-functions then y) -------
+    // ---- function tables in the compute type, x-functions then y: the
+    // B-spline functions, or the monomials xt^i, yt^j of the polynomial
+    // basis (evaluated in FP64 and rounded once, so the row, column and
+    // subtraction passes read a weight instead of dividing and raising a
+    // coordinate to a power per pixel) -----------------------------------------
     std::vector<double> tfx, tfy, tbx, tby;
     axis_table(poly, c.kdeg, c.kint, nfx, poly ? -1 : (cpr ? K : -1), p->n0, tfx);
     axis_table(poly, c.kdeg, c.kint, nfy, poly ? -1 : (cpr ? K : -1), p->n1, tfy);
@@ -264,7 +268,7 @@ int basis_build(Plan *p, cudaStream_t s) {
     all.insert(all.end(), tbx.begin(), tbx.end());
     all.insert(all.end(), tfy.begin(), tfy.end());
     all.insert(all.end(), tby.begin(), tby.end());
-    if (!poly) {
+    {
         const size_t esz = p->fp64 ? sizeof(double) : sizeof(float);
         if (cudaMalloc(&p->ftab, nft * esz) != cudaSuccess) return SFFT_ERR_OOM;
         p->ws_bytes += nft * esz;

@@ -108,11 +108,10 @@ __device__ __forceinline__ void fft_pass(cpx<T> *buf, int n, int ns, int sgn, co
 }
 
 // Whole transform of length n (power of two, 16 <= n <= 4096) on the padded
-// buffer; the block must call it with the same n in every group.  With
-// perm_lnb >= 0 the last pass stores in the residue-class layout (out_pos).
+// buffer, with the length known only at run time; see group_fft.
 template <typename T>
-__device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize, int perm_lnb = -1,
-                          int perm_na = 0) {
+__device__ void group_fft_rt(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize, int perm_lnb = -1,
+                             int perm_na = 0) {
     const int e = 31 - __clz(n);
     int ns = 1;
     const bool only_first = (e >> 2) == 0;  // no radix-16 pass follows
@@ -137,6 +136,126 @@ __device__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gt
         fft_pass<T, 16>(buf, n, ns, sgn, twp + off, gtid, gsize, last ? perm_lnb : -1, perm_na);
         if (ns > 1) off += 15 * ns;
     }
+}
+
+// ---- the same transform with the length, the sign and the pass strides known
+// at compile time (lengths 256..4096).  The arithmetic and its order are those
+// of fft_pass / group_fft_rt; what changes is the addressing: with N/R and
+// NS constants, every element a thread loads or stores sits at a constant
+// offset from one per-thread base, and the twiddles of a pass at constant
+// offsets from base + k, so no index is recomputed per element.
+//   load  pad16(j + r NB) = pad16(j) + r (NB + NB/16)          (16 | NB)
+//   store pad16(o + r NS) = pad16(o) + r NS + ((r NS) >> 4)    (o = 16 NS q + k, k < NS)
+//   residue-class store of the last pass (NA = 64, N = NA NBK, NS = N/16 = 4 NBK):
+//         out_pos(k + r NS) = out_pos(k) + 4 r
+template <typename T, int N, int R, int NS, int SGN, bool PERM>
+__device__ __forceinline__ void fft_pass_ct(cpx<T> *buf, const cpx<T> *twp, int gtid) {
+    constexpr int NB = N / R;
+    constexpr int G = N / 16;
+    constexpr int PER = 16 / R;  // butterflies per thread
+    static_assert(NB % 16 == 0, "compile-time passes need 16 | N/R");
+    constexpr int LDSTEP = NB + NB / 16;
+    cpx<T> v[PER][R];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = gtid + u * G;
+        const cpx<T> *src = buf + pad16(j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u][r] = src[r * LDSTEP];
+        if constexpr (NS > 1) {
+            const int k = j & (NS - 1);
+            const cpx<T> *tk = twp + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const cpx<T> w = tk[(r - 1) * NS];
+                v[u][r] = cmul(v[u][r], SGN < 0 ? w : mk(w.re, -w.im));
+            }
+        }
+        if constexpr (R == 16) dft16(v[u], SGN);
+        else if constexpr (R == 8) dft8(v[u], SGN);
+        else if constexpr (R == 4) dft4(v[u][0], v[u][1], v[u][2], v[u][3], SGN);
+        else dft2(v[u][0], v[u][1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = gtid + u * G;
+        const int k = j & (NS - 1);
+        const int o = (j - k) * R + k;
+        if constexpr (PERM) {
+            // last pass (NS * 16 == N): o = k; bin l = k + r NS goes to
+            // (l mod NBK) * (NA + 1) + l / NBK with NBK = N / 64
+            static_assert(R == 16 && NS * 16 == N && N >= 64, "residue-class store on the last radix-16 pass");
+            constexpr int NBK = N / 64;
+            cpx<T> *dst = buf + (k & (NBK - 1)) * 65 + k / NBK;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[4 * r] = v[u][(R == 16) ? slot16(r) : r];
+        } else {
+            cpx<T> *dst = buf + pad16(o);
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r * NS + ((r * NS) >> 4)] = v[u][(R == 16) ? slot16(r) : r];
+        }
+    }
+    __syncthreads();
+}
+
+// Radix-16 passes from stride NS on (twiddle table offset OFF), the last one
+// with the residue-class store if PERM.
+template <typename T, int N, int NS, int OFF, int SGN, bool PERM>
+__device__ __forceinline__ void fft_passes16_ct(cpx<T> *buf, const cpx<T> *twp, int gtid) {
+    if constexpr (NS < N) {
+        constexpr bool last = NS * 16 >= N;
+        fft_pass_ct<T, N, 16, NS, SGN, PERM && last>(buf, twp + OFF, gtid);
+        fft_passes16_ct<T, N, NS * 16, (NS > 1 ? OFF + 15 * NS : OFF), SGN, PERM>(buf, twp, gtid);
+    }
+}
+
+template <typename T, int LOGN, int SGN, bool PERM>
+__device__ __forceinline__ void group_fft_ct(cpx<T> *buf, const cpx<T> *twp, int gtid) {
+    constexpr int N = 1 << LOGN;
+    constexpr int E = LOGN & 3;
+    static_assert(LOGN >= 8 && LOGN <= 12, "compile-time lengths 256..4096");
+    if constexpr (E == 1) fft_pass_ct<T, N, 2, 1, SGN, false>(buf, twp, gtid);
+    if constexpr (E == 2) fft_pass_ct<T, N, 4, 1, SGN, false>(buf, twp, gtid);
+    if constexpr (E == 3) fft_pass_ct<T, N, 8, 1, SGN, false>(buf, twp, gtid);
+    fft_passes16_ct<T, N, (1 << E), 0, SGN, PERM>(buf, twp, gtid);
+}
+
+template <typename T, int SGN>
+__device__ __forceinline__ bool group_fft_ct_dispatch(cpx<T> *buf, int n, const cpx<T> *twp, int gtid, bool perm) {
+    switch (n) {
+        case 4096:
+            if (perm) group_fft_ct<T, 12, SGN, true>(buf, twp, gtid);
+            else group_fft_ct<T, 12, SGN, false>(buf, twp, gtid);
+            return true;
+        case 2048:
+            if (perm) group_fft_ct<T, 11, SGN, true>(buf, twp, gtid);
+            else group_fft_ct<T, 11, SGN, false>(buf, twp, gtid);
+            return true;
+        case 1024:
+            if (perm) group_fft_ct<T, 10, SGN, true>(buf, twp, gtid);
+            else group_fft_ct<T, 10, SGN, false>(buf, twp, gtid);
+            return true;
+        default: return false;
+    }
+}
+
+// Whole transform of length n (power of two, 16 <= n <= 4096) on the padded
+// buffer; the block must call it with the same n in every group, and gsize
+// must be n / 16.  With perm_lnb >= 0 the last pass stores in the
+// residue-class layout (out_pos).  Lengths 1024, 2048 and 4096 (and the
+// residue-class store with NA = 64) take the compile-time passes; the others
+// the run-time ones.  Both give the same results.
+template <typename T>
+__device__ __forceinline__ void group_fft(cpx<T> *buf, int n, int sgn, const cpx<T> *twp, int gtid, int gsize,
+                                          int perm_lnb = -1, int perm_na = 0) {
+    const bool perm = perm_lnb >= 0;
+    if (!perm || perm_na == 64) {
+        if (sgn < 0 ? group_fft_ct_dispatch<T, -1>(buf, n, twp, gtid, perm)
+                    : group_fft_ct_dispatch<T, 1>(buf, n, twp, gtid, perm))
+            return;
+    }
+    group_fft_rt(buf, n, sgn, twp, gtid, gsize, perm_lnb, perm_na);
 }
 
 // Strides ns of the radix-16 passes with twiddles, in execution order, for a

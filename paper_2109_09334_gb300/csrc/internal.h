@@ -64,8 +64,9 @@ struct BasisView {
     }
 };
 
-// Tabulated functions of the B-spline basis in the compute type (all null
-// for the polynomial basis): fx [nfx][n0], fy [nfy][n1], bx [nbx][n0], by [nby][n1].
+// Tabulated basis functions in the compute type (B-spline functions, or the
+// monomials xt^i, yt^j of the polynomial basis; null only before the plan's
+// tables exist): fx [nfx][n0], fy [nfy][n1], bx [nbx][n0], by [nby][n1].
 template <typename T>
 struct FTab {
     const T *fx, *fy, *bx, *by;
@@ -173,8 +174,8 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out);  // cfg alread
 void plan_free(Plan *p);
 int status_of(cudaError_t e);
 
-// the function tables of a B-spline plan in the compute type (all null for
-// the polynomial basis); ftab holds fx | bx | fy | by
+// the function tables of a plan in the compute type (B-spline functions or
+// monomials of the normalised coordinates); ftab holds fx | bx | fy | by
 template <typename T>
 inline FTab<T> ftab_of(const Plan *p) {
     FTab<T> f{nullptr, nullptr, nullptr, nullptr};
