@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
                     help="sectors64: solve the sectors' systems eight per launch, or one per pair")
     ap.add_argument("--no-masked", action="store_true", help="skip the transient-masked pair measurement")
+    ap.add_argument("--no-sectors", action="store_true", help="skip the 64-sector batch measurement")
+    ap.add_argument("--no-stream", action="store_true", help="skip the loaded serving-stream measurement")
     ap.add_argument("--oracle-sample", type=int, default=0,
                     help=argparse.SUPPRESS)  # child process: time the oracle on a crop, print JSON
     return ap.parse_args()
@@ -678,6 +680,11 @@ def run_ours(args):
                             "api": "sfft_run_pair with a mask: build on the masked pair (50 transients, "
                                    "squares of half-width 14 px), subtraction on the unmasked pair"}
 
+    if not args.no_sectors:
+        result["sectors64"] = measure_sectors(args, dev, world, rank)
+    if not args.no_stream:
+        result["stream"] = measure_stream_load(args, dev, rank)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle as it stands, on the host cores: all cores on the central
         # 1024^2 crop, one core on the central 384^2 crop (child processes,
@@ -746,20 +753,17 @@ def crop_field(n_field, fit, seed):
     return synth.make_pair(spec, seed=seed)
 
 
-def run_sectors(args):
+def measure_sectors(args, dev, world, rank):
     """Batched uneven sectors: 64 square pairs, n uniform in [512, 2048], fit
-    drawn per sector, processed as one batch; the batch is captured once
-    into a CUDA graph and replayed as one launch."""
+    drawn per sector, processed as one batch captured by the library into a
+    CUDA graph (sfft_batch_create, solve grouping autotuned) and replayed as
+    one launch (sfft_batch_launch).  Checks the replay against the pairs run
+    one at a time (bit for bit) and times both."""
     import numpy as np
     import torch
     import synth
-    from paper_2109_09334_gb300 import SfftPlan, binding, info_from_bytes
+    from paper_2109_09334_gb300 import SfftBatch, SfftPlan, binding, info_from_bytes
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        torch.distributed.init_process_group("nccl")
-    dev = torch.device("cuda", local)
     specs = synth.draw_sectors(64, seed=4 + rank)
     R, S = crop_field(4096, synth.FitParams(8, 8, 2, 2, True), seed=40 + rank)
     rng = np.random.default_rng(7 + rank)
@@ -771,88 +775,76 @@ def run_sectors(args):
         plan = SfftPlan(n, n, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype="float32", precision=args.precision)
         Rt = torch.from_numpy(np.ascontiguousarray(R[x0:x0 + n, y0:y0 + n])).to(dev)
         St = torch.from_numpy(np.ascontiguousarray(S[x0:x0 + n, y0:y0 + n])).to(dev)
-        D = torch.empty_like(Rt)
-        x = torch.empty(plan.n, dtype=torch.float64, device=dev)
-        info = torch.zeros(24, dtype=torch.uint8, device=dev)
-        work.append((plan, Rt, St, D, x, info, n, f))
+        work.append((plan, Rt, St, n, f))
     stream = torch.cuda.Stream(dev)
-
-    def run_seq():
-        for plan, Rt, St, D, x, info, n, f in work:
-            binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, x, info, D, stream)
-
-    def run_batched():  # systems solved eight per launch (sfft_run_pairs)
-        binding.sfft_run_pairs([w[0].handle for w in work], [w[1] for w in work], [w[2] for w in work], None,
-                               [w[4] for w in work], [w[5] for w in work], [w[3] for w in work], stream)
-
-    run_all = run_seq if args.sector_solve == "single" else run_batched
-
-    for _ in range(max(args.warmup, 1)):
-        run_all()
     torch.cuda.synchronize()
-    bad = [k for k, w in enumerate(work) if info_from_bytes(w[5].cpu().numpy())["status"] != 0]
-    if bad:
-        raise RuntimeError(f"solve failed on sectors {bad}")
-    launches0 = sum(binding.sfft_plan_launch_count(w[0].handle) for w in work)
-    graph, graph_note = None, "captured"
-    try:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=stream):
-            run_all()
-    except Exception as exc:  # capture refused: time the eager launches only
-        graph, graph_note = None, f"unavailable: {type(exc).__name__}: {exc}"[:200]
-    per_batch = sum(binding.sfft_plan_launch_count(w[0].handle) for w in work) - launches0
-    torch.cuda.synchronize()
+    group = {"batched": 0, "single": 1}[args.sector_solve]
+    batch = SfftBatch([w[0] for w in work], [w[1] for w in work], [w[2] for w in work], solve_group=group)
+    binfo = batch.info_dict
     K = max(1, min(args.steps, 20))
 
     def timed(fn):
-        # graph replays launch on the current stream: make it `stream`
-        with torch.cuda.stream(stream):
-            for _ in range(2):
-                fn()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(K):
-                fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
         return e0.elapsed_time(e1) / K
 
-    eager_ms = timed(run_all)
-    ref = [w[3].clone() for w in work]  # the eager batch's difference images
-    if run_all is run_batched:  # batched solves give the single-pair results bit for bit
-        for w in work:
-            w[3].zero_()
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            run_seq()
-        torch.cuda.synchronize()
-        if not all(torch.equal(a, w[3]) for a, w in zip(ref, work)):
-            raise RuntimeError("batched solves differ from the single-pair path")
-    graph_ms = None
-    if graph is not None:
-        for w in work:
-            w[3].zero_()
-        torch.cuda.synchronize()
-        graph_ms = timed(graph.replay)
-        if not all(torch.equal(a, w[3]) for a, w in zip(ref, work)):
-            raise RuntimeError("graph replay differs from the eager batch")
-    ms = graph_ms if graph_ms is not None else eager_ms
-    ms, eager_ms = max_over_ranks([ms, eager_ms], world, dev)
-    npix = sum(w[6] * w[6] for w in work)
-    out = {"metric": "pairs/s over a batch of 64 uneven sectors (512..2048 px, fit drawn per sector)",
-           "value": world * len(work) * 1e3 / ms, "unit": "pairs/s", "n_gpus": world, "steps": K,
-           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
-           "data": "synthetic sectors cut from one seeded field (one source per 500 px^2)",
-           "config": {"workload": "sectors64", "sizes": [w[6] for w in work],
-                      "fits": [[w[7].w0, w[7].dk, w[7].db] for w in work], "precision": args.precision,
-                      "solve": args.sector_solve},
-           "graph": graph_note, "eager": {"value": world * len(work) * 1e3 / eager_ms, "ms_per_batch": eager_ms},
-           "mpix_per_s": world * npix / (ms * 1e3), "gpu_launches": int(per_batch * K)}
+    graph_ms = timed(lambda: batch.launch(stream))
+    got = [d.clone() for d in batch.D]
+    bad = [k for k, i in enumerate(batch.info) if info_from_bytes(i.cpu().numpy())["status"] != 0]
+    if bad:
+        raise RuntimeError(f"solve failed on sectors {bad}")
+    # one pair at a time (sfft_run_pair), the same inputs: the reference for
+    # the batch's results and the eager comparison
+    Dk = [torch.empty_like(w[1]) for w in work]
+    xk = [torch.empty(w[0].n, dtype=torch.float64, device=dev) for w in work]
+    ik = [torch.zeros(24, dtype=torch.uint8, device=dev) for w in work]
+
+    def run_seq():
+        for k, (plan, Rt, St, n, f) in enumerate(work):
+            binding.sfft_run_pair(plan.handle, Rt, St, None, None, None, xk[k], ik[k], Dk[k], stream)
+
+    seq_ms = timed(run_seq)
+    if not all(torch.equal(a, b) for a, b in zip(got, Dk)):
+        raise RuntimeError("graph-captured batch differs from the pairs run one at a time")
+    batch.close()
+    ms, seq_ms = max_over_ranks([graph_ms, seq_ms], world, dev)
+    npix = sum(w[3] * w[3] for w in work)
+    out = {"value": world * len(work) * 1e3 / ms, "unit": "pairs/s", "ms_per_batch": ms, "steps": K,
+           "mpix_per_s": world * npix / (ms * 1e3), "gpu_launches_per_batch": binfo["launches"],
+           "api": "sfft_batch_create (library-captured CUDA graph) + sfft_batch_launch",
+           "solve_group": binfo["solve_group"], "solve_group_tuning_ms": binfo["tune_ms"],
+           "one_at_a_time": {"value": world * len(work) * 1e3 / seq_ms, "ms_per_batch": seq_ms,
+                             "api": "sfft_run_pair per sector"},
+           "sizes": [w[3] for w in work], "fits": [[w[4].w0, w[4].dk, w[4].db] for w in work],
+           "check": "every difference image bitwise equal to sfft_run_pair's"}
     for w in work:
         w[0].close()
+    return out
+
+
+def run_sectors(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    r = measure_sectors(args, dev, world, rank)
+    out = {"metric": "pairs/s over a batch of 64 uneven sectors (512..2048 px, fit drawn per sector)",
+           "value": r["value"], "unit": "pairs/s", "n_gpus": world, "steps": r["steps"],
+           "warmup": args.warmup, "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+           "data": "synthetic sectors cut from one seeded field (one source per 500 px^2)",
+           "config": {"workload": "sectors64", "sizes": r["sizes"], "fits": r["fits"], "precision": args.precision,
+                      "solve": args.sector_solve},
+           "gpu_launches": int(r["gpu_launches_per_batch"] * r["steps"]), "sectors64": r}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -927,6 +919,99 @@ def run_stream(args):
            "failed": bad, "pool_end": {"bytes": used, "lanes": lanes}}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def measure_stream_load(args, dev, rank, rates=(100.0, 300.0, 600.0), count=240, nconf=8):
+    """The serving stream under load: host requests (pinned) drawn from
+    `nconf` sector configurations (square n uniform in [1024, 4096], w in
+    4..8, D_K and D_B in 0..2, all drawn once, as a survey's sectors come in a
+    few shapes), cut from one seeded 4096^2 field, arriving as a Poisson
+    process at each rate in `rates`, through the pool (one lane per
+    configuration, depth 4, batch 2, eager flushing, 180 GB budget).  The lanes are warmed
+    (plans built) before the timed streams.  A waiter thread waits for the
+    tickets in submission order; a request's latency is arrival to the end of
+    its wait.  Requests of one configuration that arrive together share a
+    solve launch; the lanes' builds, solves and copies overlap on the GPU."""
+    import threading
+    import numpy as np
+    import torch
+    import synth
+    from paper_2109_09334_gb300 import SfftPool, info_from_bytes
+
+    R, S = crop_field(4096, synth.FitParams(8, 8, 2, 2, True), seed=60 + rank)
+    rng = np.random.default_rng(11 + rank)
+    confs = []
+    for _ in range(nconf):
+        n = int(rng.integers(1024, 4097))
+        w, dk, db = int(rng.integers(4, 9)), int(rng.integers(0, 3)), int(rng.integers(0, 3))
+        x0, y0 = (int(v) for v in rng.integers(0, 4096 - n + 1, size=2))
+        Rh = torch.from_numpy(np.ascontiguousarray(R[x0:x0 + n, y0:y0 + n])).pin_memory()
+        Sh = torch.from_numpy(np.ascontiguousarray(S[x0:x0 + n, y0:y0 + n])).pin_memory()
+        confs.append((Rh, Sh, (w, w, dk, db, True), n))
+    pool = SfftPool(180 << 30, depth=4, batch=2, eager=True)
+    # outputs: a ring of pinned buffers per configuration, reused only after
+    # the request that used them has completed
+    ring = 12
+    outs = [[(torch.empty((n, n), dtype=torch.float32).pin_memory(),) for _ in range(ring)] for *_, n in confs]
+
+    def submit(ci, slot):
+        Rh, Sh, fit, n = confs[ci]
+        while True:
+            got = pool.submit(Rh, Sh, *fit, precision=args.precision, diff=outs[ci][slot][0])
+            if got is not None:
+                return got
+            time.sleep(0.0005)  # not admitted yet
+
+    for ci in range(nconf):  # warm the lanes
+        t = submit(ci, 0)
+        pool.wait(t[0])
+    legs = []
+    for rate in rates:
+        pick = rng.integers(0, nconf, size=count)
+        gaps = rng.exponential(1.0 / rate, size=count)
+        arrive = np.cumsum(gaps) - gaps[0]
+        done_at = [None] * count
+        tickets = [None] * count
+        ready = threading.Semaphore(0)
+        used = [[] for _ in range(nconf)]  # request indices per configuration (ring reuse)
+
+        def waiter():
+            for k in range(count):
+                ready.acquire()
+                pool.wait(tickets[k][0])
+                done_at[k] = time.perf_counter()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for k in range(count):
+            delay = t0 + arrive[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ci = int(pick[k])
+            if len(used[ci]) >= ring:  # the output buffer of this slot must be free
+                prev = used[ci][-ring]
+                while done_at[prev] is None:
+                    time.sleep(0.0002)
+            tickets[k] = submit(ci, len(used[ci]) % ring)
+            used[ci].append(k)
+            ready.release()
+        th.join()
+        lat = np.array([done_at[k] - (t0 + arrive[k]) for k in range(count)]) * 1e3
+        span = max(done_at) - t0
+        bad = [k for k in range(count) if info_from_bytes(tickets[k][3].numpy())["status"] != 0]
+        npix = sum(confs[int(c)][3] ** 2 for c in pick)
+        legs.append({"rate_per_s": rate, "requests": count, "pairs_per_s": count / span,
+                     "mpix_per_s": npix / span / 1e6,
+                     "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                    "max": float(lat.max())}, "failed": bad})
+    used_bytes, lanes = pool.usage
+    pool.close()
+    return {"api": "sfft_pool_submit / sfft_pool_wait (host requests, pinned)", "depth": 4, "batch": 2,
+            "policy": "eager flush (sfft_pool_set_eager): a batch starts when its lane is idle",
+            "budget_gb": 180, "configurations": [[c[3], *c[2][:1], c[2][2], c[2][3]] for c in confs],
+            "configuration_fields": ["n", "w", "dk", "db"], "lanes_warmed": True, "legs": legs,
+            "pool_end": {"bytes": used_bytes, "lanes": lanes}}
 
 
 def run_pairs_only(args):

@@ -295,6 +295,46 @@ int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d
                    sfft_solve_info *const *d_infos, void *const *d_diffs, sfft_stream_t stream);
 
 /*
+ * The pairs of sfft_run_pairs captured once into a CUDA graph, replayed as
+ * one launch (the batched-sectors workload: a survey's uneven CCD sectors,
+ * Sec. 3 and the timings of Sec. 4 over many pairs).  Creation records, for
+ * the given plans and device buffers, every kernel of the whole sequence
+ * (builds, solves `solve_group` systems per cooperative launch, largest
+ * first, subtractions) into a graph on a private stream; each
+ * sfft_batch_launch then enqueues all of it on `stream` with one call.
+ * Arguments as sfft_run_pairs; the plans and every buffer must stay valid,
+ * at the same addresses, until sfft_batch_destroy (the graph holds them).
+ * New data is processed by writing new images into the same input buffers
+ * before a launch.  Per pair the results equal sfft_run_pair's bit for bit.
+ *   solve_group : 1..8 systems per solve launch, or 0 to autotune: the batch
+ *                 is captured with groups of 8, 4, 2 and 1, each replayed
+ *                 (once untimed, then three times timed, CUDA events) on the
+ *                 buffers' current contents, and the fastest is kept;
+ *                 creation then runs the batch 16 times and synchronises.
+ * Creation synchronises its private stream; it may not run inside another
+ * stream capture.  A plan must not be used by other calls while a launch of
+ * a batch that holds it is in flight.
+ */
+typedef struct sfft_batch_s *sfft_batch_t;
+int sfft_batch_create(const sfft_plan_t *plans, int32_t count, const void *const *d_refs,
+                      const void *const *d_scis, const uint8_t *const *d_masks, double *const *d_xs,
+                      sfft_solve_info *const *d_infos, void *const *d_diffs, int32_t solve_group,
+                      sfft_batch_t *out);
+
+/* Enqueue the whole captured batch on `stream` (one graph launch). */
+int sfft_batch_launch(sfft_batch_t batch, sfft_stream_t stream);
+
+/*
+ * The batch's solve grouping, its number of kernel launches per replay, and
+ * (autotuned batches; NULL to skip) the replay times in ms of groups 8, 4,
+ * 2 and 1.
+ */
+int sfft_batch_info(sfft_batch_t batch, int32_t *solve_group, int32_t *launches, float *tune_ms4);
+
+/* Frees the graph (NULL is a no-op); the plans and buffers stay the caller's. */
+int sfft_batch_destroy(sfft_batch_t batch);
+
+/*
  * One whole pair from and to host memory: copies h_ref, h_sci (and h_mask if
  * not NULL) to plan-owned device buffers, runs build, solve and subtract,
  * copies the coefficients, the solve status and the difference image back,
@@ -381,6 +421,17 @@ int sfft_poll(sfft_server_t server, const sfft_ticket *ticket);
 int sfft_wait(sfft_server_t server, const sfft_ticket *ticket, int64_t timeout_us);
 
 /*
+ * Continuous batching policy, off by default.  With enable != 0 a batch that
+ * is not yet full is solved at once (without waiting for `batch` requests,
+ * sfft_flush, poll or wait) whenever every request flushed before it has
+ * completed: a request that arrives while the server is idle starts its
+ * solve as soon as its build is done, and the requests that arrive while the
+ * server is busy gather into the next batch.  Results are unchanged (each
+ * system's solve does not depend on its batch partners).
+ */
+int sfft_server_set_eager(sfft_server_t server, int32_t enable);
+
+/*
  * Testing hook, off by default: with enable != 0 the server's completion
  * queries report a CUDA error (as a failed device would) without asking the
  * device, so that the error paths of sfft_poll, sfft_wait and sfft_submit can
@@ -431,6 +482,13 @@ int sfft_pool_submit(sfft_pool_t pool, const sfft_config *cfg, const sfft_reques
 /* As sfft_poll / sfft_wait for a pool ticket. */
 int sfft_pool_poll(sfft_pool_t pool, const sfft_pool_ticket *ticket);
 int sfft_pool_wait(sfft_pool_t pool, const sfft_pool_ticket *ticket, int64_t timeout_us);
+
+/*
+ * The continuous batching policy of sfft_server_set_eager for every lane of
+ * the pool, current and future; with it set, sfft_pool_wait first starts the
+ * open batches of all idle lanes before it blocks.
+ */
+int sfft_pool_set_eager(sfft_pool_t pool, int32_t enable);
 
 /* Device bytes held by the pool's lanes and their number. */
 int sfft_pool_usage(sfft_pool_t pool, uint64_t *bytes, int32_t *lanes);

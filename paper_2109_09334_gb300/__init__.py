@@ -180,6 +180,52 @@ def run_pairs(plans, refs, scis, masks=None, outs=None):
     return list(zip(Ds, xs, infos))
 
 
+class SfftBatch:
+    """A batch of pairs captured once into a CUDA graph (sfft_batch_*) and
+    replayed by launch(): pair i on plans[i] (distinct SfftPlan objects of one
+    precision) with the fixed device tensors refs[i], scis[i] (and masks[i]);
+    write new images into those tensors between launches.  Outputs D, x and
+    info per pair are allocated here (or taken from outs) and rewritten by
+    every launch.  solve_group: systems per solve launch (1..8), or 0 to pick
+    the fastest grouping by timing replays at creation."""
+
+    def __init__(self, plans, refs, scis, masks=None, outs=None, solve_group=0):
+        torch = _torch()
+        for p, r, s in zip(plans, refs, scis):
+            p._check_img(r), p._check_img(s)
+        self.plans = list(plans)
+        self.refs, self.scis = list(refs), list(scis)
+        self.masks = None if masks is None else list(masks)
+        self.D = [outs[i] if outs is not None and outs[i] is not None else
+                  torch.empty(p.shape, dtype=p.dtype, device=p.device) for i, p in enumerate(plans)]
+        self.x = [torch.empty(p.n, dtype=torch.float64, device=p.device) for p in plans]
+        self.info = [torch.zeros(ctypes.sizeof(sfft_solve_info), dtype=torch.uint8, device=p.device)
+                     for p in plans]
+        self.handle = binding.sfft_batch_create([p.handle for p in plans], self.refs, self.scis, self.masks,
+                                                self.x, self.info, self.D, solve_group)
+
+    @property
+    def info_dict(self):
+        return binding.sfft_batch_info(self.handle)
+
+    def launch(self, stream=None):
+        """Enqueue the whole batch on `stream` (default: torch's current stream)."""
+        if stream is None:
+            stream = _torch().cuda.current_stream()
+        binding.sfft_batch_launch(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            binding.sfft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class SfftServer:
     """Several pairs of one configuration in flight (sfft_submit / sfft_poll / sfft_wait).
 
@@ -190,7 +236,7 @@ class SfftServer:
     """
 
     def __init__(self, n0, n1, w0, w1, dk, db, const_phot_ratio, dtype="float32", precision="mixed", depth=2,
-                 batch=1, spline=None):
+                 batch=1, spline=None, eager=False):
         torch = _torch()
         self.cfg = make_config(n0, n1, w0, w1, dk, db, const_phot_ratio, dtype, precision, spline)
         self.n = sfft_num_unknowns(self.cfg)
@@ -199,6 +245,8 @@ class SfftServer:
                       "float64": torch.float64, "f64": torch.float64}[str(dtype)]
         self.handle = sfft_server_create(self.cfg, depth, batch)
         self._pending = {}
+        if eager:
+            binding.sfft_server_set_eager(self.handle, True)
 
     @property
     def workspace_bytes(self):
@@ -274,9 +322,11 @@ class SfftPool:
     (sfft_pool_*): one lane per configuration, created on first use,
     idle lanes released least recently used first to admit new ones."""
 
-    def __init__(self, budget_bytes, depth=2, batch=1):
+    def __init__(self, budget_bytes, depth=2, batch=1, eager=False):
         self.handle = binding.sfft_pool_create(budget_bytes, depth, batch)
         self._keep = {}
+        if eager:
+            binding.sfft_pool_set_eager(self.handle, True)
 
     def submit(self, ref, sci, w0, w1, dk, db, const_phot_ratio, precision="mixed", mask=None, diff=None,
                stream=None, spline=None):

@@ -90,6 +90,10 @@ def library():
         lib.sfft_run_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pair_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_run_pairs.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        lib.sfft_batch_create.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32, ctypes.POINTER(vp)]
+        lib.sfft_batch_launch.argtypes = [vp, vp]
+        lib.sfft_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+        lib.sfft_batch_destroy.argtypes = [vp]
         reqp, tkp = ctypes.POINTER(sfft_request), ctypes.POINTER(sfft_ticket)
         lib.sfft_server_create.argtypes = [cfgp, i32, i32, ctypes.POINTER(vp)]
         lib.sfft_flush.argtypes = [vp]
@@ -101,6 +105,8 @@ def library():
         lib.sfft_stream_wait_ticket.argtypes = [vp, tkp, vp]
         lib.sfft_server_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         lib.sfft_server_debug_fail_queries.argtypes = [vp, i32]
+        lib.sfft_server_set_eager.argtypes = [vp, i32]
+        lib.sfft_pool_set_eager.argtypes = [vp, i32]
         ptk = ctypes.POINTER(sfft_pool_ticket)
         lib.sfft_pool_create.argtypes = [ctypes.c_uint64, i32, i32, ctypes.POINTER(vp)]
         lib.sfft_pool_destroy.argtypes = [vp]
@@ -268,6 +274,36 @@ def sfft_run_pairs(plans, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, strea
            "sfft_run_pairs")
 
 
+def sfft_batch_create(plans, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, solve_group=0):
+    """Capture the pairs of sfft_run_pairs into a CUDA graph; returns the batch handle."""
+    n = len(plans)
+    for name, v in (("d_refs", d_refs), ("d_scis", d_scis), ("d_diffs", d_diffs), ("d_masks", d_masks),
+                    ("d_xs", d_xs), ("d_infos", d_infos)):
+        if v is not None and len(v) != n:
+            raise ValueError(f"sfft_batch_create: {name} has {len(v)} entries for {n} plans")
+    hp = (ctypes.c_void_p * n)(*plans)
+    h = ctypes.c_void_p()
+    _check(library().sfft_batch_create(hp, n, _ptr_array(d_refs), _ptr_array(d_scis), _ptr_array(d_masks),
+                                       _ptr_array(d_xs), _ptr_array(d_infos), _ptr_array(d_diffs),
+                                       int(solve_group), ctypes.byref(h)), "sfft_batch_create")
+    return h.value
+
+
+def sfft_batch_launch(batch, stream=None):
+    _check(library().sfft_batch_launch(batch, _s(stream)), "sfft_batch_launch")
+
+
+def sfft_batch_info(batch):
+    g, nl = ctypes.c_int32(), ctypes.c_int32()
+    t = (ctypes.c_float * 4)()
+    _check(library().sfft_batch_info(batch, ctypes.byref(g), ctypes.byref(nl), t), "sfft_batch_info")
+    return {"solve_group": g.value, "launches": nl.value, "tune_ms": {k: t[i] for i, k in enumerate((8, 4, 2, 1))}}
+
+
+def sfft_batch_destroy(batch):
+    _check(library().sfft_batch_destroy(batch), "sfft_batch_destroy")
+
+
 def sfft_run_pair_host(plan, h_ref, h_sci, h_mask, h_x, h_info, h_diff, stream=None):
     _check(library().sfft_run_pair_host(plan, _p(h_ref), _p(h_sci), _p(h_mask), _p(h_x), _p(h_info),
                                         _p(h_diff), _s(stream)), "sfft_run_pair_host")
@@ -336,6 +372,14 @@ def sfft_server_launch_count(server):
 def sfft_server_debug_fail_queries(server, enable):
     """Testing hook: make the server's completion queries report a CUDA error."""
     _check(library().sfft_server_debug_fail_queries(server, int(bool(enable))), "sfft_server_debug_fail_queries")
+
+
+def sfft_server_set_eager(server, enable):
+    _check(library().sfft_server_set_eager(server, int(bool(enable))), "sfft_server_set_eager")
+
+
+def sfft_pool_set_eager(pool, enable):
+    _check(library().sfft_pool_set_eager(pool, int(bool(enable))), "sfft_pool_set_eager")
 
 
 def sfft_pool_create(budget_bytes, depth=2, batch=1):

@@ -680,9 +680,11 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci, const 
     return run_pair((Plan *)plan, d_ref, d_sci, d_mask, d_M, d_rhs, d_x, d_info, d_diff, (cudaStream_t)stream);
 }
 
-int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs, const void *const *d_scis,
-                   const uint8_t *const *d_masks, double *const *d_xs, sfft_solve_info *const *d_infos,
-                   void *const *d_diffs, sfft_stream_t stream) {
+namespace {
+
+// Host-side checks of a set of pairs (sfft_run_pairs, sfft_batch_create).
+int check_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs, const void *const *d_scis,
+                const uint8_t *const *d_masks, void *const *d_diffs) {
     if (!plans || count < 1 || !d_refs || !d_scis || !d_diffs) return SFFT_ERR_INVALID;
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !d_refs[i] || !d_scis[i] || !d_diffs[i]) return SFFT_ERR_INVALID;
@@ -692,7 +694,31 @@ int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return SFFT_ERR_INVALID;  // one workspace per pair
     }
-    cudaStream_t s = (cudaStream_t)stream;
+    return SFFT_OK;
+}
+
+// Enqueue the pairs on s: every build, the systems solved `group` (1..8) per
+// launch, largest first, then every subtraction.
+cudaError_t enqueue_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs,
+                          const void *const *d_scis, const uint8_t *const *d_masks, double *const *d_xs,
+                          sfft_solve_info *const *d_infos, void *const *d_diffs, int group, cudaStream_t s);
+
+}  // namespace
+
+int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs, const void *const *d_scis,
+                   const uint8_t *const *d_masks, double *const *d_xs, sfft_solve_info *const *d_infos,
+                   void *const *d_diffs, sfft_stream_t stream) {
+    const int rc = check_pairs(plans, count, d_refs, d_scis, d_masks, d_diffs);
+    if (rc != SFFT_OK) return rc;
+    return status_of(enqueue_pairs(plans, count, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, kMaxSolveBatch,
+                                   (cudaStream_t)stream));
+}
+
+namespace {
+
+cudaError_t enqueue_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_refs,
+                          const void *const *d_scis, const uint8_t *const *d_masks, double *const *d_xs,
+                          sfft_solve_info *const *d_infos, void *const *d_diffs, int group, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
         Plan *p = (Plan *)plans[i];
@@ -714,8 +740,8 @@ int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return ((Plan *)plans[a])->n > ((Plan *)plans[b])->n; });
-    for (int g = 0; g < count && e == cudaSuccess; g += kMaxSolveBatch) {
-        const int cnt = count - g < kMaxSolveBatch ? count - g : kMaxSolveBatch;
+    for (int g = 0; g < count && e == cudaSuccess; g += group) {
+        const int cnt = count - g < group ? count - g : group;
         Plan *ps[kMaxSolveBatch];
         const double *M[kMaxSolveBatch], *rhs[kMaxSolveBatch];
         double *x[kMaxSolveBatch];
@@ -734,7 +760,131 @@ int sfft_run_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d
         if (p->last_mask) e = row_transform(p, p->last_ref, p->last_sci, nullptr, false, s);
         if (e == cudaSuccess) e = subtract_from_rows(p, p->last_x, p->last_diff, s);
     }
-    return status_of(e);
+    return e;
+}
+
+}  // namespace
+
+// ---- a batch of pairs captured once into a CUDA graph -------------------------
+
+struct sfft_batch_s {
+    cudaGraphExec_t exec = nullptr;
+    int count = 0, group = 0, launches = 0;
+    float tune_ms[4] = {0, 0, 0, 0};  // replay time of groups 8, 4, 2, 1 (autotune only)
+};
+
+namespace {
+
+// Capture the batch with solve groups of `group` on a private stream.
+cudaError_t capture_batch(const sfft_plan_t *plans, int32_t count, const void *const *d_refs,
+                          const void *const *d_scis, const uint8_t *const *d_masks, double *const *d_xs,
+                          sfft_solve_info *const *d_infos, void *const *d_diffs, int group, cudaStream_t cs,
+                          cudaGraphExec_t *exec, int *launches) {
+    uint64_t l0 = 0, l1 = 0;
+    for (int i = 0; i < count; ++i) l0 += ((Plan *)plans[i])->launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t ee = enqueue_pairs(plans, count, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, group, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (ee != cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < count; ++i) l1 += ((Plan *)plans[i])->launches;
+    *launches = (int)(l1 - l0);
+    return e;
+}
+
+}  // namespace
+
+int sfft_batch_create(const sfft_plan_t *plans, int32_t count, const void *const *d_refs, const void *const *d_scis,
+                      const uint8_t *const *d_masks, double *const *d_xs, sfft_solve_info *const *d_infos,
+                      void *const *d_diffs, int32_t solve_group, sfft_batch_t *out) {
+    if (!out) return SFFT_ERR_INVALID;
+    *out = nullptr;
+    if (solve_group < 0 || solve_group > kMaxSolveBatch) return SFFT_ERR_INVALID;
+    const int rc = check_pairs(plans, count, d_refs, d_scis, d_masks, d_diffs);
+    if (rc != SFFT_OK) return rc;
+    sfft_batch_s *b = new (std::nothrow) sfft_batch_s();
+    if (!b) return SFFT_ERR_OOM;
+    b->count = count;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess && solve_group > 0) {
+        b->group = solve_group;
+        e = capture_batch(plans, count, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, solve_group, cs, &b->exec,
+                          &b->launches);
+    } else if (e == cudaSuccess) {
+        // autotune: capture with solve groups of 8, 4, 2 and 1, replay each
+        // (after one untimed replay) three times on the caller's data and
+        // keep the fastest; the results do not depend on the grouping
+        const int groups[4] = {8, 4, 2, 1};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best = 0.f;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            cudaGraphExec_t ex = nullptr;
+            int nl = 0;
+            e = capture_batch(plans, count, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, groups[k], cs, &ex, &nl);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ex, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(ex, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                if (ex) cudaGraphExecDestroy(ex);
+                break;
+            }
+            b->tune_ms[k] = ms / 3.f;
+            if (!b->exec || ms < best) {
+                if (b->exec) cudaGraphExecDestroy(b->exec);
+                b->exec = ex;
+                b->group = groups[k];
+                b->launches = nl;
+                best = ms;
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+    if (cs) {
+        const cudaError_t es = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess) e = es;
+        cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        delete b;
+        return status_of(e);
+    }
+    *out = b;
+    return SFFT_OK;
+}
+
+int sfft_batch_launch(sfft_batch_t batch, sfft_stream_t stream) {
+    if (!batch) return SFFT_ERR_INVALID;
+    return status_of(cudaGraphLaunch(batch->exec, (cudaStream_t)stream));
+}
+
+int sfft_batch_info(sfft_batch_t batch, int32_t *solve_group, int32_t *launches, float *tune_ms4) {
+    if (!batch) return SFFT_ERR_INVALID;
+    if (solve_group) *solve_group = batch->group;
+    if (launches) *launches = batch->launches;
+    if (tune_ms4)
+        for (int k = 0; k < 4; ++k) tune_ms4[k] = batch->tune_ms[k];
+    return SFFT_OK;
+}
+
+int sfft_batch_destroy(sfft_batch_t batch) {
+    if (!batch) return SFFT_OK;
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    delete batch;
+    return SFFT_OK;
 }
 
 int sfft_run_pair_host(sfft_plan_t plan, const void *h_ref, const void *h_sci, const uint8_t *h_mask,

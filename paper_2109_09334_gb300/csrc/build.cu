@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
     const int np = padded_len(n1) + 4;  // +4: rows start in different banks
-    cpx<T> *tw = reinterpret_cast<cpx<T> *>(smem_raw);  // n1
-    cpx<T> *Z = tw + n1;                                 // TR * np
+    // the pass-ordered twiddles are read through L1 (a shared copy per block
+    // cost more than it saved)
+    const cpx<T> *tw = tw1g;
+    cpx<T> *Z = reinterpret_cast<cpx<T> *>(smem_raw);  // TR * np
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int grp = tid / G, gt = tid - grp * G;
     const int nseq = nfy + 1;
@@ -69,8 +71,6 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     const int x0b = (blockIdx.x / nfft) * TR;
     const int sa = 2 * f, sb = 2 * f + 1;
     cpx<T> *zr = Z + (size_t)grp * np;
-    const int ntw = pass_table_len(n1);
-    for (int q = tid; q < ntw; q += nthr) tw[q] = tw1g[q];
     if (x0b + grp < n0) {
         // thread gt loads pixels [16 gt, 16 gt + 16) of its row (all loads in flight)
         const size_t rowoff = (size_t)(x0b + grp) * n1;
@@ -88,9 +88,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
                 sv[c] = keep ? sv[c] : (T)0;
             }
         }
+        const T inv = (T)1 / (T)(n1 - 1);  // yt = (2y - (n1 - 1)) / (n1 - 1), by one multiply
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const T yt = coord<T>(y0 + c, n1);
+            const T yt = (T)(2 * (y0 + c) - (n1 - 1)) * inv;
             // weights yt^j (polynomial) or the tabulated y-functions (B-spline)
             const T wa = fy ? (sa < nfy ? fy[(size_t)sa * n1 + y0 + c] : (T)0) : ipow(yt, sa);
             const T wb = fy ? (sb < nfy ? fy[(size_t)sb * n1 + y0 + c] : (T)0) : ipow(yt, sb);
@@ -607,8 +608,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // shared table.  Each output keeps a plain FP32 partial over kFold residue
 // classes that is folded into a two-sum accumulator.
 constexpr int kPad = 8;   // complex elements of padding per image tile / transpose region
-// threads per block of the gather: the FP32 lag-range-16 variant keeps four
-// blocks of 28 product groups resident per SM; the others take up to 48 groups
+// threads per block of the gather: the FP32 lag-range-16 variant runs blocks
+// of 28 product groups, with registers for two blocks per SM (at four, the
+// register cap of 72 spilled the accumulators: 0.54 -> 0.45 ms at 4096^2);
+// the others take up to 48 groups
 template <typename T, int NS>
 __host__ __device__ constexpr int kGatherThreads() { return (sizeof(T) == 4 && NS == 5) ? 224 : 384; }
 constexpr int kFold = 4;  // residue classes per plain partial sum
@@ -622,7 +625,7 @@ __device__ __forceinline__ int out_slot(int c, int s1) {
 }
 
 template <typename T, int G, int NS>
-__global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS == 5) ? 4 : 1) k_gather(int n0, int n1, int nk, int nxp, int nbk, int npairs, int hmax,
+__global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS == 5) ? 2 : 1) k_gather(int n0, int n1, int nk, int nxp, int nbk, int npairs, int hmax,
                                                 const PairDesc *__restrict__ pairs, const cpx<T> *__restrict__ U,
                                                 const cpx<T> *__restrict__ xhat, const cpx<T> *__restrict__ tw0,
                                                 cpx<T> *__restrict__ Q) {
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
             dftG<T, G>(u, 1);
 #pragma unroll
             for (int o = 0; o < NS; ++o)
-                if (o_ok[o]) part[o] = part[o] + cmul(u[o < 3 ? o : o + 3], wrow_lb[o_rho[o]]);
+                if (o_ok[o]) part[o] = cfma(part[o], u[o < 3 ? o : o + 3], wrow_lb[o_rho[o]]);
         } else if (act) {
             const cpx<T> *wrow_lb = sW + (size_t)lb * wrow + hmax;
             // lane handles s2 = lane + G*c for c < 8/G; G-point DFT over r1
@@ -750,7 +753,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
                     else if (rp >= NA - h0) rho = rp - NA;
                     else continue;
                     const int o = out_slot<G, NS>(c, s1);
-                    if (o >= 0) part[o] = part[o] + cmul(u[s1], wrow_lb[rho]);
+                    if (o >= 0) part[o] = cfma(part[o], u[s1], wrow_lb[rho]);
                 }
             }
         }
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(kXcThreads) k_xcorr(int n0, int n1, BasisView 
 #pragma unroll
                 for (int k = 0; k < kXcLags; ++k)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) part[k] = part[k] + cmul(a[q], bw[q + k]);
+                    for (int q = 0; q < 4; ++q) part[k] = cfma(part[k], a[q], bw[q + k]);
                 if (++step == kXcFold) {
 #pragma unroll
                     for (int k = 0; k < kXcLags; ++k) {
@@ -1159,15 +1162,17 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     int TR = (sizeof(T) == 4 ? 1024 : 512) / G;
     if (TR > 16) TR = 16;
     if (TR > p->n0) TR = p->n0;
-    auto smem_of = [&](int tr) { return ((size_t)p->n1 + (size_t)tr * (padded_len(p->n1) + 4)) * sizeof(cpx<T>); };
+    auto smem_of = [&](int tr) { return (size_t)tr * (padded_len(p->n1) + 4) * sizeof(cpx<T>); };
     while (TR > 1 && smem_of(TR) > 200 * 1024) TR /= 2;
     if (p->tune_tr > 0 && p->tune_tr < TR) TR = p->tune_tr;
     const size_t smem = smem_of(TR);
     auto kern = k_rows<T, I>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // polynomial weights yt^j are computed in the kernel (a multiply per
+    // power), cheaper than the table's per-thread strided reads
     kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->nfy, TR, (const I *)ref,
                                                               (const I *)sci, mask, (cpx<T> *)p->F,
-                                                              (const cpx<T> *)p->twp1, ft.fy);
+                                                              (const cpx<T> *)p->twp1, p->bspline ? ft.fy : nullptr);
     }
     p->launches++;
     if (moments && !p->bspline) {

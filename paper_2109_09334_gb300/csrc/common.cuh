@@ -29,6 +29,25 @@ template <typename T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
 }
+// acc + a * b and acc - a * b as four fused multiply-adds each (the
+// products are not rounded separately, so the results differ from
+// acc +- cmul(a, b) in the last bits; both are single-rounding-per-term sums)
+template <typename T>
+__device__ __forceinline__ cpx<T> cfma(cpx<T> acc, cpx<T> a, cpx<T> b) {
+    T re = fma(a.re, b.re, acc.re);
+    re = fma(-a.im, b.im, re);
+    T im = fma(a.re, b.im, acc.im);
+    im = fma(a.im, b.re, im);
+    return mk(re, im);
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cfms(cpx<T> acc, cpx<T> a, cpx<T> b) {
+    T re = fma(-a.re, b.re, acc.re);
+    re = fma(a.im, b.im, re);
+    T im = fma(-a.re, b.im, acc.im);
+    im = fma(-a.im, b.re, im);
+    return mk(re, im);
+}
 // conj(a) * b
 template <typename T>
 __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {

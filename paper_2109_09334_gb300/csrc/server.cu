@@ -82,6 +82,9 @@ struct Server {
     // testing hook (sfft_server_debug_fail_queries): completion queries
     // report a CUDA error without asking the device
     bool fail_queries = false;
+    // eager flushing (sfft_server_set_eager): an incomplete batch is solved
+    // at once when everything flushed before it has completed
+    bool eager = false;
 };
 
 namespace {
@@ -230,6 +233,8 @@ int flush(Server *v) {
     return SFFT_OK;
 }
 
+int eager_flush(Server *v);
+
 int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
     const bool host = r->memory == SFFT_REQ_HOST;
     if (v->err != SFFT_OK) return v->err;
@@ -286,7 +291,19 @@ int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
     v->next_seq = seq + 1;
     *seq_out = seq;
     if (v->next_seq - v->flushed >= (uint64_t)v->batch) return flush(v);
-    return SFFT_OK;
+    return eager_flush(v);
+}
+
+// Continuous batching: with eager set, an incomplete batch is flushed as
+// soon as every request flushed before it has completed, so a request never
+// waits for batch partners while its server has nothing else in flight; when
+// the server is busy, the requests that arrive meanwhile gather into one
+// batch (caller holds mu).
+int eager_flush(Server *v) {
+    if (!v->eager || v->next_seq == v->flushed) return SFFT_OK;
+    const int rc = advance(v);
+    if (rc != SFFT_OK) return rc;
+    return v->watermark == v->flushed ? flush(v) : SFFT_OK;
 }
 
 }  // namespace
@@ -325,6 +342,7 @@ uint64_t server_bytes(const Server *v) {
 struct Pool {
     uint64_t budget = 0, used = 0, next_id = 1, clock = 0;
     int depth = 1, batch = 1;
+    bool eager = false;  // lanes flush eagerly (sfft_pool_set_eager)
     Lane lanes[kMaxPoolLanes];
     int nlanes = 0;
     std::mutex mu;
@@ -381,6 +399,14 @@ int sfft_server_create(const sfft_config *cfg, int32_t depth, int32_t batch, sff
     const int rc = create_server(cfg, depth, batch, &s);
     if (rc == SFFT_OK) *out = (sfft_server_t)s;
     return rc;
+}
+
+int sfft_server_set_eager(sfft_server_t server, int32_t enable) {
+    if (!server) return SFFT_ERR_INVALID;
+    Server *v = (Server *)server;
+    std::lock_guard<std::mutex> lock(v->mu);
+    v->eager = enable != 0;
+    return eager_flush(v);
 }
 
 int sfft_server_debug_fail_queries(sfft_server_t server, int32_t enable) {
@@ -551,6 +577,7 @@ int sfft_pool_submit(sfft_pool_t pool, const sfft_config *cfg, const sfft_reques
             sfft_server_destroy((sfft_server_t)srv);
             return SFFT_ERR_BUSY;
         }
+        srv->eager = pl->eager;
         lane = &pl->lanes[pl->nlanes++];
         lane->id = pl->next_id++;
         lane->cfg = *cfg;
@@ -574,6 +601,13 @@ int sfft_pool_wait(sfft_pool_t pool, const sfft_pool_ticket *ticket, int64_t tim
     {
         std::lock_guard<std::mutex> lock(pl->mu);
         if (ticket->lane == 0 || ticket->lane >= pl->next_id) return SFFT_ERR_INVALID;
+        if (pl->eager) {  // before blocking: start the open batches of idle lanes
+            for (int k = 0; k < pl->nlanes; ++k) {
+                Server *o = pl->lanes[k].srv;
+                std::lock_guard<std::mutex> lk(o->mu);
+                eager_flush(o);
+            }
+        }
         Lane *l = find_lane(pl, ticket->lane);
         if (!l) return SFFT_OK;  // a lane is released only once all its requests have completed
         srv = l->srv;
@@ -595,6 +629,22 @@ int sfft_pool_poll(sfft_pool_t pool, const sfft_pool_ticket *ticket) {
     if (!l) return SFFT_OK;
     sfft_ticket t{ticket->seq};
     return sfft_poll((sfft_server_t)l->srv, &t);
+}
+
+int sfft_pool_set_eager(sfft_pool_t pool, int32_t enable) {
+    if (!pool) return SFFT_ERR_INVALID;
+    Pool *pl = (Pool *)pool;
+    std::lock_guard<std::mutex> lock(pl->mu);
+    pl->eager = enable != 0;
+    int rc = SFFT_OK;
+    for (int k = 0; k < pl->nlanes; ++k) {
+        Server *o = pl->lanes[k].srv;
+        std::lock_guard<std::mutex> lk(o->mu);
+        o->eager = pl->eager;
+        const int r = eager_flush(o);
+        if (rc == SFFT_OK) rc = r;
+    }
+    return rc;
 }
 
 int sfft_pool_usage(sfft_pool_t pool, uint64_t *bytes, int32_t *lanes) {

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
             for (int a = (W0 >= 0 ? W0 : w0); a >= -(W0 >= 0 ? W0 : w0); --a) {
                 const cpx<T> kv = kt[a + w0];
 #pragma unroll
-                for (int q = 0; q < Q; ++q) acc[q] = acc[q] - cmul(kv, win[q]);
+                for (int q = 0; q < Q; ++q) acc[q] = cfms(acc[q], kv, win[q]);
 #pragma unroll
                 for (int q = 0; q + 1 < Q; ++q) win[q] = win[q + 1];
                 win[Q - 1] = W[padq(wrapx(x0 + Q - a))];

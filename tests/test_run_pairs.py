@@ -146,3 +146,66 @@ def test_run_pairs_rejects_duplicates_and_mixed_precision(lib):
     assert e.value.status == B.SFFT_ERR_INVALID
     a.close()
     b.close()
+
+
+def test_batch_rejects_bad_arguments(lib):
+    """sfft_batch_create checks its arguments before any capture or CUDA call."""
+    from paper_2109_09334_gb300 import binding as B
+    vp = ctypes.c_void_p
+    one = (vp * 1)(1)
+    h = vp()
+    assert lib.sfft_batch_create(one, 1, one, one, None, None, None, one, 0, None) == B.SFFT_ERR_INVALID
+    for group in (-1, 9):
+        assert lib.sfft_batch_create(one, 1, one, one, None, None, None, one, group, ctypes.byref(h)) == \
+            B.SFFT_ERR_INVALID
+    assert lib.sfft_batch_create(None, 1, one, one, None, None, None, one, 0, ctypes.byref(h)) == B.SFFT_ERR_INVALID
+    assert lib.sfft_batch_create(one, 0, one, one, None, None, None, one, 0, ctypes.byref(h)) == B.SFFT_ERR_INVALID
+    assert h.value is None
+    assert lib.sfft_batch_launch(None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_batch_info(None, None, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_batch_destroy(None) == B.SFFT_OK
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("solve_group", [0, 3])
+def test_batch_graph_matches_run_pair(lib, solve_group):
+    """The captured batch (autotuned grouping, or groups of three) replayed
+    twice, with new images written into the input buffers in between:
+    every pair bitwise equal to sfft_run_pair on the same inputs."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftBatch, SfftPlan, info_from_bytes
+    plans, inputs = [], []
+    for k, (n0, n1, w, dk, db, cpr) in enumerate(MIXED):
+        plans.append(SfftPlan(n0, n1, w, w, dk, db, cpr))
+        inputs.append(_pair(n0, n1, k, 500, torch.float32))
+    refs = [torch.empty_like(i[0]) for i in inputs]
+    scis = [torch.empty_like(i[1]) for i in inputs]
+    masks = [i[2] for i in inputs]
+    for r, s, i in zip(refs, scis, inputs):
+        r.copy_(i[0])
+        s.copy_(i[1])
+    torch.cuda.synchronize()
+    batch = SfftBatch(plans, refs, scis, masks, solve_group=solve_group)
+    info = batch.info_dict
+    assert info["solve_group"] == (solve_group or info["solve_group"]) and 1 <= info["solve_group"] <= 8
+    assert info["launches"] > len(plans)
+    for rnd in range(2):
+        if rnd == 1:  # new data in the same buffers
+            for k, (r, s) in enumerate(zip(refs, scis)):
+                r.copy_(torch.roll(inputs[k][0], 1, 0))
+                s.copy_(torch.roll(inputs[k][1], 1, 0))
+        stream = torch.cuda.current_stream()
+        batch.launch(stream)
+        torch.cuda.synchronize()
+        got = [(D.cpu().numpy(), x.cpu().numpy(), info_from_bytes(i.cpu().numpy()))
+               for D, x, i in zip(batch.D, batch.x, batch.info)]
+        for k, p in enumerate(plans):
+            eD, ex, ei = _expected(p, refs[k], scis[k], masks[k])
+            assert ei["status"] == 0
+            assert got[k][2] == ei, (rnd, k)
+            assert np.array_equal(got[k][1], ex), (rnd, k)
+            assert np.array_equal(got[k][0], eD), (rnd, k)
+    batch.close()
+    for p in plans:
+        p.close()

@@ -206,3 +206,35 @@ def test_failed_completion_query_ends_wait_with_error(lib):
     torch.cuda.synchronize()
     srv.close()
     assert lib.sfft_server_debug_fail_queries(None, 1) == B.SFFT_ERR_INVALID
+
+
+@pytest.mark.gpu
+def test_eager_flush_solves_incomplete_batch_without_wait(lib):
+    """With eager flushing, a lone request in a batch of four is solved and
+    subtracted as soon as it is submitted to an idle server: after a device
+    synchronisation (no poll, wait or flush) its outputs equal sfft_run_pair's
+    bit for bit.  Without it the batch waits: the outputs are untouched."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, SfftServer
+    n0 = n1 = 64
+    R, S, _ = make_pairs(n0, n1, 1, seed=51)[0]
+    Rt = torch.from_numpy(R.astype(np.float32)).cuda()
+    St = torch.from_numpy(S.astype(np.float32)).cuda()
+    plan = SfftPlan(n0, n1, 2, 2, 1, 1, 1, dtype="float32", precision="mixed")
+    De, xe, _, _, _ = plan.run_pair(Rt, St)
+    torch.cuda.synchronize()
+    for eager in (True, False):
+        srv = SfftServer(n0, n1, 2, 2, 1, 1, 1, dtype="float32", precision="mixed", depth=4, batch=4, eager=eager)
+        D = torch.full_like(Rt, float("nan"))
+        t, _, x, _ = srv.submit(Rt, St, diff=D)
+        torch.cuda.synchronize()
+        if eager:
+            np.testing.assert_array_equal(D.cpu().numpy(), De.cpu().numpy())
+            np.testing.assert_array_equal(x.cpu().numpy(), xe.cpu().numpy())
+        else:
+            assert torch.isnan(D).all()
+        assert srv.wait(t)
+        np.testing.assert_array_equal(D.cpu().numpy(), De.cpu().numpy())
+        srv.close()
+    plan.close()
