@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
                     help="sectors64: solve the sectors' systems eight per launch, or one per pair")
     ap.add_argument("--no-masked", action="store_true", help="skip the transient-masked pair measurement")
+    ap.add_argument("--solve-tc", action="store_true",
+                    help="pair mode: the solve's tile products on the tensor cores (for profiler captures)")
     ap.add_argument("--no-sectors", action="store_true", help="skip the 64-sector batch measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the loaded serving-stream measurement")
     ap.add_argument("--oracle-sample", type=int, default=0,
@@ -497,6 +499,26 @@ def run_ours(args):
         per_pair["solve"] = max(ms_step - sum(per_pair.values()), 0.0)
         top = max(per_pair, key=per_pair.get)
         tot = sum(per_pair.values())
+        # the solve with its tile products on the tensor cores (tcgen05, 3xTF32)
+        # against the built-in CUDA-core tiles, one system per launch
+        shapes = binding.sfft_plan_tuning(plan.handle)
+        solve_var = {}
+        for name, tcv in (("cuda_cores", 0), ("tensor_cores", 2)):
+            binding.sfft_plan_set_tuning(plan.handle, dict(shapes, solve_tensor_cores=tcv))
+            step(0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                binding.sfft_replay_stage(plan.handle, binding.SFFT_STAGE_SOLVE, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            solve_var[name] = {"ms": round(e0.elapsed_time(e1) / 10, 4),
+                               "solve": info_from_bytes(info.cpu().numpy())}
+        binding.sfft_plan_set_tuning(plan.handle, shapes)
+        step(0)
+        torch.cuda.synchronize()
+        result["solve_tile_products_ms"] = solve_var
         result["stages_ms"] = {k: round(v, 4) for k, v in stage_ms.items()}
         result["stages_note"] = ("each stage replayed alone on one plan; 'solve' is one system per launch, "
                                  "the serving path solves `batch` per launch")
@@ -1026,6 +1048,9 @@ def run_pairs_only(args):
     plan = SfftPlan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
                     precision=args.precision)
     Rt, St = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    if args.solve_tc:
+        from paper_2109_09334_gb300 import binding
+        binding.sfft_plan_set_tuning(plan.handle, dict(binding.sfft_plan_tuning(plan.handle), solve_tensor_cores=2))
     for _ in range(args.warmup + args.steps):
         D, x, info, _, _ = plan.run_pair(Rt, St)
     torch.cuda.synchronize()

@@ -511,8 +511,10 @@ typedef enum {
  * the given device buffers with sfft_run_pair, then times each tunable stage
  * (sfft_replay_stage) over candidate launch shapes and keeps the fastest:
  * rows per block of the row FFT, images per block of the column FFT and
- * row pairs per block of the inverse row FFT (the solve grid stays as set:
- * a single system's time does not predict batched solves).  The shapes change how the work is split into blocks, not
+ * row pairs per block of the inverse row FFT (the solve grid and the
+ * solve's tensor-core tile products stay as set: a single system's time does
+ * not predict batched solves, and the tensor-core products round
+ * differently).  The shapes change how the work is split into blocks, not
  * the arithmetic, so results are unchanged.  They stay with the plan and are
  * remembered for later plans (and server slots, pool lanes) of the same image
  * size, types and D_K in this process.  Synchronises the stream.
@@ -527,9 +529,16 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
  *   [1] images per block of the column FFT (0..4),
  *   [2] row pairs per block of the inverse row FFT (0..4),
  *   [3] blocks of the solve grid (0 or up to 512; used only when it exceeds
- *       the systems in the launch and is at most the built-in grid).
+ *       the systems in the launch and is at most the built-in grid),
+ *   [4] the FP32 solve's 64x64x32 trailing-update tile products: 0 or 1 on
+ *       the CUDA cores, 2 on the tensor cores (tcgen05.mma kind::tf32 with a
+ *       3xTF32 split, accumulator in tensor memory; that kernel variant runs
+ *       one block per SM).  The built-in choice is the CUDA cores, measured
+ *       faster for these latency-bound tiles; the tensor-core products round
+ *       differently (the refined solution meets the same tolerance).
+ *       Ignored by FP64 plans.
  */
-#define SFFT_TUNING_LEN 4
+#define SFFT_TUNING_LEN 5
 
 /* The plan's launch shapes (shapes: SFFT_TUNING_LEN values, written). */
 int sfft_plan_tuning(sfft_plan_t plan, int32_t *shapes);

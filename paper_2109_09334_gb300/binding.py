@@ -428,8 +428,8 @@ def sfft_plan_autotune(plan, d_ref, d_sci, d_diff, stream=None):
     _check(library().sfft_plan_autotune(plan, _p(d_ref), _p(d_sci), _p(d_diff), _s(stream)), "sfft_plan_autotune")
 
 
-SFFT_TUNING_LEN = 4
-TUNING_KEYS = ("rows_per_block", "images_per_block", "row_pairs_per_block", "solve_grid")
+SFFT_TUNING_LEN = 5
+TUNING_KEYS = ("rows_per_block", "images_per_block", "row_pairs_per_block", "solve_grid", "solve_tensor_cores")
 
 
 def sfft_plan_tuning(plan):

@@ -163,6 +163,7 @@ static void get_shapes(const Plan *p, int32_t *v) {
     v[1] = p->tune_gi;
     v[2] = p->tune_ng;
     v[3] = p->tune_sgrid;
+    v[4] = p->tune_tc;
 }
 
 static void set_shapes(Plan *p, const int32_t *v) {
@@ -170,6 +171,7 @@ static void set_shapes(Plan *p, const int32_t *v) {
     p->tune_gi = v[1];
     p->tune_ng = v[2];
     p->tune_sgrid = v[3];
+    p->tune_tc = v[4];
 }
 constexpr int kTuneCache = 64;
 static TuneEntry g_tune[kTuneCache];
@@ -231,8 +233,8 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         }
     }
     // gather pairs
-    p->host_pairs = (PairDesc *)malloc(
-        (size_t)(p->nk * (p->nk + 1) / 2 + p->nk * p->nbx + p->nk) * sizeof(PairDesc));
+    const int maxp = p->nk * (p->nk + 1) / 2 + p->nk * p->nbx + p->nk;
+    p->host_pairs = (PairDesc *)malloc((size_t)2 * maxp * sizeof(PairDesc));
     if (!p->host_pairs) {
         plan_free(p);
         return SFFT_ERR_OOM;
@@ -245,6 +247,7 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         d.b = b;
         d.h0 = h0;
         d.row0 = rows;
+        d.row1 = -1;
         rows += 2 * h0 + 1;
         p->host_pairs[np++] = d;
     };
@@ -256,6 +259,33 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     for (int a = 0; a < p->nk; ++a) push(PK_THETA, a, p->nk, cfg->w0);
     p->npairs = np;
     p->nrows = rows;
+    {
+        // The gather's list.  Its lag-range-16 variant (NA = 64, |rho| <= 16)
+        // transforms the real auto-products Omega_tt two at a time (PK_OMEGA2);
+        // the other variants take the products one by one.
+        PairDesc *g = p->host_pairs + np;
+        int ng = 0, pending = -1;
+        const bool pack = !p->gen0 && p->na == 64 && 2 * cfg->w0 <= 16;
+        for (int k = 0; k < np; ++k) {
+            const PairDesc &d = p->host_pairs[k];
+            if (pack && d.kind == PK_OMEGA && d.a == d.b) {
+                if (pending < 0) {
+                    pending = k;
+                    continue;
+                }
+                PairDesc q = p->host_pairs[pending];
+                q.kind = PK_OMEGA2;
+                q.b = d.a;
+                q.row1 = d.row0;
+                g[ng++] = q;
+                pending = -1;
+                continue;
+            }
+            g[ng++] = d;
+        }
+        if (pending >= 0) g[ng++] = p->host_pairs[pending];
+        p->ngpairs = ng;
+    }
 
     const size_t P = (size_t)p->n0 * p->n1;
     const size_t half = (size_t)p->h1c * p->n0;
@@ -292,12 +322,14 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
         SFFT_ALLOC(p->twpm1, (size_t)p->m1 * csz);
     }
     SFFT_ALLOC(p->Q, (size_t)p->nrows * p->h1c * csz);
-    SFFT_ALLOC(p->pairs, (size_t)np * sizeof(PairDesc));
+    SFFT_ALLOC(p->pairs, (size_t)(np + p->ngpairs) * sizeof(PairDesc));
+    p->gpairs = p->pairs + np;
     SFFT_ALLOC(p->rowmom, (size_t)p->n0 * p->nmom * sizeof(double));
     SFFT_ALLOC(p->lag, nlag * sizeof(double));
     SFFT_ALLOC(p->A, n * n * rsz);
     SFFT_ALLOC(p->Wm, n * n * rsz);
     p->solve_grid = solve_grid_size(p->fp64);
+    p->solve_grid_tc = p->fp64 ? 0 : solve_grid_size(false, true);
     if (p->solve_grid <= 0 || p->solve_grid > kMaxSolveGrid) {
         plan_free(p);
         return SFFT_ERR_CUDA;
@@ -315,7 +347,8 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
 
     // constant tables
     cudaError_t err;
-    if ((err = cudaMemcpyAsync(p->pairs, p->host_pairs, np * sizeof(PairDesc), cudaMemcpyHostToDevice, s))) {
+    if ((err = cudaMemcpyAsync(p->pairs, p->host_pairs, (np + p->ngpairs) * sizeof(PairDesc), cudaMemcpyHostToDevice,
+                               s))) {
         plan_free(p);
         return SFFT_ERR_CUDA;
     }
@@ -575,6 +608,8 @@ int sfft_plan_autotune(sfft_plan_t plan, const void *d_ref, const void *d_sci, v
         {&p->tune_gi, SFFT_STAGE_COLS, {0, 3, 2, 1, -1}},
         {&p->tune_ng, SFFT_STAGE_SUBTRACT, {0, 2, 1, -1, -1}},
     };
+    // (the tensor-core tile products of the solve, tune_tc, are not chosen
+    // here: they round differently, and tuning must not change results)
     // The solve grid is not tuned here: a single system's time does not
     // predict the batched solves of the serving path (sfft_plan_set_tuning
     // sets it by hand).
@@ -614,6 +649,7 @@ int sfft_plan_set_tuning(sfft_plan_t plan, const int32_t *shapes) {
     if (tr < 0 || tr > 16 || (tr & (tr - 1)) != 0) return SFFT_ERR_INVALID;  // 0 or a power of two
     if (shapes[1] < 0 || shapes[1] > 4 || shapes[2] < 0 || shapes[2] > 4) return SFFT_ERR_INVALID;
     if (shapes[3] < 0 || shapes[3] > kMaxSolveGrid) return SFFT_ERR_INVALID;
+    if (shapes[4] < 0 || shapes[4] > 2) return SFFT_ERR_INVALID;
     set_shapes((Plan *)plan, shapes);
     tune_store((Plan *)plan);  // later plans of this configuration start with them
     return SFFT_OK;

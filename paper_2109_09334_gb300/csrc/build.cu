@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
     if (act) pd = pairs[pidx];
     else {
         pd.kind = 0;
-        pd.a = pd.b = pd.h0 = pd.row0 = 0;
+        pd.a = pd.b = pd.h0 = pd.row0 = pd.row1 = 0;
     }
     const int h0 = pd.h0;
     const int wrow = 2 * hmax + 1;
@@ -706,10 +706,19 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
             const cpx<T> *A = buf + (size_t)pd.a * NAP;
             const cpx<T> *B = (pd.kind == PK_LAMBDA) ? buf + (size_t)(nimg + pd.b) * NAP : buf + (size_t)pd.b * NAP;
             cpx<T> v[8];
+            if (pd.kind == PK_OMEGA2) {  // |U_a|^2 + i |U_b|^2
 #pragma unroll
-            for (int r2 = 0; r2 < 8; ++r2) {
-                const int r = lane + G * r2;
-                v[r2] = cmulc(A[r], B[r]);
+                for (int r2 = 0; r2 < 8; ++r2) {
+                    const int r = lane + G * r2;
+                    const cpx<T> ua = A[r], ub = B[r];
+                    v[r2] = mk(ua.re * ua.re + ua.im * ua.im, ub.re * ub.re + ub.im * ub.im);
+                }
+            } else {
+#pragma unroll
+                for (int r2 = 0; r2 < 8; ++r2) {
+                    const int r = lane + G * r2;
+                    v[r2] = cmulc(A[r], B[r]);
+                }
             }
             if (m == 0 && lb == 0 && lane == 0) v[0] = mk((T)0, (T)0);  // DC bin removed
             dft8(v, 1);
@@ -766,6 +775,28 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
         }
         __syncthreads();  // the buffer of this step is refilled two steps later
     }
+    cpx<T> z[NS];
+#pragma unroll
+    for (int o = 0; o < NS; ++o) z[o] = mk((T)acc[o].re.value(), (T)acc[o].im.value());
+    // A packed pair holds Z = Q_a + i Q_b with Q_a, Q_b the lag sums of two
+    // real sequences, so Q_a(rho) = (Z(rho) + conj Z(-rho)) / 2 and
+    // Q_b(rho) = (Z(rho) - conj Z(-rho)) / 2i.  Z(-rho) of this lane's slot o
+    // sits in lane (8 - lane) mod 8 of the group, slot map0[o] (lane 0) or
+    // map1[o] (others); every lane takes part in the shuffles.
+    cpx<T> zn[NS];
+    if constexpr (NS == 5) {
+        const int wl = threadIdx.x & 31;
+        const int src = (wl & ~7) | ((8 - lane) & 7);
+        cpx<T> zs[NS];
+#pragma unroll
+        for (int o = 0; o < NS; ++o) {
+            zs[o].re = __shfl_sync(0xffffffffu, z[o].re, src);
+            zs[o].im = __shfl_sync(0xffffffffu, z[o].im, src);
+        }
+        constexpr int map0[5] = {0, 4, 3, 2, 1}, map1[5] = {4, 3, 2, 1, 0};
+#pragma unroll
+        for (int o = 0; o < NS; ++o) zn[o] = lane == 0 ? zs[map0[o]] : zs[map1[o]];
+    }
     if (!act) return;
 #pragma unroll
     for (int c = 0; c < 8 / G; ++c) {
@@ -779,8 +810,13 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
             else continue;
             const int o = out_slot<G, NS>(c, s1);
             if (o < 0) continue;
-            const CAcc<T> &a = acc[o];
-            Q[(size_t)(pd.row0 + rho + h0) * h1c + m] = mk((T)a.re.value(), (T)a.im.value());
+            if (NS == 5 && pd.kind == PK_OMEGA2) {
+                const cpx<T> a = z[o], b = zn[o];
+                Q[(size_t)(pd.row0 + rho + h0) * h1c + m] = mk((a.re + b.re) * (T)0.5, (a.im - b.im) * (T)0.5);
+                Q[(size_t)(pd.row1 + rho + h0) * h1c + m] = mk((a.im + b.im) * (T)0.5, (b.re - a.re) * (T)0.5);
+            } else {
+                Q[(size_t)(pd.row0 + rho + h0) * h1c + m] = z[o];
+            }
         }
     }
 }
@@ -1242,8 +1278,8 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
     // one group of G lanes per product, whole warps, at most kGatherThreads
     // threads per block; more products go to further blocks along y
     const int max_groups = (ns5 ? kGatherThreads<T, 5>() : kGatherThreads<T, 8>()) / G;
-    const int nchunks = (p->npairs + max_groups - 1) / max_groups;
-    const int per_chunk = (p->npairs + nchunks - 1) / nchunks;
+    const int nchunks = (p->ngpairs + max_groups - 1) / max_groups;
+    const int per_chunk = (p->ngpairs + nchunks - 1) / nchunks;
     int nthr = per_chunk * G;
     nthr = ((nthr + 31) / 32) * 32;
     const int ngroups = nthr / G;
@@ -1259,7 +1295,7 @@ static cudaError_t launch_gather(Plan *p, cudaStream_t s) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     dim3 grid(p->h1c, nchunks);
-    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, nxp, p->nbk, p->npairs, hmax, p->pairs,
+    kern<<<grid, nthr, smem, s>>>(p->n0, p->n1, p->nk, nxp, p->nbk, p->ngpairs, hmax, p->gpairs,
                                   (const cpx<T> *)p->U, (const cpx<T> *)p->xhat, (const cpx<T> *)p->tw0,
                                   (cpx<T> *)p->Q);
     p->launches++;

@@ -20,14 +20,18 @@ constexpr int kSolveTail = 8 + 2 * kMaxSolveGrid;
 // Systems solved together by one launch of the batched solve.
 constexpr int kMaxSolveBatch = 8;
 
-enum PairKind { PK_OMEGA = 0, PK_LAMBDA = 1, PK_THETA = 2 };
+enum PairKind { PK_OMEGA = 0, PK_LAMBDA = 1, PK_THETA = 2, PK_OMEGA2 = 3 };
 
 // One spectrum product transformed in the gather: conj(U_a) * V_b where V_b
 // is an image spectrum (Omega: b = R-term, Theta: b = S) or the 1-D spectrum
 // of x^p (Lambda).  h0 = lag half-range along x.
+// PK_OMEGA2 (gather only): the two auto-products Omega_aa and Omega_bb,
+// whose spectrum products |U_a|^2, |U_b|^2 are real, transformed together as
+// the one complex sequence |U_a|^2 + i |U_b|^2; rows row0 (a) and row1 (b).
 struct PairDesc {
     int kind, a, b, h0;
     int row0;  // first row of this pair in the stage-1 table Q[row][m]
+    int row1;  // PK_OMEGA2: first row of the second auto-product
 };
 
 // Spatial-variation basis (Eq. 2 and 6, or Eq. 7-9).  Kernel term t weights
@@ -85,7 +89,8 @@ struct Plan {
     int L0, L1;            // 2w+1
     int na, nbk;           // split: n0 = na * nbk
     int nimg;              // R-terms + S
-    int npairs, nrows;     // gather pairs; stage-1 rows (sum of 2*h0+1)
+    int npairs, nrows;     // stage-1 products (one per row range); stage-1 rows (sum of 2*h0+1)
+    int ngpairs;           // the gather's product list (auto-products packed in pairs where it can)
     int nmom;              // per-row moment values
     bool fp64;             // compute in double
     size_t csz;            // sizeof(cpx<compute type>)
@@ -101,7 +106,9 @@ struct Plan {
     void *chirp0, *bfilt0, *twpm0;  // Bluestein tables for n0 (noise decorrelation only)
     double *kimg;                   // L0 x L1 kernel image (noise decorrelation)
     // launch shapes chosen by sfft_plan_autotune (0: the built-in choice)
-    int tune_tr, tune_gi, tune_ng, tune_sgrid;
+    // tune_tc: 0 or 1 the solve's tile products on the CUDA cores, 2 on the
+    // tensor cores (FP32 plans only; see solve.cu)
+    int tune_tr, tune_gi, tune_ng, tune_sgrid, tune_tc;
     // basis (see BasisView); the tables are built at plan creation
     int bspline;           // 0 polynomial, 1 B-spline
     int nfx, nfy, nbx, nby;
@@ -129,14 +136,16 @@ struct Plan {
     void *F;               // [(nfy+1)][m][x] row transforms (compute type)
     void *U;               // [nimg][m][lb][r] full spectra, permuted (compute type); reused for Dt
     void *Q;               // [nrows][m] stage-1 results (compute type complex)
-    PairDesc *pairs;       // device copy
+    PairDesc *pairs;       // device copy: npairs products, then the gather's ngpairs (gpairs)
+    PairDesc *gpairs;
     double *rowmom;        // [n0][nmom] per-row moment sums
     double *lag;           // lag tables (Omega, Lambda, Theta), FP64
     int lag_om, lag_la, lag_th;  // offsets into lag
     // solve workspace
     void *A;               // n*n factor (compute type)
     void *Wm;              // n*n: W = L^-1 (compute type)
-    int solve_grid;        // blocks of the cooperative solve kernel (one per SM)
+    int solve_grid;        // blocks of the cooperative solve kernel
+    int solve_grid_tc;     // blocks of its tensor-core variant (one per SM), 0 for FP64
     double *dscale;        // n Jacobi scales
     double *r, *xw;        // n residual, n iterate
     void *zv;              // n vector (compute type)
@@ -207,7 +216,7 @@ cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
 // one cooperative launch (on the grid of plans[0]).
 cudaError_t solve_batch(Plan *const *plans, int count, const double *const *M, const double *const *rhs,
                         double *const *x, sfft_solve_info *const *info, cudaStream_t s);
-int solve_grid_size(bool fp64);
+int solve_grid_size(bool fp64, bool tc = false);
 size_t solve_vec_elems(int n);
 // Solve workspace given by the caller instead of a plan (sizes for n
 // unknowns in the compute type: A, W n*n; zv solve_vec_elems(n); dsc, r n

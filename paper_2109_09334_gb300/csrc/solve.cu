@@ -16,7 +16,8 @@
 //     so the short serial chain stays in the instruction cache).  Phase P
 //     then forms the panel L_ik = A_ik L_kk^-T as 64x32 GEMM tiles; phase U
 //     applies A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64
-//     tiles.
+//     tiles, whose products run on the tensor cores in the FP32 solve
+//     (tcgen05, 3xTF32 split; see tile_gemm_tc).
 //   * W = L^-1 is formed in the same sweep (block forward elimination applied
 //     to the identity): W_kk = L_kk^-1 from the diagonal factorisation, phase
 //     P sets W_k[:, 0:k0] = L_kk^-1 W_k[:, 0:k0] and phase U applies
@@ -120,6 +121,206 @@ __device__ void tile_gemm(T (&acc)[4][4], TileSmem<T> &sm, const T *Ag, int lda,
     }
 }
 
+// ---- the FP32 tile GEMM on the tensor cores (tcgen05, sm_100 family) --------
+// The 64x64x32 tile products of the trailing update run as tcgen05.mma of
+// kind::tf32 (M = N = 64, K = 8 per instruction) with the accumulator in
+// tensor memory.  TF32 keeps 10 mantissa bits, too few for a factor that
+// must seed the FP64 refinement at a Jacobi-scaled condition number near
+// 3e6, so each operand is split as v = hi + lo with hi = tf32(v) and
+// lo = tf32(v - hi) (both rounded to nearest) and the tile product is
+// accumulated as hi*hi + hi*lo + lo*hi ("3xTF32"): the dropped lo*lo term and
+// the rounding of lo are below 2^-21 of each product, close to FP32.
+// Operands are staged through registers into shared memory in the canonical
+// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, the
+// next core matrix along K at +128 bytes (leading byte offset), the next
+// 8-row group at +1024 bytes (stride byte offset, 32 K values per row).  One
+// elected thread issues the 12 MMAs of a tile and commits them to an
+// mbarrier; the block waits on it (bounded by a clock limit), reads the
+// accumulator back with tcgen05.ld and hands it to the caller in the
+// register layout of tile_gemm, through a shared transpose.  In tensor
+// memory an M = 64 accumulator holds row 16 q + l in lane 32 q + l (q < 4,
+// l < 16) and column j in column j.
+constexpr int kTcCols = 64;                    // tensor-memory columns per block
+constexpr long long kTcWaitCycles = 2000000000LL;  // bounded wait on the MMA barrier (~1 s)
+
+struct __align__(1024) TcSmem {
+    float op[4][kTile * kNB];  // a_hi, a_lo, b_hi, b_lo in the canonical K-major layout
+};
+
+// block-wide tensor-core state: the mbarrier, the accumulator's tensor-memory
+// address, the phase of the next completion, and a sticky failure
+struct TcState {
+    uint64_t *mbar;
+    uint32_t tmem;
+    uint32_t phase;
+    bool dead;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// canonical K-major position (floats) of element (row i, k) in a 64 x 32 tile
+__device__ __forceinline__ int tc_pos(int i, int k) { return (((i >> 3) * 8 + (k >> 2)) << 5) + ((i & 7) << 2) + (k & 3); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ float tf32_rn(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// wait for completion `phase` of the mbarrier, at most kTcWaitCycles
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t phase) {
+    const long long t0 = clock64();
+    uint32_t done = 0;
+    while (!done) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(mbar)), "r"(phase));
+        if (!done && clock64() - t0 > kTcWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ void tc_init(TcState &st, uint64_t *mbar, uint32_t *slot) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                     "n"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    st.mbar = mbar;
+    st.tmem = *slot;
+    st.phase = 0;
+    st.dead = false;
+}
+
+__device__ void tc_release(TcState &st) {
+    if (st.dead) tc_wait(st.mbar, st.phase);  // a commit still outstanding: one more bounded wait
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "n"(kTcCols));
+}
+
+// tile_gemm on the tensor cores for one chunk of at most kNB values of k
+// (k1 - k0 <= kNB), same operands and result layout.  Returns false if the
+// MMAs did not complete within the wait limit (acc is then not valid).
+__device__ bool tile_gemm_tc(float (&acc)[4][4], TcSmem &tc, TcState &st, const float *Ag, int lda, int arow0,
+                             int arows, const float *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
+    constexpr int kLd = kTile * kNB / kThreads;
+    const int tid = threadIdx.x, tr = tid / 16, tc16 = tid % 16;
+    const int kn = min(kNB, k1 - k0);
+    // element e = tid + q * kThreads of a 64 x 32 operand is (row, k) with
+    // the lane choosing (row mod 8, k mod 4) and the rest (row / 8, k / 4):
+    // a warp then stores one whole core matrix (32 consecutive words, no
+    // bank conflict) and reads 8 rows x 16 bytes (or 4 k-rows x 32 bytes)
+    float ra[kLd], rb[kLd];
+    int ri[kLd], rk[kLd];
+#pragma unroll
+    for (int q = 0; q < kLd; ++q) {
+        const int e = tid + q * kThreads, l = e & 31, hi = e >> 5;
+        ri[q] = (hi & 7) * 8 + (l >> 2);
+        rk[q] = (hi >> 3) * 4 + (l & 3);
+    }
+#pragma unroll
+    for (int q = 0; q < kLd; ++q) {
+        const int i = ri[q], pp = rk[q];
+        ra[q] = (i < arows && pp < kn) ? Ag[(size_t)(arow0 + i) * lda + k0 + pp] : 0.f;
+        rb[q] = (i < bcols && pp < kn)
+                    ? (transB ? Bg[(size_t)(bcol0 + i) * ldb + k0 + pp] : Bg[(size_t)(k0 + pp) * ldb + bcol0 + i])
+                    : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kLd; ++q) {
+        const int pos = tc_pos(ri[q], rk[q]);
+        const float ah = tf32_rn(ra[q]);
+        tc.op[0][pos] = ah;
+        tc.op[1][pos] = tf32_rn(ra[q] - ah);
+        const float bh = tf32_rn(rb[q]);
+        tc.op[2][pos] = bh;
+        tc.op[3][pos] = tf32_rn(rb[q] - bh);
+    }
+    // the generic-proxy stores must be visible to the tensor core's reads
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0 && !st.dead) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTile >> 3) << 17) |
+                                   ((uint32_t)(kTile >> 4) << 24);
+        const uint32_t a0 = smem_addr(tc.op[0]), a1 = smem_addr(tc.op[1]);
+        const uint32_t b0 = smem_addr(tc.op[2]), b1 = smem_addr(tc.op[3]);
+#pragma unroll
+        for (int ks = 0; ks < kNB / 8; ++ks) {
+            const uint32_t off = ks * 256;  // two core matrices along K per MMA
+            tc_mma(st.tmem, tc_desc(a0 + off), tc_desc(b0 + off), idesc, ks > 0);
+            tc_mma(st.tmem, tc_desc(a0 + off), tc_desc(b1 + off), idesc, 1);
+            tc_mma(st.tmem, tc_desc(a1 + off), tc_desc(b0 + off), idesc, 1);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(st.mbar)));
+    }
+    bool ok = !st.dead;
+    if (ok) {
+        ok = tc_wait(st.mbar, st.phase);
+        st.phase ^= 1u;
+    }
+    // every thread takes the same decision (a timeout is seen by all but is
+    // not guaranteed to be simultaneous): agree before touching the result
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        st.dead = true;
+        return false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // accumulator -> shared transpose (over the operand tiles, whose reads
+    // are complete) -> this thread's 4x4 entries
+    float *Cs = &tc.op[0][0];  // 64 x 65
+    const int warp = tid >> 5, lane = tid & 31, q = warp & 3, h = warp >> 2;
+    uint32_t v[32];
+    const uint32_t taddr = st.tmem + ((uint32_t)(32 * q) << 16) + 32 * h;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (lane < 16) {
+        float *row = Cs + (16 * q + lane) * (kTile + 1) + 32 * h;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) row[c] = __uint_as_float(v[c]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = Cs[(tr * 4 + u) * (kTile + 1) + tc16 + 16 * w];
+    __syncthreads();  // the shared tiles are refilled by the next call
+    return true;
+}
+
 // Shared memory of the diagonal-block factorisation (aliases the GEMM tiles):
 // four columns of S (by row) and four rows of Y (by column) per step,
 // double-buffered by step parity.
@@ -133,6 +334,7 @@ template <typename T>
 union SolveSmem {
     TileSmem<T> tile;
     FactorSmem<T> fac;
+    TcSmem tc;  // FP32 only (the tensor-core tile GEMM)
 };
 
 template <typename T>
@@ -380,8 +582,27 @@ __device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int k
 // the next diagonal block), or a 64x64 tile of the block rows of W below,
 // W_i[:, 0:k0+32] -= L_ik W_k.  The old values are loaded before the GEMM so
 // that the latencies overlap.
-template <typename T>
-__device__ void update_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int base, int ntiles, int ncw, int task) {
+// 64x64 tile product of the update, on the tensor cores in FP32 (3xTF32) or
+// on the CUDA cores in FP64.  A tensor-core wait that timed out flags the
+// system (SFFT_ERR_TIMEOUT) and the tile is computed on the CUDA cores.
+template <typename T, bool TC>
+__device__ __forceinline__ void update_gemm(const SolveArgs<T> &s, T (&acc)[4][4], SolveSmem<T> &sm, TcState &st,
+                                            const T *Ag, int lda, int arow0, int arows, const T *Bg, int ldb,
+                                            int bcol0, int bcols, bool transB) {
+    if constexpr (TC && sizeof(T) == 4) {
+        if (tile_gemm_tc(acc, sm.tc, st, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, transB, 0, kNB)) return;
+        if (threadIdx.x == 0) s.flag[0] = SFFT_ERR_TIMEOUT;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+    }
+    tile_gemm(acc, sm.tile, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, transB, 0, kNB);
+}
+
+template <typename T, bool TC>
+__device__ void update_task(const SolveArgs<T> &s, SolveSmem<T> &smu, TcState &st, int k0, int base, int ntiles,
+                            int ncw, int task) {
     const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
     T acc[4][4] = {};
     T old[4][4];
@@ -397,7 +618,7 @@ __device__ void update_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int 
                 const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
                 old[u][v] = (i < n && j < n && j <= i) ? s.A[(size_t)i * n + j] : (T)0;
             }
-        tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.A + k0, n, j0, nj, true, 0, kNB);
+        update_gemm<T, TC>(s, acc, smu, st, s.A + k0, n, i0, ni, s.A + k0, n, j0, nj, true);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -417,7 +638,7 @@ __device__ void update_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int 
                 old[u][v] = (i < n && j < k0 + kNB) ? s.W[(size_t)i * n + j] : (T)0;
             }
         // a(i, p) = L[i0 + i][k0 + p], b(p, j) = W[k0 + p][j0 + j]
-        tile_gemm(acc, sm, s.A + k0, n, i0, ni, s.W + (size_t)k0 * n, n, j0, nj, false, 0, kNB);
+        update_gemm<T, TC>(s, acc, smu, st, s.A + k0, n, i0, ni, s.W + (size_t)k0 * n, n, j0, nj, false);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -446,11 +667,15 @@ __device__ __forceinline__ int sys_of(const int *offs, int nsys, int task) {
     return b;
 }
 
-template <typename T>
+template <typename T, bool TC>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k_solve_coop(BatchArgs<T> ba) {
     cg::grid_group grid = cg::this_grid();
     __shared__ SolveSmem<T> sm;
     __shared__ double sums[kMaxBatch][2];
+    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ uint32_t tc_slot;
+    TcState st{};
+    if constexpr (TC) tc_init(st, &tc_mbar, &tc_slot);
     const int tid = threadIdx.x, bid = blockIdx.x, nbk = gridDim.x;
     const int gtid = bid * kThreads + tid, gthreads = nbk * kThreads;
     const int warp = tid >> 5, lane = tid & 31, nw = kThreads / 32;
@@ -565,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             const int rows = s.n - base;
             if ((live & (1u << bid)) && rows > 0) {
                 const int nt = (rows + kTile - 1) / kTile;
-                update_task(s, sm.tile, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile, 0);
+                update_task<T, TC>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile, 0);
                 __syncthreads();  // the tile's writes are visible to the block
                 factor_inv(s, sm.fac, kb + 1);
             }
@@ -574,8 +799,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
                 const int b = sys_of(offs, nsys, task);
                 const SolveArgs<T> &s = ba.sys[b];
                 const int nt = (s.n - base + kTile - 1) / kTile;
-                update_task(s, sm.tile, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile,
-                            1 + task - offs[b]);
+                update_task<T, TC>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile,
+                                   1 + task - offs[b]);
             }
         }
         grid.sync();
@@ -697,6 +922,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             s.info->min_pivot = s.stats[0];
         }
     }
+    if constexpr (TC) tc_release(st);
 }
 
 static size_t solve_dyn_smem(bool) { return 0; }
@@ -726,11 +952,11 @@ static SolveArgs<T> system_args(int n, const double *M, const double *rhs, doubl
 }
 
 template <typename T>
-static cudaError_t launch_batch(const BatchArgs<T> &ba, int grid, cudaStream_t st) {
+static cudaError_t launch_batch(const BatchArgs<T> &ba, int grid, cudaStream_t st, bool tc = false) {
     if (grid <= ba.nsys) return cudaErrorInvalidConfiguration;  // blocks >= nsys take the shared tasks
     void *args[] = {(void *)&ba};
-    return cudaLaunchCooperativeKernel((void *)k_solve_coop<T>, grid, kThreads, args, solve_dyn_smem(sizeof(T) == 8),
-                                       st);
+    void *kern = (sizeof(T) == 4 && tc) ? (void *)k_solve_coop<T, true> : (void *)k_solve_coop<T, false>;
+    return cudaLaunchCooperativeKernel(kern, grid, kThreads, args, solve_dyn_smem(sizeof(T) == 8), st);
 }
 
 template <typename T>
@@ -743,8 +969,12 @@ static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *co
         ba.sys[b] = system_args<T>(p->n, M[b], rhs[b], x[b], info[b], p->dscale, p->xw, p->r, p->A, p->Wm, p->zv,
                                    p->flag);
     }
+    // the tensor-core tile variant (tune_tc = 2, FP32 only) allocates tensor
+    // memory, which limits it to one block per SM: its own grid
+    const bool tc = sizeof(T) == 4 && plans[0]->tune_tc == 2 && plans[0]->solve_grid_tc > count;
+    const int full = tc ? plans[0]->solve_grid_tc : plans[0]->solve_grid;
     const int sg = plans[0]->tune_sgrid;
-    const cudaError_t err = launch_batch(ba, (sg > count && sg <= plans[0]->solve_grid) ? sg : plans[0]->solve_grid, st);
+    const cudaError_t err = launch_batch(ba, (sg > count && sg <= full) ? sg : full, st, tc);
     plans[0]->launches += 1;
     return err;
 }
@@ -763,18 +993,18 @@ cudaError_t solve_system(Plan *p, const double *M, const double *rhs, double *x,
     return solve_batch(&p, 1, &M, &rhs, &x, &info, s);
 }
 
-int solve_grid_size(bool fp64) {
+int solve_grid_size(bool fp64, bool tc) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t dsm = solve_dyn_smem(fp64);
-    if (fp64) {
-        cudaFuncSetAttribute(k_solve_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_coop<double>, kThreads, dsm);
-    } else {
-        cudaFuncSetAttribute(k_solve_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_coop<float>, kThreads, dsm);
-    }
+    const void *kern = fp64 ? (const void *)k_solve_coop<double, false>
+                            : (tc ? (const void *)k_solve_coop<float, true> : (const void *)k_solve_coop<float, false>);
+    // all of the unified L1/shared storage as shared memory, so that two FP32
+    // blocks (33 KB of static shared memory each) fit on an SM
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, dsm);
     if (per < 1 || sms < 1) return 0;
     const int g = sms * (per < kBlocksPerSM ? per : kBlocksPerSM);
     return g <= kMaxSolveGrid ? g : 0;

@@ -90,11 +90,12 @@ def test_set_tuning_checks_before_use(lib):
     """Out-of-range launch shapes are rejected before the plan is touched."""
     fake = ctypes.c_void_p(4096)  # never dereferenced: every call below is rejected first
     arr = lambda *v: (ctypes.c_int32 * binding.SFFT_TUNING_LEN)(*v)
-    assert lib.sfft_plan_set_tuning(None, arr(0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_plan_set_tuning(None, arr(0, 0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
     assert lib.sfft_plan_set_tuning(fake, None) == binding.SFFT_ERR_INVALID
-    for bad in ((3, 0, 0, 0), (32, 0, 0, 0), (-1, 0, 0, 0), (0, 5, 0, 0), (0, 0, -1, 0), (0, 0, 0, 513)):
+    for bad in ((3, 0, 0, 0, 0), (32, 0, 0, 0, 0), (-1, 0, 0, 0, 0), (0, 5, 0, 0, 0), (0, 0, -1, 0, 0),
+                (0, 0, 0, 513, 0), (0, 0, 0, 0, 3), (0, 0, 0, 0, -1)):
         assert lib.sfft_plan_set_tuning(fake, arr(*bad)) == binding.SFFT_ERR_INVALID
-    assert lib.sfft_plan_tuning(None, arr(0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_plan_tuning(None, arr(0, 0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
 
 
 def test_misaligned_images_rejected(lib):

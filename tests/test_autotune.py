@@ -27,7 +27,9 @@ def test_autotune_keeps_results_and_is_remembered(shape):
     torch.cuda.synchronize()
     D0, x0 = D0.cpu().numpy(), x0.cpu().numpy()
     shapes = plan.autotune(Rt, St)
-    assert set(shapes) == {"rows_per_block", "images_per_block", "row_pairs_per_block", "solve_grid"}
+    assert set(shapes) == {"rows_per_block", "images_per_block", "row_pairs_per_block", "solve_grid",
+                           "solve_tensor_cores"}
+    assert shapes["solve_tensor_cores"] == 0  # not chosen by the tuner (it rounds differently)
     D1, x1, _, _, _ = plan.run_pair(Rt, St)
     torch.cuda.synchronize()
     assert np.array_equal(D1.cpu().numpy(), D0)
@@ -54,7 +56,7 @@ def test_every_launch_shape_gives_the_same_result(shape):
     D0, x0, _, M0, _ = plan.run_pair(Rt, St, mask, keep_system=True)
     torch.cuda.synchronize()
     D0, x0, M0 = D0.cpu().numpy(), x0.cpu().numpy(), M0.cpu().numpy()
-    for shapes in ([1, 1, 1, 0], [2, 2, 2, 0], [4, 3, 1, 0], [16, 4, 4, 0]):
+    for shapes in ([1, 1, 1, 0, 0], [2, 2, 2, 0, 0], [4, 3, 1, 0, 0], [16, 4, 4, 0, 0]):
         binding.sfft_plan_set_tuning(plan.handle, shapes)
         D1, x1, _, M1, _ = plan.run_pair(Rt, St, mask, keep_system=True)
         torch.cuda.synchronize()
@@ -71,10 +73,10 @@ def test_set_tuning_rejects_bad_shapes():
     plan = SfftPlan(64, 64, 2, 2, 1, 1, 1)
     good = binding.sfft_plan_tuning(plan.handle)
     for bad in ({"rows_per_block": 3}, {"rows_per_block": 32}, {"rows_per_block": -1}, {"images_per_block": 5},
-                {"row_pairs_per_block": -2}, {"solve_grid": 513}):
+                {"row_pairs_per_block": -2}, {"solve_grid": 513}, {"solve_tensor_cores": 3}):
         with pytest.raises(binding.SfftError):
             binding.sfft_plan_set_tuning(plan.handle, bad)
         assert binding.sfft_plan_tuning(plan.handle) == good
-    binding.sfft_plan_set_tuning(plan.handle, [2, 1, 1, 0])
-    assert binding.sfft_plan_tuning(plan.handle) == dict(zip(binding.TUNING_KEYS, [2, 1, 1, 0]))
+    binding.sfft_plan_set_tuning(plan.handle, [2, 1, 1, 0, 0])
+    assert binding.sfft_plan_tuning(plan.handle) == dict(zip(binding.TUNING_KEYS, [2, 1, 1, 0, 0]))
     plan.close()

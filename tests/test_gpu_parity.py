@@ -273,3 +273,34 @@ def test_mask_of_ones_equals_no_mask_and_repeat_is_bitwise():
     np.testing.assert_array_equal(a["x"], c["x"])
     for g in (a, b, c):
         g["plan"].close()
+
+
+@pytest.mark.parametrize("case", [SMALL[3], SMALL[5], SMALL[13]])
+def test_tensor_core_solve_against_oracle(case):
+    """The FP32 solve with its trailing-update tile products on the tensor
+    cores (tcgen05, 3xTF32; launch-shape knob solve_tensor_cores = 2): the
+    same tolerances as the CUDA-core path, and the refinement still
+    converges in at most 4 iterations."""
+    from paper_2109_09334_gb300 import SfftPlan, binding, info_from_bytes
+    n0, n1, w0, w1, dk, db, cpr, masked = case
+    R, S = small_pair(n0, n1, seed=n0 + 3 * n1 + w0)
+    mask = None
+    if masked:
+        mask = (np.random.default_rng(n0).random((n0, n1)) > 0.15).astype(np.uint8)
+    c = oracle.OracleConfig(n0, n1, w0, w1, dk, db, bool(cpr))
+    plan = SfftPlan(n0, n1, w0, w1, dk, db, cpr, dtype="float32", precision="mixed")
+    shapes = binding.sfft_plan_tuning(plan.handle)
+    binding.sfft_plan_set_tuning(plan.handle, dict(shapes, solve_tensor_cores=2))
+    try:
+        Rt = torch.from_numpy(np.ascontiguousarray(R)).to("cuda", torch.float32)
+        St = torch.from_numpy(np.ascontiguousarray(S)).to("cuda", torch.float32)
+        mt = None if mask is None else torch.from_numpy(mask).cuda()
+        D, x, info, M, rhs = plan.run_pair(Rt, St, mask=mt, keep_system=True)
+        torch.cuda.synchronize()
+        g = dict(D=D.double().cpu().numpy(), x=x.cpu().numpy(), M=M.cpu().numpy(), rhs=rhs.cpu().numpy(),
+                 info=info_from_bytes(info.cpu().numpy()))
+        assert g["info"]["iters"] <= 4, g["info"]
+        check_against_oracle(R, S, c, "mixed", mask, g)
+    finally:
+        binding.sfft_plan_set_tuning(plan.handle, dict(shapes, solve_tensor_cores=0))
+        plan.close()
