@@ -4,7 +4,9 @@
 // tables, M, rhs and solve workspace) plus staging buffers for requests in
 // host memory, and three streams:
 //   sc  copies of host requests' inputs to the slot's staging buffers;
-//   sb  the build of each pair (row/column FFTs, gather, lag sums, assembly);
+//   sb  plan set-up; the build of each pair (row/column FFTs, gather, lag
+//       sums, assembly) runs on its slot's own stream, so that builds of
+//       different pairs overlap;
 //   ss  (highest priority) the solves and the subtractions;
 //   so  the copies of the results back to host requests, so that they
 //       overlap the next group's solve and subtractions.
@@ -15,7 +17,7 @@
 // the group's subtractions follow.  The solve is a latency-bound chain of
 // grid-wide steps, so solving several systems in one launch costs little
 // more than solving one.  Events order the streams:
-//   built[i]: sb -> ss (M, rhs of the slot ready);
+//   built[i]: the slot's build stream -> ss (M, rhs of the slot ready);
 //   done[i]:  ss or so -> sb, sc (the slot's previous pair is finished, so
 //             its workspace and staging buffers may be overwritten);
 //   subtracted[i]: ss -> so (a host request's results are ready to copy).
@@ -68,6 +70,9 @@ struct Server {
     size_t img_bytes = 0, pixels = 0;
     Slot slots[kMaxDepth];
     cudaStream_t sc = nullptr, sb = nullptr, ss = nullptr, so = nullptr;
+    // one build stream per slot, so that the builds of different pairs overlap
+    // on the GPU (their small kernels leave most SMs idle)
+    cudaStream_t sbs[kMaxDepth] = {};
     cudaEvent_t input_ready = nullptr;
     cudaEvent_t ring[kRing] = {};
     uint64_t next_seq = 0;   // sequence number of the next request
@@ -105,6 +110,8 @@ void server_free(Server *v) {
     if (v->input_ready) cudaEventDestroy(v->input_ready);
     cudaStream_t sts[] = {v->sc, v->sb, v->ss, v->so};
     for (cudaStream_t s : sts)
+        if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : v->sbs)
         if (s) cudaStreamDestroy(s);
     delete v;
 }
@@ -147,6 +154,8 @@ int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->sb, cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->ss, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&v->so, cudaStreamNonBlocking, lo);
+    for (int i = 0; i < depth && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithPriority(&v->sbs[i], cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->input_ready, cudaEventDisableTiming);
     for (int k = 0; k < kRing && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&v->ring[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -204,8 +213,10 @@ int flush(Server *v) {
         x[k] = s.x;
         info[k] = s.info;
     }
-    // sb is in order: the last build's event covers the earlier ones
-    cudaError_t e = cudaStreamWaitEvent(v->ss, v->slots[(end - 1) % v->depth].built, 0);
+    // the group's builds ran on their slots' streams: wait for each
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < cnt && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(v->ss, v->slots[(first + k) % v->depth].built, 0);
     if (e == cudaSuccess) e = solve_batch(plans, cnt, M, rhs, x, info, v->ss);
     for (int k = 0; k < cnt && e == cudaSuccess; ++k) {
         const uint64_t seq = first + k;
@@ -266,19 +277,20 @@ int submit(Server *v, const sfft_request *r, uint64_t *seq_out) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.sci, r->sci, v->img_bytes, cudaMemcpyHostToDevice, v->sc);
         if (e == cudaSuccess && r->mask) e = cudaMemcpyAsync(s.mask, r->mask, v->pixels, cudaMemcpyHostToDevice, v->sc);
         if (e == cudaSuccess) e = cudaEventRecord(s.copied, v->sc);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, s.copied, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sbs[seq % v->depth], s.copied, 0);
         ref = s.ref;
         sci = s.sci;
         mask = r->mask ? s.mask : nullptr;
     } else {
         // the inputs are ready in the caller's stream order
         e = cudaEventRecord(v->input_ready, (cudaStream_t)r->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, v->input_ready, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sbs[seq % v->depth], v->input_ready, 0);
     }
     // the slot's previous pair has finished with its workspace
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(v->sb, s.done, 0);
-    if (e == cudaSuccess) e = build_system(p, ref, sci, mask, p->M_own, p->rhs_own, v->sb);
-    if (e == cudaSuccess) e = cudaEventRecord(s.built, v->sb);
+    cudaStream_t sb = v->sbs[seq % v->depth];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, s.done, 0);
+    if (e == cudaSuccess) e = build_system(p, ref, sci, mask, p->M_own, p->rhs_own, sb);
+    if (e == cudaSuccess) e = cudaEventRecord(s.built, sb);
     if (e != cudaSuccess) return status_of(e);
     s.host = host;
     s.in_ref = ref;
@@ -426,6 +438,7 @@ int sfft_server_destroy(sfft_server_t server) {
     }
     cudaStreamSynchronize(v->sc);
     cudaStreamSynchronize(v->sb);
+    for (int i = 0; i < v->depth; ++i) cudaStreamSynchronize(v->sbs[i]);
     cudaStreamSynchronize(v->ss);
     cudaStreamSynchronize(v->so);
     server_free(v);
