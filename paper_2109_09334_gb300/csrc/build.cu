@@ -102,21 +102,26 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
     }
     __syncthreads();
     group_fft(zr, n1, -1, tw, gt, G);
-    // separate the two real transforms and write them transposed
+    // separate the two real transforms and write them transposed: thread tid
+    // takes row r = tid mod TR and frequencies m = tid / TR + k * (nthr / TR),
+    // so its addresses advance by constant steps
     const int h1c = n1 / 2 + 1;
-    const int total = h1c * TR;
-    cpx<T> *Fa = F + (size_t)sa * h1c * n0 + x0b;
-    cpx<T> *Fb = F + (size_t)sb * h1c * n0 + x0b;
     const int ltr = __ffs(TR) - 1;  // TR is a power of two
-    for (int idx = tid; idx < total; idx += nthr) {
-        const int m = idx >> ltr, r = idx & (TR - 1);
-        if (x0b + r >= n0) continue;  // rows past the end (n0 not a multiple of TR)
+    const int r = tid & (TR - 1);
+    if (x0b + r < n0) {  // rows past the end (n0 not a multiple of TR)
+        const int mstep = nthr >> ltr;
+        const size_t ostep = (size_t)mstep * n0;
         const cpx<T> *zz = Z + (size_t)r * np;
-        const cpx<T> z = zz[pad16(m)];
-        const cpx<T> zc = conj(zz[pad16((n1 - m) & (n1 - 1))]);
-        const size_t o = (size_t)m * n0 + r;
-        Fa[o] = scale(z + zc, (T)0.5);
-        if (sb < nseq) Fb[o] = mul_i(scale(z - zc, (T)0.5), -1);
+        int m = tid >> ltr;
+        cpx<T> *fa = F + (size_t)sa * h1c * n0 + x0b + r + (size_t)m * n0;
+        cpx<T> *fb = F + (size_t)sb * h1c * n0 + x0b + r + (size_t)m * n0;
+        const bool two = sb < nseq;
+        for (; m < h1c; m += mstep, fa += ostep, fb += ostep) {
+            const cpx<T> z = zz[pad16(m)];
+            const cpx<T> zc = conj(zz[pad16((n1 - m) & (n1 - 1))]);
+            *fa = scale(z + zc, (T)0.5);
+            if (two) *fb = mul_i(scale(z - zc, (T)0.5), -1);
+        }
     }
 }
 
@@ -563,10 +568,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_cols(int n0, int
     const int lna = __ffs(na) - 1, lnb = __ffs(nbk) - 1;
     group_fft(zr, n0, -1, tw, gt, G, lnb, na);
     if (act) {
+        // element o = gt + G k sits at (o / na) (na + 1) + o mod na in the
+        // residue-class layout; with na | G that advances by (G / na)(na + 1)
         cpx<T> *out = U + ((size_t)t * h1c + m) * n0;
-        for (int o = gt; o < n0; o += G) {
-            const int lb = o >> lna, r = o & (na - 1);
-            out[o] = zr[lb * (na + 1) + r];
+        if ((G & (na - 1)) == 0) {
+            const cpx<T> *src = zr + (gt >> lna) * (na + 1) + (gt & (na - 1));
+            const int sstep = (G >> lna) * (na + 1);
+            for (int o = gt; o < n0; o += G, src += sstep) out[o] = *src;
+        } else {
+            for (int o = gt; o < n0; o += G) {
+                const int lb = o >> lna, r = o & (na - 1);
+                out[o] = zr[lb * (na + 1) + r];
+            }
         }
     }
 }
