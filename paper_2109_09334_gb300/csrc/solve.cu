@@ -974,7 +974,17 @@ static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *co
     const bool tc = sizeof(T) == 4 && plans[0]->tune_tc == 2 && plans[0]->solve_grid_tc > count;
     const int full = tc ? plans[0]->solve_grid_tc : plans[0]->solve_grid;
     const int sg = plans[0]->tune_sgrid;
-    const cudaError_t err = launch_batch(ba, (sg > count && sg <= full) ? sg : full, st, tc);
+    int grid = full;
+    if (sg > count && sg <= full) {
+        grid = sg;  // set by hand
+    } else if (count == 1 && !tc && sizeof(T) == 4 && full >= 2 * kMaxSolveBatch) {
+        // one system alone: one block per SM (the step's serial chain, not the
+        // tile throughput, sets its time; 1.12 -> 1.02 ms at n = 1735); several:
+        // every resident block (batches of 8 on 304 blocks measured 561 pairs/s
+        // serving against 515 on 152)
+        grid = full / kBlocksPerSM;
+    }
+    const cudaError_t err = launch_batch(ba, grid, st, tc);
     plans[0]->launches += 1;
     return err;
 }
