@@ -87,6 +87,12 @@ SMALL = [
     (100, 96, 4, 4, 2, 2, 1, False),
     # a half-width above 16: Lambda through the gather, not in closed form
     (64, 96, 2, 20, 1, 1, 1, False),
+    # the size limits: the largest and smallest axes, power of two or not,
+    # and the largest degrees
+    (16, 4096, 1, 3, 2, 2, 1, False),
+    (4096, 16, 3, 1, 1, 1, 0, True),
+    (4093, 17, 2, 2, 1, 1, 1, False),
+    (64, 64, 2, 2, 3, 3, 1, False),
 ]
 
 
@@ -304,3 +310,22 @@ def test_tensor_core_solve_against_oracle(case):
     finally:
         binding.sfft_plan_set_tuning(plan.handle, dict(shapes, solve_tensor_cores=0))
         plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fully_masked_pair_reports_singular(precision):
+    """A mask that hides every pixel leaves the build no data: the kernel
+    columns (built from the masked R) and the right-hand side vanish, only
+    the background block C (Eq. B11, from the unmasked basis functions)
+    remains, and the solve reports SINGULAR instead of coefficients."""
+    from paper_2109_09334_gb300 import binding as B
+    R, S = small_pair(32, 32, 77)
+    dtype = "float64" if precision == "fp64" else "float32"
+    c = oracle.OracleConfig(32, 32, 1, 1, 1, 1, True)
+    g = gpu_run(R, S, 1, 1, 1, 1, 1, precision, dtype, mask=np.zeros((32, 32), np.uint8))
+    assert g["info"]["status"] == B.SFFT_ERR_SINGULAR, g["info"]
+    k = kernel_unknowns(c)
+    assert not np.any(g["M"][k]) and not np.any(g["rhs"])
+    Mo, _ = oracle.build_system(R, S, c, mask=np.zeros((32, 32), np.uint8))
+    assert rel(g["M"], Mo) <= 1e-10
+    g["plan"].close()
