@@ -627,7 +627,7 @@ constexpr int kPad = 8;   // complex elements of padding per image tile / transp
 // the others take up to 48 groups
 template <typename T, int NS>
 __host__ __device__ constexpr int kGatherThreads() { return (sizeof(T) == 4 && NS == 5) ? 224 : 384; }
-constexpr int kFold = 4;  // residue classes per plain partial sum
+constexpr int kFold = 4;  // residue classes per plain partial sum (a power of two)
 
 // NS output slots per lane: 8 in general; 5 when every lag half-range is at most
 // 16 and G = 8 (then only s1 in {0, 1, 2, 6, 7} can be needed).
@@ -695,14 +695,25 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
     constexpr int kPer16 = 16 / (int)sizeof(cpx<T>);
     constexpr int kChunksPerImg = NA / kPer16;
     const int chunks = (nimg + nxp) * kChunksPerImg;
+    // 16-byte chunk c of a residue-class tile: its source for class 0 and its
+    // place in the tile (the source of class lb is lb * NA elements further)
+    auto chunk_src = [&](int c) {
+        const int img = c / kChunksPerImg, r = (c - img * kChunksPerImg) * kPer16;
+        return (img < nimg) ? U + (size_t)img * colstride + (size_t)m * n0 + r : xhat + (size_t)(img - nimg) * n0 + r;
+    };
+    auto chunk_dst = [&](int c) {
+        const int img = c / kChunksPerImg, r = (c - img * kChunksPerImg) * kPer16;
+        return img * NAP + r;
+    };
+    // this thread's first two chunks, kept (most launches have no others)
+    const cpx<T> *src0 = tid < chunks ? chunk_src(tid) : U, *src1 = tid + nthr < chunks ? chunk_src(tid + nthr) : U;
+    const int dst0 = tid < chunks ? chunk_dst(tid) : 0, dst1 = tid + nthr < chunks ? chunk_dst(tid + nthr) : 0;
     auto prefetch = [&](int lb, int buf) {
         cpx<T> *dst = sU + (size_t)buf * tile;
-        for (int c = tid; c < chunks; c += nthr) {
-            const int img = c / kChunksPerImg, r = (c - img * kChunksPerImg) * kPer16;
-            const cpx<T> *src = (img < nimg) ? U + (size_t)img * colstride + (size_t)m * n0 + (size_t)lb * NA + r
-                                             : xhat + (size_t)(img - nimg) * n0 + (size_t)lb * NA + r;
-            cp_async16(dst + (size_t)img * NAP + r, src);
-        }
+        const size_t off = (size_t)lb * NA;
+        if (tid < chunks) cp_async16(dst + dst0, src0 + off);
+        if (tid + nthr < chunks) cp_async16(dst + dst1, src1 + off);
+        for (int c = tid + 2 * nthr; c < chunks; c += nthr) cp_async16(dst + chunk_dst(c), chunk_src(c) + off);
         cp_async_commit();
     };
     prefetch(0, 0);
@@ -738,8 +749,10 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
 #pragma unroll
             for (int s2 = 1; s2 < 8; ++s2) v[s2] = cmul(v[s2], wi[s2]);
             if (G == 8) {
+                // transpose through rows of 9 (8 + 1 pad): constant offsets
+                // from one base per lane, no bank conflicts for 64-bit words
 #pragma unroll
-                for (int s2 = 0; s2 < 8; ++s2) tg[s2 * 8 + (lane ^ s2)] = v[s2];
+                for (int s2 = 0; s2 < 8; ++s2) tg[s2 * 9 + lane] = v[s2];
             } else {
 #pragma unroll
                 for (int s2 = 0; s2 < 8; ++s2) tg[s2 * G + lane] = v[s2];
@@ -752,7 +765,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
             const cpx<T> *wrow_lb = sW + (size_t)lb * wrow + hmax;
             cpx<T> u[G];
 #pragma unroll
-            for (int r1 = 0; r1 < G; ++r1) u[r1] = tg[lane * 8 + (r1 ^ lane)];
+            for (int r1 = 0; r1 < G; ++r1) u[r1] = tg[lane * 9 + r1];
             dftG<T, G>(u, 1);
 #pragma unroll
             for (int o = 0; o < NS; ++o)
@@ -765,7 +778,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
                 const int s2 = lane + G * c;
                 cpx<T> u[G];
 #pragma unroll
-                for (int r1 = 0; r1 < G; ++r1) u[r1] = (G == 8) ? tg[s2 * 8 + (r1 ^ s2)] : tg[s2 * G + r1];
+                for (int r1 = 0; r1 < G; ++r1) u[r1] = (G == 8) ? tg[s2 * 9 + r1] : tg[s2 * G + r1];
                 dftG<T, G>(u, 1);
 #pragma unroll
                 for (int s1 = 0; s1 < G; ++s1) {
@@ -779,7 +792,7 @@ __global__ void __launch_bounds__(kGatherThreads<T, NS>(), (sizeof(T) == 4 && NS
                 }
             }
         }
-        if (act && ((lb % kFold) == kFold - 1 || lb == nbk - 1)) {
+        if (act && ((lb & (kFold - 1)) == kFold - 1 || lb == nbk - 1)) {
 #pragma unroll
             for (int o = 0; o < NS; ++o) {
                 acc[o].add(part[o]);
