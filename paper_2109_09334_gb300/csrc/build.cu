@@ -1023,17 +1023,17 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
     const int nk = bv.nk;
     const int nbt = bv.nb;
     const int h1 = (pd.kind == PK_OMEGA) ? 2 * w1 : w1;
-    const int nr1 = 2 * h1 + 1;
     int nq = 1;
     if (pd.kind == PK_LAMBDA) nq = bv.lamn(pd.b);  // background terms whose x-function is p = b
     const cpx<T> *q = Q + (size_t)row * h1c;
     const double invP = 1.0 / ((double)n0 * (double)n1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // outputs in chunks of up to kS2Out consecutive rho1 of one q index (cpq
-    // chunks per q); warp w takes chunk w % nchr of the round and every
-    // nsp-th slice of the frequencies, nsp = nw / nchr
-    __shared__ Acc<T> part[8][kS2Out];
-    const int cpq = (nr1 + kS2Out - 1) / kS2Out;
+    // outputs in chunks of up to kS2Out lags rho1 >= 0 of one q index, each
+    // with its mirror -rho1 (cpq chunks per q): both come from one twiddle,
+    // Re(v e) and Re(v conj e).  Warp w takes chunk w % nchr of the round and
+    // every nsp-th slice of the frequencies, nsp = nw / nchr
+    __shared__ Acc<T> part[8][2 * kS2Out];
+    const int cpq = (h1 + 1 + kS2Out - 1) / kS2Out;
     const int nch = nq * cpq;
     for (int c0 = 0; c0 < nch; c0 += nw) {
         const int nchr = min(nw, nch - c0);  // chunks in this round
@@ -1041,16 +1041,16 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
         const int ch = c0 + warp % nchr, sp = warp / nchr;
         const bool act = sp < nsp;
         // each lane: plain partial sums over kS2Fold of its frequencies, folded
-        // into two-sum accumulators (one rounding per term, compensated sums)
-        Acc<T> a[kS2Out];
-        T pl[kS2Out];
+        // into two-sum accumulators (one rounding per term, compensated sums);
+        // [k] lag r0 + k, [kS2Out + k] lag -(r0 + k)
+        Acc<T> a[2 * kS2Out];
+        T pl[2 * kS2Out];
 #pragma unroll
-        for (int k = 0; k < kS2Out; ++k) {
+        for (int k = 0; k < 2 * kS2Out; ++k) {
             a[k].zero();
             pl[k] = (T)0;
         }
-        const int qi = ch / cpq, roff = (ch - qi * cpq) * kS2Out;
-        const int r0 = roff - h1;  // first rho1 of the chunk
+        const int qi = ch / cpq, r0 = (ch - qi * cpq) * kS2Out;  // first rho1 >= 0 of the chunk
         if (act) {
             int cnt = 0;
             const int mstep = nsp * 32;
@@ -1066,16 +1066,17 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
                 if (idx0 >= n1) idx0 -= n1;
 #pragma unroll
                 for (int k = 0; k < kS2Out; ++k) {
-                    if (roff + k < nr1) {
+                    if (r0 + k <= h1) {
                         const cpx<T> e = conj(tw1[idx]);
                         pl[k] += v.re * e.re - v.im * e.im;
+                        pl[kS2Out + k] += v.re * e.re + v.im * e.im;
                     }
                     idx += mm;
                     if (idx >= n1) idx -= n1;
                 }
                 if (++cnt == kS2Fold) {
 #pragma unroll
-                    for (int k = 0; k < kS2Out; ++k) {
+                    for (int k = 0; k < 2 * kS2Out; ++k) {
                         a[k].add(pl[k]);
                         pl[k] = (T)0;
                     }
@@ -1083,25 +1084,25 @@ __global__ void k_stage2(int n0, int n1, int w0, int w1, BasisView bv, int npair
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kS2Out; ++k) a[k].add(pl[k]);
+            for (int k = 0; k < 2 * kS2Out; ++k) a[k].add(pl[k]);
         }
 #pragma unroll
-        for (int k = 0; k < kS2Out; ++k)
+        for (int k = 0; k < 2 * kS2Out; ++k)
             for (int s = 16; s > 0; s >>= 1) shfl_add(a[k], s);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < kS2Out; ++k) part[warp][k] = a[k];
+            for (int k = 0; k < 2 * kS2Out; ++k) part[warp][k] = a[k];
         }
         __syncthreads();
         // warps of the same chunk combine their slices in a fixed order
-        if (threadIdx.x < nchr * kS2Out) {
-            const int cc = threadIdx.x / kS2Out, k = threadIdx.x % kS2Out;
+        if (threadIdx.x < nchr * 2 * kS2Out) {
+            const int cc = threadIdx.x / (2 * kS2Out), k = threadIdx.x % (2 * kS2Out);
             const int chw = c0 + cc;
-            const int qo = chw / cpq, rw = (chw - qo * cpq) * kS2Out + k;
+            const int qo = chw / cpq, rr = (chw - qo * cpq) * kS2Out + (k % kS2Out);
             Acc<T> t = part[cc][k];
             for (int sp2 = 1; sp2 < nsp; ++sp2) t.add(part[cc + sp2 * nchr][k]);
-            if (rw < nr1) {
-                const int rho1 = rw - h1;
+            if (rr <= h1 && !(k >= kS2Out && rr == 0)) {
+                const int rho1 = k < kS2Out ? rr : -rr;
                 const double val = t.wide() * invP;
                 size_t idx;
                 if (pd.kind == PK_OMEGA) {

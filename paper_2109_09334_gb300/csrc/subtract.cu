@@ -163,6 +163,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_sub_cols(int n0
         if (P2 || x0 + q < n0) out[q] = acc[q];
 }
 
+// two consecutive complex values from global memory (16-byte aligned for
+// float: one 16-byte load)
+__device__ __forceinline__ void load_pair(const cpx<float> *p, cpx<float> &a, cpx<float> &b) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    a = mk(v.x, v.y);
+    b = mk(v.z, v.w);
+}
+__device__ __forceinline__ void load_pair(const cpx<double> *p, cpx<double> &a, cpx<double> &b) {
+    a = p[0];
+    b = p[1];
+}
+
 // Inverse real FFT of rows: NG groups of G = n1/16 threads per block, each
 // group transforms two rows at once (real and imaginary part of one complex
 // FFT of the Hermitian-extended row spectra).
@@ -181,14 +193,24 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_rows_inv(int n0,
     const cpx<T> *tw = tw1g;  // pass-ordered twiddles, read through L1
     cpx<T> *zr = Z + (size_t)grp * np;
     {
-        // 16 frequencies per thread, all loads in flight
+        // 16 frequencies per thread, all loads in flight; rows xa, xb are
+        // adjacent, so with an even n0 both come in one 2-element load
         cpx<T> A[16], B[16];
+        if (xb < n0 && (n0 & 1) == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const int mm = gt + c * G;
-            const int mr = (mm <= half) ? mm : n1 - mm;
-            A[c] = xa < n0 ? Dt[(size_t)mr * n0 + xa] : mk((T)0, (T)0);
-            B[c] = xb < n0 ? Dt[(size_t)mr * n0 + xb] : mk((T)0, (T)0);
+            for (int c = 0; c < 16; ++c) {
+                const int mm = gt + c * G;
+                const int mr = (mm <= half) ? mm : n1 - mm;
+                load_pair(Dt + (size_t)mr * n0 + xa, A[c], B[c]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int mm = gt + c * G;
+                const int mr = (mm <= half) ? mm : n1 - mm;
+                A[c] = xa < n0 ? Dt[(size_t)mr * n0 + xa] : mk((T)0, (T)0);
+                B[c] = xb < n0 ? Dt[(size_t)mr * n0 + xb] : mk((T)0, (T)0);
+            }
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
