@@ -126,7 +126,11 @@ int sfft_num_unknowns(const sfft_config *cfg, int32_t *n);
  */
 int sfft_plan_create(const sfft_config *cfg, sfft_stream_t stream, sfft_plan_t *out);
 
-/* Synchronises the plan's last stream, then frees its workspace. NULL is a no-op. */
+/*
+ * Waits for all work on the device (the plan's buffers may be in use on any
+ * stream the caller gave it, or in a captured batch), then frees its
+ * workspace.  NULL is a no-op.
+ */
 int sfft_plan_destroy(sfft_plan_t plan);
 
 /* Device bytes the plan holds. */

@@ -11,7 +11,9 @@ only provides device memory and streams).
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
+import weakref
 
 from . import binding
 from .binding import make_request  # noqa: F401
@@ -46,6 +48,30 @@ def _torch():
     return torch
 
 
+_live = weakref.WeakSet()  # objects that hold library handles
+_registered = False
+
+
+def _close_all():
+    """Release the handles still open (batches, servers and pools before
+    plans) while torch and the CUDA runtime are still up."""
+    for o in sorted(list(_live), key=lambda o: isinstance(o, SfftPlan)):
+        try:
+            o.close()
+        except Exception:
+            pass
+
+
+def _track(obj):
+    # registered with the first object, after torch is imported, so that it
+    # runs before torch's own exit handlers
+    global _registered
+    if not _registered:
+        atexit.register(_close_all)
+        _registered = True
+    _live.add(obj)
+
+
 def info_from_bytes(buf):
     """Parse a 24-byte sfft_solve_info copied to the host."""
     raw = bytes(buf)
@@ -65,6 +91,7 @@ class SfftPlan:
         self.n = sfft_num_unknowns(self.cfg)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = sfft_plan_create(self.cfg, self.stream)
+        _track(self)
         self.shape = (n0, n1)
         self.dtype = {"float32": torch.float32, "f32": torch.float32,
                       "float64": torch.float64, "f64": torch.float64}[str(dtype)]
@@ -203,6 +230,7 @@ class SfftBatch:
                      for p in plans]
         self.handle = binding.sfft_batch_create([p.handle for p in plans], self.refs, self.scis, self.masks,
                                                 self.x, self.info, self.D, solve_group)
+        _track(self)
 
     @property
     def info_dict(self):
@@ -244,6 +272,7 @@ class SfftServer:
         self.dtype = {"float32": torch.float32, "f32": torch.float32,
                       "float64": torch.float64, "f64": torch.float64}[str(dtype)]
         self.handle = sfft_server_create(self.cfg, depth, batch)
+        _track(self)
         self._pending = {}
         if eager:
             binding.sfft_server_set_eager(self.handle, True)
@@ -324,6 +353,7 @@ class SfftPool:
 
     def __init__(self, budget_bytes, depth=2, batch=1, eager=False):
         self.handle = binding.sfft_pool_create(budget_bytes, depth, batch)
+        _track(self)
         self._keep = {}
         if eager:
             binding.sfft_pool_set_eager(self.handle, True)

@@ -504,7 +504,8 @@ int sfft_plan_create(const sfft_config *cfg, sfft_stream_t stream, sfft_plan_t *
 int sfft_plan_destroy(sfft_plan_t plan) {
     if (!plan) return SFFT_OK;
     Plan *p = (Plan *)plan;
-    cudaStreamSynchronize(p->last_stream);
+    // the streams the plan last ran on may have been destroyed since
+    cudaDeviceSynchronize();
     plan_free(p);
     return SFFT_OK;
 }
@@ -844,6 +845,10 @@ int sfft_batch_create(const sfft_plan_t *plans, int32_t count, const void *const
     sfft_batch_s *b = new (std::nothrow) sfft_batch_s();
     if (!b) return SFFT_ERR_OOM;
     b->count = count;
+    // the capture runs on a stream of its own, destroyed below: the plans
+    // keep the stream they last ran on
+    std::vector<cudaStream_t> prev(count);
+    for (int i = 0; i < count; ++i) prev[i] = ((Plan *)plans[i])->last_stream;
     cudaStream_t cs = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e == cudaSuccess && solve_group > 0) {
@@ -893,6 +898,7 @@ int sfft_batch_create(const sfft_plan_t *plans, int32_t count, const void *const
         if (e == cudaSuccess) e = es;
         cudaStreamDestroy(cs);
     }
+    for (int i = 0; i < count; ++i) ((Plan *)plans[i])->last_stream = prev[i];
     if (e != cudaSuccess) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         delete b;

@@ -56,68 +56,130 @@ struct SolveArgs {
     sfft_solve_info *info;
 };
 
+// Both operands of a tile product are staged with k contiguous, rows of
+// kNB + 4 values: groups of four k are 16-byte aligned for vector loads, and
+// rows 1 apart start 4 banks apart.
 template <typename T>
-struct TileSmem {
-    T a[kTile][kNB + 1];
-    T b[kNB][kTile + 1];
+struct __align__(16) TileSmem {
+    T a[kTile][kNB + 4];   // a(i, p)
+    T bt[kTile][kNB + 4];  // b(p, j) at bt[j][p]
 };
+
+// four consecutive values of shared memory (16-byte aligned)
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
+// Operands of one 32-deep chunk of a 64x64 tile product, loaded into
+// registers (kLdOps elements of each per thread): all loads of a chunk are
+// in flight before the first store to shared memory.
+constexpr int kLdOps = kTile * kNB / kThreads;
+template <typename T>
+struct TileOps {
+    T ra[kLdOps], rb[kLdOps];
+};
+
+// Element e of a 64 x 32 operand read from a k-major (row-major in k) source:
+// a warp takes 8 consecutive j (32-byte segments) of 4 consecutive k, so the
+// transposing store to bt[j][k] is free of bank conflicts.
+__device__ __forceinline__ void op_rowmajor_pos(int e, int &j, int &p) {
+    const int l = e & 31, hi = e >> 5;
+    j = (hi & 7) * 8 + (l >> 2);
+    p = (hi >> 3) * 4 + (l & 3);
+}
+
+// chunk [kk, kk + kn) of the operands of tile_gemm (same a, b, bounds)
+template <bool TB, typename T>
+__device__ __forceinline__ void tile_load(TileOps<T> &o, const T *Ag, int lda, int arow0, int arows, const T *Bg,
+                                          int ldb, int bcol0, int bcols, int kk, int kn) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kLdOps; ++q) {
+        const int e = tid + q * kThreads, i = e / kNB, p = e % kNB;
+        o.ra[q] = (i < arows && p < kn) ? Ag[(size_t)(arow0 + i) * lda + kk + p] : (T)0;
+    }
+    if constexpr (TB) {
+#pragma unroll
+        for (int q = 0; q < kLdOps; ++q) {
+            const int e = tid + q * kThreads, j = e / kNB, p = e % kNB;
+            o.rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(bcol0 + j) * ldb + kk + p] : (T)0;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kLdOps; ++q) {
+            int j, p;
+            op_rowmajor_pos(tid + q * kThreads, j, p);
+            o.rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(kk + p) * ldb + bcol0 + j] : (T)0;
+        }
+    }
+}
+
+// acc += the product of one loaded chunk: stage it in shared memory, then
+// each thread accumulates its 4x4 outputs (rows 4 tr + u, columns tc + 16 v)
+// over the 32 values of k in order, reading four k at a time per row
+template <bool TB, typename T>
+__device__ __forceinline__ void tile_mul(T (&acc)[4][4], TileSmem<T> &sm, const TileOps<T> &o) {
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+#pragma unroll
+    for (int q = 0; q < kLdOps; ++q) {
+        const int e = tid + q * kThreads;
+        sm.a[e / kNB][e % kNB] = o.ra[q];
+        if constexpr (TB) {
+            sm.bt[e / kNB][e % kNB] = o.rb[q];
+        } else {
+            int j, p;
+            op_rowmajor_pos(e, j, p);
+            sm.bt[j][p] = o.rb[q];
+        }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int p4 = 0; p4 < kNB; p4 += 4) {
+        T av[4][4], bv[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld4(&sm.a[tr * 4 + u][p4], av[u]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ld4(&sm.bt[tc + 16 * v][p4], bv[v]);
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u][pp] * bv[v][pp];
+    }
+    __syncthreads();
+}
 
 // 64x64 tile:  acc(i, j) += sum_{k0 <= k < k1} a(i, k) b(k, j)
 //   a(i, k) = Ag[(arow0 + i) * lda + k]
 //   b(k, j) = transB ? Bg[(bcol0 + j) * ldb + k] : Bg[k * ldb + bcol0 + j]
-// rows i >= arows and columns j >= bcols read as zero.
+// rows i >= arows and columns j >= bcols read as zero.  All loads of a
+// 32-deep chunk are issued before the first store to shared memory, so that
+// their latencies overlap.
 template <typename T>
 __device__ void tile_gemm(T (&acc)[4][4], TileSmem<T> &sm, const T *Ag, int lda, int arow0, int arows,
                           const T *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
-    constexpr int kLd = kTile * kNB / kThreads;  // elements of each operand per thread
-    const int tid = threadIdx.x;
-    const int tr = tid / 16, tc = tid % 16;
     for (int kk = k0; kk < k1; kk += kNB) {
-        const int kn = min(kNB, k1 - kk);
-        // all loads of the chunk are issued before the first store to shared
-        // memory, so that their latencies overlap
-        T ra[kLd], rb[kLd];
-#pragma unroll
-        for (int q = 0; q < kLd; ++q) {
-            const int e = tid + q * kThreads, i = e / kNB, p = e % kNB;
-            ra[q] = (i < arows && p < kn) ? Ag[(size_t)(arow0 + i) * lda + kk + p] : (T)0;
-        }
+        TileOps<T> o;
         if (transB) {
-#pragma unroll
-            for (int q = 0; q < kLd; ++q) {
-                const int e = tid + q * kThreads, j = e / kNB, p = e % kNB;
-                rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(bcol0 + j) * ldb + kk + p] : (T)0;
-            }
+            tile_load<true>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kNB, k1 - kk));
+            tile_mul<true>(acc, sm, o);
         } else {
-#pragma unroll
-            for (int q = 0; q < kLd; ++q) {
-                const int e = tid + q * kThreads, p = e / kTile, j = e % kTile;
-                rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(kk + p) * ldb + bcol0 + j] : (T)0;
-            }
+            tile_load<false>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kNB, k1 - kk));
+            tile_mul<false>(acc, sm, o);
         }
-#pragma unroll
-        for (int q = 0; q < kLd; ++q) {
-            const int e = tid + q * kThreads;
-            sm.a[e / kNB][e % kNB] = ra[q];
-            if (transB)
-                sm.b[e % kNB][e / kNB] = rb[q];
-            else
-                sm.b[e / kTile][e % kTile] = rb[q];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int p = 0; p < kNB; ++p) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) av[u] = sm.a[tr * 4 + u][p];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) bv[v] = sm.b[p][tc + 16 * v];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
-        }
-        __syncthreads();
     }
 }
 
@@ -226,7 +288,7 @@ __device__ void tc_release(TcState &st) {
 // MMAs did not complete within the wait limit (acc is then not valid).
 __device__ bool tile_gemm_tc(float (&acc)[4][4], TcSmem &tc, TcState &st, const float *Ag, int lda, int arow0,
                              int arows, const float *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
-    constexpr int kLd = kTile * kNB / kThreads;
+    constexpr int kLd = kLdOps;
     const int tid = threadIdx.x, tr = tid / 16, tc16 = tid % 16;
     const int kn = min(kNB, k1 - k0);
     // element e = tid + q * kThreads of a 64 x 32 operand is (row, k) with
@@ -342,22 +404,6 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int q) {
     return q == 0 ? v[0] : (q == 1 ? v[1] : (q == 2 ? v[2] : v[3]));
 }
 
-// four consecutive values of shared memory (16-byte aligned)
-__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    o[0] = v.x;
-    o[1] = v.y;
-    o[2] = v.z;
-    o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
-    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-    o[0] = a.x;
-    o[1] = a.y;
-    o[2] = b.x;
-    o[3] = b.y;
-}
-
 // 1 / sqrt(d): the FP32 factor only seeds the FP64 refinement, so the
 // hardware approximation serves; FP64 takes the correctly rounded path.
 __device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
@@ -384,7 +430,7 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb) {
     for (int q = 0; q < 4; ++q) {
         const int c = u + 8 * q;
         T v = (T)0;
-        if (t < nb && c < nb) v = s.A[(size_t)(k0 + t) * n + k0 + c];
+        if (t < nb && c <= t) v = s.A[(size_t)(k0 + t) * n + k0 + c];  // the lower triangle only
         else if (t == c) v = (T)1;  // identity beyond the matrix edge
         sv[q] = v;
         yv[q] = (t == c) ? (T)1 : (T)0;
@@ -580,72 +626,144 @@ __device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int k
 // Phase U task `task` of one system at panel k0: a 64x64 tile of the
 // trailing lower triangle, A_ij -= L_ik L_jk^T (task < ntiles; task 0 holds
 // the next diagonal block), or a 64x64 tile of the block rows of W below,
-// W_i[:, 0:k0+32] -= L_ik W_k.  The old values are loaded before the GEMM so
-// that the latencies overlap.
-// 64x64 tile product of the update, on the tensor cores in FP32 (3xTF32) or
-// on the CUDA cores in FP64.  A tensor-core wait that timed out flags the
-// system (SFFT_ERR_TIMEOUT) and the tile is computed on the CUDA cores.
-template <typename T, bool TC>
-__device__ __forceinline__ void update_gemm(const SolveArgs<T> &s, T (&acc)[4][4], SolveSmem<T> &sm, TcState &st,
-                                            const T *Ag, int lda, int arow0, int arows, const T *Bg, int ldb,
-                                            int bcol0, int bcols, bool transB) {
-    if constexpr (TC && sizeof(T) == 4) {
-        if (tile_gemm_tc(acc, sm.tc, st, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, transB, 0, kNB)) return;
-        if (threadIdx.x == 0) s.flag[0] = SFFT_ERR_TIMEOUT;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+// W_i[:, 0:k0+32] -= L_ik W_k.  Columns k0..k0+31 of W below the diagonal
+// block are first written by this step, so their old values are zero and
+// are not read (W is never cleared).
+template <typename T>
+struct UpdTile {
+    int i0, j0, ni, nj;
+    bool wtile;     // a tile of W (else of A)
+    TileOps<T> op;  // operands of the product, loaded ahead of it
+};
+
+template <typename T>
+__device__ __forceinline__ void upd_desc(UpdTile<T> &u, const SolveArgs<T> &s, int k0, int base, int ntiles, int ncw,
+                                         int task) {
+    const int n = s.n;
+    u.wtile = task >= ntiles;
+    if (!u.wtile) {
+        int ti, tj;
+        lower_tile(task, &ti, &tj);
+        u.i0 = base + ti * kTile;
+        u.j0 = base + tj * kTile;
+        u.nj = min(kTile, n - u.j0);
+    } else {
+        const int q = task - ntiles;
+        u.i0 = base + (q / ncw) * kTile;
+        u.j0 = (q % ncw) * kTile;
+        u.nj = min(kTile, k0 + kNB - u.j0);
     }
-    tile_gemm(acc, sm.tile, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, transB, 0, kNB);
+    u.ni = min(kTile, n - u.i0);
 }
 
+// a(i, p) = L[i0 + i][k0 + p]; b(p, j) = L[j0 + j][k0 + p] (A tile) or
+// W[k0 + p][j0 + j] (W tile)
+template <bool WT, typename T>
+__device__ __forceinline__ void upd_load(UpdTile<T> &u, const SolveArgs<T> &s, int k0) {
+    const int n = s.n;
+    tile_load<!WT>(u.op, s.A + k0, n, u.i0, u.ni, WT ? s.W + (size_t)k0 * n : s.A + k0, n, u.j0, u.nj, 0, kNB);
+}
+
+// element (i, j) of the tile is stored (A: lower triangle; W: columns below k0 + 32)
+template <bool WT>
+__device__ __forceinline__ bool upd_in(int n, int k0, int i, int j) {
+    return i < n && (WT ? j < k0 + kNB : (j < n && j <= i));
+}
+
+template <bool WT, typename T>
+__device__ __forceinline__ void upd_old(const UpdTile<T> &u, const SolveArgs<T> &s, int k0, T (&old)[4][4]) {
+    const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    const T *C = WT ? s.W : s.A;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
+            old[a][v] = (upd_in<WT>(n, k0, i, j) && !(WT && j >= k0)) ? C[(size_t)i * n + j] : (T)0;
+        }
+}
+
+template <bool WT, typename T>
+__device__ __forceinline__ void upd_store(const UpdTile<T> &u, const SolveArgs<T> &s, int k0, const T (&old)[4][4],
+                                          const T (&acc)[4][4]) {
+    const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    T *C = WT ? s.W : s.A;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
+            if (upd_in<WT>(n, k0, i, j)) C[(size_t)i * n + j] = old[a][v] - acc[a][v];
+        }
+}
+
+// the tile whose operands are in u.op: old values (their loads overlap the
+// product), product on the CUDA cores, store
+template <bool WT, typename T>
+__device__ __forceinline__ void upd_finish(const UpdTile<T> &u, const SolveArgs<T> &s, TileSmem<T> &sm, int k0) {
+    T old[4][4], acc[4][4] = {};
+    upd_old<WT>(u, s, k0, old);
+    tile_mul<!WT>(acc, sm, u.op);
+    upd_store<WT>(u, s, k0, old, acc);
+}
+
+// One task on its own.  The tensor-core variant takes the tile product on
+// the tensor cores in FP32 (3xTF32); a tensor-core wait that timed out flags
+// the system (SFFT_ERR_TIMEOUT) and the tile is computed on the CUDA cores.
 template <typename T, bool TC>
 __device__ void update_task(const SolveArgs<T> &s, SolveSmem<T> &smu, TcState &st, int k0, int base, int ntiles,
                             int ncw, int task) {
-    const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
-    T acc[4][4] = {};
-    T old[4][4];
-    if (task < ntiles) {
-        int ti, tj;
-        lower_tile(task, &ti, &tj);
-        const int i0 = base + ti * kTile, j0 = base + tj * kTile;
-        const int ni = min(kTile, n - i0), nj = min(kTile, n - j0);
+    UpdTile<T> u;
+    upd_desc(u, s, k0, base, ntiles, ncw, task);
+    if constexpr (TC && sizeof(T) == 4) {
+        const int n = s.n;
+        T old[4][4], acc[4][4] = {};
+        if (u.wtile)
+            upd_old<true>(u, s, k0, old);
+        else
+            upd_old<false>(u, s, k0, old);
+        const T *Bg = u.wtile ? s.W + (size_t)k0 * n : s.A + k0;
+        if (!tile_gemm_tc(acc, smu.tc, st, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, 0, kNB)) {
+            if (threadIdx.x == 0) s.flag[0] = SFFT_ERR_TIMEOUT;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                old[u][v] = (i < n && j < n && j <= i) ? s.A[(size_t)i * n + j] : (T)0;
-            }
-        update_gemm<T, TC>(s, acc, smu, st, s.A + k0, n, i0, ni, s.A + k0, n, j0, nj, true);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                if (i < n && j < n && j <= i) s.A[(size_t)i * n + j] = old[u][v] - acc[u][v];
-            }
+                for (int v = 0; v < 4; ++v) acc[a][v] = (T)0;
+            tile_gemm(acc, smu.tile, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, 0, kNB);
+        }
+        if (u.wtile)
+            upd_store<true>(u, s, k0, old, acc);
+        else
+            upd_store<false>(u, s, k0, old, acc);
+    } else if (u.wtile) {
+        upd_load<true>(u, s, k0);
+        upd_finish<true>(u, s, smu.tile, k0);
     } else {
-        const int q = task - ntiles, ti = q / ncw, tj = q % ncw;
-        const int i0 = base + ti * kTile, j0 = tj * kTile;
-        const int ni = min(kTile, n - i0), nj = min(kTile, k0 + kNB - j0);
+        upd_load<false>(u, s, k0);
+        upd_finish<false>(u, s, smu.tile, k0);
+    }
+}
+
+// row i of A = D M D up to the diagonal, eight loads of each operand in flight per lane
+template <typename T>
+__device__ __forceinline__ void scale_row(const SolveArgs<T> &s, int i, int lane) {
+    const int n = s.n;
+    const double di = s.dsc[i];
+    const double *Mi = s.M + (size_t)i * n;
+    T *Ai = s.A + (size_t)i * n;
+    for (int j0 = lane; j0 <= i; j0 += 8 * 32) {
+        double m[8], d[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + 32 * q;
+            m[q] = j <= i ? Mi[j] : 0.0;
+            d[q] = j <= i ? s.dsc[j] : 0.0;
+        }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                old[u][v] = (i < n && j < k0 + kNB) ? s.W[(size_t)i * n + j] : (T)0;
-            }
-        // a(i, p) = L[i0 + i][k0 + p], b(p, j) = W[k0 + p][j0 + j]
-        update_gemm<T, TC>(s, acc, smu, st, s.A + k0, n, i0, ni, s.W + (size_t)k0 * n, n, j0, nj, false);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int i = i0 + tr * 4 + u, j = j0 + tc + 16 * v;
-                if (i < n && j < k0 + kNB) s.W[(size_t)i * n + j] = old[u][v] - acc[u][v];
-            }
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + 32 * q;
+            if (j <= i) Ai[j] = (T)(m[q] * di * d[q]);
+        }
     }
 }
 
@@ -707,31 +825,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             s.dsc[i] = (d > 0.0) ? 1.0 / sqrt(d) : 0.0;
             s.x[i] = 0.0;
         }
-        for (size_t e = gtid; e < (size_t)n * n; e += gthreads) s.W[e] = (T)0;
+    }
+    int wofs[kMaxBatch + 1];  // flat W^T y tasks of all systems
+    int yofs[kMaxBatch + 1];  // flat row-pair tasks (k, n - 1 - k) of all systems
+    wofs[0] = yofs[0] = 0;
+    for (int b = 0; b < nsys; ++b) {
+        wofs[b + 1] = wofs[b] + ((ba.sys[b].n + 31) / 32) * kSeg;
+        yofs[b + 1] = yofs[b] + (ba.sys[b].n + 1) / 2;
     }
     grid.sync();
-    for (int row = bid; row < nrows_all; row += nbk) {
-        const int b = sys_of(nrow, nsys, row), i = row - nrow[b];
+    // A = D M D on the lower triangle (nothing reads the upper one), one warp
+    // per row pair (k, n - 1 - k)
+    for (int task = bid * nw + warp; task < yofs[nsys]; task += nbk * nw) {
+        const int b = sys_of(yofs, nsys, task), k = task - yofs[b];
         const SolveArgs<T> &s = ba.sys[b];
-        const int n = s.n;
-        const double di = s.dsc[i];
-        const double *Mi = s.M + (size_t)i * n;
-        T *Ai = s.A + (size_t)i * n;
-        // four independent loads in flight before the stores
-        for (int j0 = tid; j0 < n; j0 += 4 * kThreads) {
-            double m[4], d[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + q * kThreads;
-                m[q] = j < n ? Mi[j] : 0.0;
-                d[q] = j < n ? s.dsc[j] : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = j0 + q * kThreads;
-                if (j < n) Ai[j] = (T)(m[q] * di * d[q]);
-            }
-        }
+        scale_row(s, k, lane);
+        if (s.n - 1 - k != k) scale_row(s, s.n - 1 - k, lane);
     }
     grid.sync();
 
@@ -821,13 +930,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         if (lane == 0) sums[warp][1] = bb;
     }
     __syncthreads();
-    int wofs[kMaxBatch + 1];  // flat W^T y tasks of all systems
-    int yofs[kMaxBatch + 1];  // flat W z tasks (row pairs) of all systems
-    wofs[0] = yofs[0] = 0;
-    for (int b = 0; b < nsys; ++b) {
-        wofs[b + 1] = wofs[b] + ((ba.sys[b].n + 31) / 32) * kSeg;
-        yofs[b + 1] = yofs[b] + (ba.sys[b].n + 1) / 2;
-    }
     for (int it = 0; it <= kMaxIters && done != all; ++it) {
         // r = rhs - M x (FP64); z = D r
         for (int row = bid * nw + warp; row < nrows_all; row += nbk * nw) {
