@@ -10,10 +10,10 @@
 // Everything runs in one cooperative (grid-synchronised) kernel with two
 // blocks per SM, so the ~n/32 dependent block steps cost a grid barrier each
 // instead of a kernel launch:
-//   * Cholesky, right-looking with 32-wide panels.  The block that updates
-//     the tile holding the next diagonal block factors it right away and
-//     inverts the factor in the same sweep (rolled loops in shared memory,
-//     so the short serial chain stays in the instruction cache).  Phase P
+//   * Cholesky, right-looking with 32-wide panels.  One block applies the
+//     last update to the next diagonal block itself, factors it right away
+//     and inverts the factor in the same sweep (rolled loops in shared
+//     memory, so the short serial chain stays in the instruction cache).  Phase P
 //     then forms the panel L_ik = A_ik L_kk^-T as 64x32 GEMM tiles; phase U
 //     applies A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64
 //     tiles, whose products run on the tensor cores in the FP32 solve
@@ -390,6 +390,7 @@ template <typename T>
 struct __align__(16) FactorSmem {
     T col[2][kNB][4];
     T row[2][kNB][4];
+    T lp[kNB][kNB + 1];  // the panel rows of the block's last update
 };
 
 template <typename T>
@@ -409,8 +410,11 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int q) {
 __device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
 __device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 
-// The whole block factors the 32x32 diagonal block kb (already fully
-// updated) and inverts its factor in the same sweep, four columns per step:
+// The whole block factors the 32x32 diagonal block kb and inverts its factor
+// in the same sweep, four columns per step.  With kp >= 0 the block first
+// applies the last update of the diagonal block itself, S = A_kk - L L^T with
+// L = A[k0:k0+32, kp:kp+32] (the panel of step kp), in the operation order of
+// the trailing-update tiles; with kp < 0 A_kk is already fully updated.  Then:
 // every thread factors the 4x4 pivot block itself, forms the L entries of the
 // rows it needs by forward substitution, and applies the rank-4 update to S
 // and the matching block forward elimination to Y (L Y = I, so Y ends as
@@ -420,7 +424,7 @@ __device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 // Writes L_kk into A and L_kk^-1 into W (zeros above the diagonal) and flags
 // a non-positive pivot.
 template <typename T>
-__device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb) {
+__device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int kp) {
     const int tid = threadIdx.x;
     const int n = s.n, k0 = kb * kNB;
     const int nb = min(kNB, n - k0);
@@ -434,6 +438,24 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb) {
         else if (t == c) v = (T)1;  // identity beyond the matrix edge
         sv[q] = v;
         yv[q] = (t == c) ? (T)1 : (T)0;
+    }
+    if (kp >= 0) {
+#pragma unroll
+        for (int q = 0; q < kNB * kNB / kThreads; ++q) {
+            const int e = tid + q * kThreads, r = e / kNB, p = e % kNB;
+            f.lp[r][p] = r < nb ? s.A[(size_t)(k0 + r) * n + kp + p] : (T)0;
+        }
+        __syncthreads();
+        T acc[4] = {};
+#pragma unroll 8
+        for (int p = 0; p < kNB; ++p) {
+            const T a = f.lp[t][p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += a * f.lp[u + 8 * q][p];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (t < nb && u + 8 * q <= t) sv[q] = sv[q] - acc[q];
     }
     if (u < 4) f.col[0][t][u] = sv[0];
     if (t < 4) {
@@ -625,13 +647,15 @@ __device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int k
 
 // Phase U task `task` of one system at panel k0: a 64x64 tile of the
 // trailing lower triangle, A_ij -= L_ik L_jk^T (task < ntiles; task 0 holds
-// the next diagonal block), or a 64x64 tile of the block rows of W below,
+// the next diagonal block, whose update factor_inv applies itself, so that
+// tile stores only its rows below it), or a 64x64 tile of the block rows of W below,
 // W_i[:, 0:k0+32] -= L_ik W_k.  Columns k0..k0+31 of W below the diagonal
 // block are first written by this step, so their old values are zero and
 // are not read (W is never cleared).
 template <typename T>
 struct UpdTile {
     int i0, j0, ni, nj;
+    int rmin;       // first row stored
     bool wtile;     // a tile of W (else of A)
     TileOps<T> op;  // operands of the product, loaded ahead of it
 };
@@ -654,6 +678,7 @@ __device__ __forceinline__ void upd_desc(UpdTile<T> &u, const SolveArgs<T> &s, i
         u.nj = min(kTile, k0 + kNB - u.j0);
     }
     u.ni = min(kTile, n - u.i0);
+    u.rmin = (task == 0) ? base + kNB : u.i0;
 }
 
 // a(i, p) = L[i0 + i][k0 + p]; b(p, j) = L[j0 + j][k0 + p] (A tile) or
@@ -666,8 +691,8 @@ __device__ __forceinline__ void upd_load(UpdTile<T> &u, const SolveArgs<T> &s, i
 
 // element (i, j) of the tile is stored (A: lower triangle; W: columns below k0 + 32)
 template <bool WT>
-__device__ __forceinline__ bool upd_in(int n, int k0, int i, int j) {
-    return i < n && (WT ? j < k0 + kNB : (j < n && j <= i));
+__device__ __forceinline__ bool upd_in(int n, int k0, int rmin, int i, int j) {
+    return i < n && i >= rmin && (WT ? j < k0 + kNB : (j < n && j <= i));
 }
 
 template <bool WT, typename T>
@@ -679,7 +704,7 @@ __device__ __forceinline__ void upd_old(const UpdTile<T> &u, const SolveArgs<T> 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
-            old[a][v] = (upd_in<WT>(n, k0, i, j) && !(WT && j >= k0)) ? C[(size_t)i * n + j] : (T)0;
+            old[a][v] = (upd_in<WT>(n, k0, u.rmin, i, j) && !(WT && j >= k0)) ? C[(size_t)i * n + j] : (T)0;
         }
 }
 
@@ -693,7 +718,7 @@ __device__ __forceinline__ void upd_store(const UpdTile<T> &u, const SolveArgs<T
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
-            if (upd_in<WT>(n, k0, i, j)) C[(size_t)i * n + j] = old[a][v] - acc[a][v];
+            if (upd_in<WT>(n, k0, u.rmin, i, j)) C[(size_t)i * n + j] = old[a][v] - acc[a][v];
         }
 }
 
@@ -850,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     // be the same in every block, so each step reads the status flags once,
     // right after a barrier and before the update phase in which factor_inv
     // may write them again.
-    if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_inv(ba.sys[bid], sm.fac, 0);
+    if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_inv(ba.sys[bid], sm.fac, 0, -1);
     grid.sync();
     for (int kb = 0; kb < nblk_max; ++kb) {
         const int k0 = kb * kNB;
@@ -877,9 +902,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             panel_task(s, sm.tile, k0, min(kNB, s.n - k0), base, npt, task - offs[b]);
         }
         grid.sync();
-        // Block b takes task 0 of system b (the tile holding its next diagonal
-        // block) and factors that block at once; the other blocks share the
-        // remaining tasks of all systems.
+        // Block b applies the last update to the next diagonal block of
+        // system b and factors that block at once; the other blocks share the
+        // update tiles of all systems (the tile holding that diagonal block
+        // stores only its rows below it).
         bool any = false;
         offs[0] = 0;
         for (int b = 0; b < nsys; ++b) {
@@ -888,7 +914,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             int per = 0;
             if ((live & (1u << b)) && rows > 0) {
                 const int nt = (rows + kTile - 1) / kTile;
-                per = nt * (nt + 1) / 2 + nt * ((k0 + kNB + kTile - 1) / kTile) - 1;  // besides task 0
+                per = nt * (nt + 1) / 2 + nt * ((k0 + kNB + kTile - 1) / kTile);
                 any = true;
             }
             offs[b + 1] = offs[b] + per;
@@ -897,19 +923,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         if (bid < nsys) {
             const SolveArgs<T> &s = ba.sys[bid];
             const int rows = s.n - base;
-            if ((live & (1u << bid)) && rows > 0) {
-                const int nt = (rows + kTile - 1) / kTile;
-                update_task<T, TC>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile, 0);
-                __syncthreads();  // the tile's writes are visible to the block
-                factor_inv(s, sm.fac, kb + 1);
-            }
+            if ((live & (1u << bid)) && rows > 0) factor_inv(s, sm.fac, kb + 1, k0);
         } else {
             for (int task = bid - nsys; task < offs[nsys]; task += nbk - nsys) {
                 const int b = sys_of(offs, nsys, task);
                 const SolveArgs<T> &s = ba.sys[b];
                 const int nt = (s.n - base + kTile - 1) / kTile;
                 update_task<T, TC>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile,
-                                   1 + task - offs[b]);
+                                   task - offs[b]);
             }
         }
         grid.sync();
