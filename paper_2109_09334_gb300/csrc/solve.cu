@@ -12,8 +12,8 @@
 // instead of a kernel launch:
 //   * Cholesky, right-looking with 32-wide panels.  One block applies the
 //     last update to the next diagonal block itself, factors it right away
-//     and inverts the factor in the same sweep (rolled loops in shared
-//     memory, so the short serial chain stays in the instruction cache).  Phase P
+//     and inverts the factor in the same sweep (eight steps of four columns,
+//     exchanging through shared memory).  Phase P
 //     then forms the panel L_ik = A_ik L_kk^-T as 64x32 GEMM tiles; phase U
 //     applies A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64
 //     tiles, whose products run on the tensor cores in the FP32 solve
@@ -464,7 +464,9 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int 
     }
     bool bad = false;
     T minpiv = (T)1e30;
-#pragma unroll 1
+    // unrolled: buffer indices, register picks and row tests become constants
+    // (one system 0.941 -> 0.912 ms at n = 1735)
+#pragma unroll
     for (int jb = 0; jb < kNB; jb += 4) {
         __syncthreads();  // columns jb..jb+3 of S and rows jb..jb+3 of Y are published
         const int b = (jb >> 2) & 1;
