@@ -795,6 +795,8 @@ def measure_sectors(args, dev, world, rank):
         x0, y0 = (int(v) for v in rng.integers(0, 4096 - n + 1, size=2))
         f = sp.fit
         plan = SfftPlan(n, n, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype="float32", precision=args.precision)
+        # systems solved several per launch: 64-wide Cholesky panels
+        plan.solve_panel = 64 if args.sector_solve == "batched" else 32
         Rt = torch.from_numpy(np.ascontiguousarray(R[x0:x0 + n, y0:y0 + n])).to(dev)
         St = torch.from_numpy(np.ascontiguousarray(S[x0:x0 + n, y0:y0 + n])).to(dev)
         work.append((plan, Rt, St, n, f))
@@ -842,6 +844,7 @@ def measure_sectors(args, dev, world, rank):
            "mpix_per_s": world * npix / (ms * 1e3), "gpu_launches_per_batch": binfo["launches"],
            "api": "sfft_batch_create (library-captured CUDA graph) + sfft_batch_launch",
            "solve_group": binfo["solve_group"], "solve_group_tuning_ms": binfo["tune_ms"],
+           "solve_panel": work[0][0].solve_panel,
            "one_at_a_time": {"value": world * len(work) * 1e3 / seq_ms, "ms_per_batch": seq_ms,
                              "api": "sfft_run_pair per sector"},
            "sizes": [w[3] for w in work], "fits": [[w[4].w0, w[4].dk, w[4].db] for w in work],

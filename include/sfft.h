@@ -137,6 +137,20 @@ int sfft_plan_destroy(sfft_plan_t plan);
 int sfft_plan_workspace_bytes(sfft_plan_t plan, uint64_t *bytes);
 
 /*
+ * Panel width of the blocked Cholesky factorisation of the FP32 solve (the
+ * solve of Eq. 18; FP64 plans always use 32): 32 (the default) or 64.  With
+ * 64 a solve needs half the grid barriers and half the passes over the
+ * trailing matrix but a longer serial chain per diagonal block: faster when
+ * several systems share a launch (sfft_run_pairs, batches, servers), slower
+ * for one system alone.  The widths round differently (both meet the
+ * solve's tolerance); systems solved in one launch must share the width
+ * (SFFT_ERR_INVALID otherwise).  Server slots and pool lanes that batch
+ * four or more pairs (batch >= 4) use 64.  SFFT_ERR_INVALID for another width.
+ */
+int sfft_plan_set_solve_panel(sfft_plan_t plan, int32_t width);
+int sfft_plan_solve_panel(sfft_plan_t plan, int32_t *width);
+
+/*
  * Build the normal equations M theta = rhs of Eq. 18 (blocks Eq. 19-24) from
  * the reference R and science S, through the lag tables of App. B
  * (Eq. B5-B16): forward FFTs of the monomial-weighted images R^ij = xt^i yt^j R
@@ -283,8 +297,9 @@ int sfft_run_pair(sfft_plan_t plan, const void *d_ref, const void *d_sci,
  * (grouped by number of unknowns, largest first), and every pair is
  * subtracted (Eq. 3).  Per pair the results equal those of
  * sfft_run_pair on the same plan and inputs, bit for bit.
- *   plans[count]   : distinct plans sharing cfg.precision; a plan listed
- *                    twice, or a precision mismatch, is SFFT_ERR_INVALID.
+ *   plans[count]   : distinct plans sharing cfg.precision (and, for FP32,
+ *                    the solve panel width); a plan listed twice, or a
+ *                    mismatch, is SFFT_ERR_INVALID.
  *   d_refs, d_scis, d_diffs : count device image pointers, each as in
  *                    sfft_run_pair (d_diffs[i] distinct from the inputs).
  *   d_masks        : NULL, or count pointers, each NULL or a mask.

@@ -112,6 +112,15 @@ class SfftPlan:
     def workspace_bytes(self):
         return sfft_plan_workspace_bytes(self.handle)
 
+    @property
+    def solve_panel(self):
+        """Panel width of the FP32 solve's blocked Cholesky (32 or 64)."""
+        return binding.sfft_plan_solve_panel(self.handle)
+
+    @solve_panel.setter
+    def solve_panel(self, width):
+        binding.sfft_plan_set_solve_panel(self.handle, width)
+
     def _check_img(self, t):
         torch = _torch()
         assert t.is_cuda and t.dtype == self.dtype and tuple(t.shape) == self.shape and t.is_contiguous(), \

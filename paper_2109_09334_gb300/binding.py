@@ -81,6 +81,8 @@ def library():
         lib.sfft_plan_create.argtypes = [cfgp, vp, ctypes.POINTER(vp)]
         lib.sfft_plan_destroy.argtypes = [vp]
         lib.sfft_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sfft_plan_set_solve_panel.argtypes = [vp, ctypes.c_int32]
+        lib.sfft_plan_solve_panel.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
         lib.sfft_build_system.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.sfft_solve_static.argtypes = [vp, vp, i32, i32, vp, vp, vp]
@@ -192,6 +194,16 @@ def sfft_plan_create(cfg, stream=None):
 
 def sfft_plan_destroy(plan):
     _check(library().sfft_plan_destroy(plan), "sfft_plan_destroy")
+
+
+def sfft_plan_set_solve_panel(plan, width):
+    _check(library().sfft_plan_set_solve_panel(plan, int(width)), "sfft_plan_set_solve_panel")
+
+
+def sfft_plan_solve_panel(plan):
+    w = ctypes.c_int32()
+    _check(library().sfft_plan_solve_panel(plan, ctypes.byref(w)), "sfft_plan_solve_panel")
+    return w.value
 
 
 def sfft_plan_workspace_bytes(plan):

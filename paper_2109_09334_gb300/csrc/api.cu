@@ -206,6 +206,7 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     Plan *p = new (std::nothrow) Plan();
     if (!p) return SFFT_ERR_OOM;
     memset((void *)p, 0, sizeof(Plan));
+    p->solve_panel = 32;
     p->cfg = *cfg;
     p->n0 = cfg->n0;
     p->n1 = cfg->n1;
@@ -510,6 +511,18 @@ int sfft_plan_destroy(sfft_plan_t plan) {
     return SFFT_OK;
 }
 
+int sfft_plan_set_solve_panel(sfft_plan_t plan, int32_t width) {
+    if (!plan || (width != 32 && width != 64)) return SFFT_ERR_INVALID;
+    ((Plan *)plan)->solve_panel = width;
+    return SFFT_OK;
+}
+
+int sfft_plan_solve_panel(sfft_plan_t plan, int32_t *width) {
+    if (!plan || !width) return SFFT_ERR_INVALID;
+    *width = ((Plan *)plan)->solve_panel;
+    return SFFT_OK;
+}
+
 int sfft_plan_workspace_bytes(sfft_plan_t plan, uint64_t *bytes) {
     if (!plan || !bytes) return SFFT_ERR_INVALID;
     *bytes = ((Plan *)plan)->ws_bytes;
@@ -728,6 +741,8 @@ int check_pairs(const sfft_plan_t *plans, int32_t count, const void *const *d_re
         if (d_diffs[i] == d_refs[i] || d_diffs[i] == d_scis[i]) return SFFT_ERR_INVALID;
         if (!images_aligned(d_refs[i], d_scis[i], d_masks ? d_masks[i] : nullptr)) return SFFT_ERR_INVALID;
         if (((Plan *)plans[i])->fp64 != ((Plan *)plans[0])->fp64) return SFFT_ERR_INVALID;
+        if (!((Plan *)plans[0])->fp64 && ((Plan *)plans[i])->solve_panel != ((Plan *)plans[0])->solve_panel)
+            return SFFT_ERR_INVALID;  // one solve kernel per launch
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return SFFT_ERR_INVALID;  // one workspace per pair
     }

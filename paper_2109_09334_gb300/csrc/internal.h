@@ -109,6 +109,8 @@ struct Plan {
     // tune_tc: 0 or 1 the solve's tile products on the CUDA cores, 2 on the
     // tensor cores (FP32 plans only; see solve.cu)
     int tune_tr, tune_gi, tune_ng, tune_sgrid, tune_tc;
+    // panel width of the FP32 blocked Cholesky: 32 (default) or 64 (solve.cu)
+    int solve_panel;
     // basis (see BasisView); the tables are built at plan creation
     int bspline;           // 0 polynomial, 1 B-spline
     int nfx, nfy, nbx, nby;

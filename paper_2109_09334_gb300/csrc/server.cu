@@ -170,6 +170,10 @@ int create_server(const sfft_config *cfg, int depth, int batch, Server **out) {
             server_free(v);
             return rc;
         }
+        // four or more systems per solve launch: the 64-wide panels (half the
+        // barriers and trailing passes, a longer chain per step; measured at
+        // n = 1735: 8 systems 3.26 -> 2.77 ms, 4 even, 2 slower)
+        if (batch >= 4) s.plan->solve_panel = 64;
         e = cudaMalloc(&s.ref, v->img_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&s.sci, v->img_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&s.diff, v->img_bytes);

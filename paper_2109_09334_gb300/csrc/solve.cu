@@ -36,7 +36,10 @@ namespace cg = cooperative_groups;
 
 namespace sfft {
 
-constexpr int kNB = 32;         // Cholesky panel width / diagonal block size
+// Cholesky panel width NB (template parameter of the kernel): 32 or 64
+constexpr int kNBMax = 64;
+constexpr int kDB = 32;         // sub-block of the diagonal block factored in one sweep
+constexpr int kKC = 32;         // k chunk of a tile product staged at once
 constexpr int kTile = 64;       // trailing-update and GEMM output tile
 constexpr int kMaxIters = 12;   // refinement iterations
 constexpr double kTol = 1e-12;  // ||r|| / ||rhs||
@@ -47,7 +50,7 @@ constexpr int kMaxBatch = kMaxSolveBatch;  // systems solved together by one lau
 
 template <typename T>
 struct SolveArgs {
-    int n, nblk;
+    int n;
     const double *M, *rhs;
     double *dsc, *x, *r, *stats;  // stats[0..3]
     T *A, *W, *z, *y, *wseg;
@@ -56,13 +59,10 @@ struct SolveArgs {
     sfft_solve_info *info;
 };
 
-// Both operands of a tile product are staged with k contiguous, rows of
-// kNB + 4 values: groups of four k are 16-byte aligned for vector loads, and
-// rows 1 apart start 4 banks apart.
 template <typename T>
-struct __align__(16) TileSmem {
-    T a[kTile][kNB + 4];   // a(i, p)
-    T bt[kTile][kNB + 4];  // b(p, j) at bt[j][p]
+struct TileSmem {
+    T a[kTile][kKC + 1];  // a(i, p)
+    T b[kKC][kTile + 1];  // b(p, j)
 };
 
 // four consecutive values of shared memory (16-byte aligned)
@@ -84,20 +84,11 @@ __device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
 // Operands of one 32-deep chunk of a 64x64 tile product, loaded into
 // registers (kLdOps elements of each per thread): all loads of a chunk are
 // in flight before the first store to shared memory.
-constexpr int kLdOps = kTile * kNB / kThreads;
+constexpr int kLdOps = kTile * kKC / kThreads;
 template <typename T>
 struct TileOps {
     T ra[kLdOps], rb[kLdOps];
 };
-
-// Element e of a 64 x 32 operand read from a k-major (row-major in k) source:
-// a warp takes 8 consecutive j (32-byte segments) of 4 consecutive k, so the
-// transposing store to bt[j][k] is free of bank conflicts.
-__device__ __forceinline__ void op_rowmajor_pos(int e, int &j, int &p) {
-    const int l = e & 31, hi = e >> 5;
-    j = (hi & 7) * 8 + (l >> 2);
-    p = (hi >> 3) * 4 + (l & 3);
-}
 
 // chunk [kk, kk + kn) of the operands of tile_gemm (same a, b, bounds)
 template <bool TB, typename T>
@@ -106,60 +97,65 @@ __device__ __forceinline__ void tile_load(TileOps<T> &o, const T *Ag, int lda, i
     const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kLdOps; ++q) {
-        const int e = tid + q * kThreads, i = e / kNB, p = e % kNB;
+        const int e = tid + q * kThreads, i = e / kKC, p = e % kKC;
         o.ra[q] = (i < arows && p < kn) ? Ag[(size_t)(arow0 + i) * lda + kk + p] : (T)0;
     }
     if constexpr (TB) {
 #pragma unroll
         for (int q = 0; q < kLdOps; ++q) {
-            const int e = tid + q * kThreads, j = e / kNB, p = e % kNB;
+            const int e = tid + q * kThreads, j = e / kKC, p = e % kKC;
             o.rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(bcol0 + j) * ldb + kk + p] : (T)0;
         }
     } else {
 #pragma unroll
         for (int q = 0; q < kLdOps; ++q) {
-            int j, p;
-            op_rowmajor_pos(tid + q * kThreads, j, p);
+            const int e = tid + q * kThreads, p = e / kTile, j = e % kTile;
             o.rb[q] = (j < bcols && p < kn) ? Bg[(size_t)(kk + p) * ldb + bcol0 + j] : (T)0;
         }
     }
 }
 
-// acc += the product of one loaded chunk: stage it in shared memory, then
-// each thread accumulates its 4x4 outputs (rows 4 tr + u, columns tc + 16 v)
-// over the 32 values of k in order, reading four k at a time per row
+// acc += the product of one loaded chunk: stage it in shared memory
+// (tile_stage), then each thread accumulates its 4x4 outputs (rows 4 tr + u,
+// columns tc + 16 v) over the 32 values of k in order (tile_compute).
 template <bool TB, typename T>
-__device__ __forceinline__ void tile_mul(T (&acc)[4][4], TileSmem<T> &sm, const TileOps<T> &o) {
+__device__ __forceinline__ void tile_stage(TileSmem<T> &sm, const TileOps<T> &o) {
     const int tid = threadIdx.x;
-    const int tr = tid / 16, tc = tid % 16;
 #pragma unroll
     for (int q = 0; q < kLdOps; ++q) {
         const int e = tid + q * kThreads;
-        sm.a[e / kNB][e % kNB] = o.ra[q];
-        if constexpr (TB) {
-            sm.bt[e / kNB][e % kNB] = o.rb[q];
-        } else {
-            int j, p;
-            op_rowmajor_pos(e, j, p);
-            sm.bt[j][p] = o.rb[q];
-        }
+        sm.a[e / kKC][e % kKC] = o.ra[q];
+        if constexpr (TB)
+            sm.b[e % kKC][e / kKC] = o.rb[q];
+        else
+            sm.b[e / kTile][e % kTile] = o.rb[q];
     }
     __syncthreads();
-#pragma unroll 2
-    for (int p4 = 0; p4 < kNB; p4 += 4) {
-        T av[4][4], bv[4][4];
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_compute(T (&acc)[4][4], const TileSmem<T> &sm) {
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+#pragma unroll 8
+    for (int p = 0; p < kKC; ++p) {
+        T av[4], bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ld4(&sm.a[tr * 4 + u][p4], av[u]);
+        for (int u = 0; u < 4; ++u) av[u] = sm.a[tr * 4 + u][p];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) ld4(&sm.bt[tc + 16 * v][p4], bv[v]);
+        for (int v = 0; v < 4; ++v) bv[v] = sm.b[p][tc + 16 * v];
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += av[u][pp] * bv[v][pp];
+            for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
     }
     __syncthreads();
+}
+
+template <bool TB, typename T>
+__device__ __forceinline__ void tile_mul(T (&acc)[4][4], TileSmem<T> &sm, const TileOps<T> &o) {
+    tile_stage<TB>(sm, o);
+    tile_compute(acc, sm);
 }
 
 // 64x64 tile:  acc(i, j) += sum_{k0 <= k < k1} a(i, k) b(k, j)
@@ -171,13 +167,13 @@ __device__ __forceinline__ void tile_mul(T (&acc)[4][4], TileSmem<T> &sm, const 
 template <typename T>
 __device__ void tile_gemm(T (&acc)[4][4], TileSmem<T> &sm, const T *Ag, int lda, int arow0, int arows,
                           const T *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
-    for (int kk = k0; kk < k1; kk += kNB) {
+    for (int kk = k0; kk < k1; kk += kKC) {
         TileOps<T> o;
         if (transB) {
-            tile_load<true>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kNB, k1 - kk));
+            tile_load<true>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kKC, k1 - kk));
             tile_mul<true>(acc, sm, o);
         } else {
-            tile_load<false>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kNB, k1 - kk));
+            tile_load<false>(o, Ag, lda, arow0, arows, Bg, ldb, bcol0, bcols, kk, min(kKC, k1 - kk));
             tile_mul<false>(acc, sm, o);
         }
     }
@@ -206,7 +202,7 @@ constexpr int kTcCols = 64;                    // tensor-memory columns per bloc
 constexpr long long kTcWaitCycles = 2000000000LL;  // bounded wait on the MMA barrier (~1 s)
 
 struct __align__(1024) TcSmem {
-    float op[4][kTile * kNB];  // a_hi, a_lo, b_hi, b_lo in the canonical K-major layout
+    float op[4][kTile * kKC];  // a_hi, a_lo, b_hi, b_lo in the canonical K-major layout
 };
 
 // block-wide tensor-core state: the mbarrier, the accumulator's tensor-memory
@@ -283,14 +279,14 @@ __device__ void tc_release(TcState &st) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "n"(kTcCols));
 }
 
-// tile_gemm on the tensor cores for one chunk of at most kNB values of k
-// (k1 - k0 <= kNB), same operands and result layout.  Returns false if the
+// tile_gemm on the tensor cores for one chunk of at most kKC values of k
+// (k1 - k0 <= kKC), same operands and result layout.  Returns false if the
 // MMAs did not complete within the wait limit (acc is then not valid).
 __device__ bool tile_gemm_tc(float (&acc)[4][4], TcSmem &tc, TcState &st, const float *Ag, int lda, int arow0,
                              int arows, const float *Bg, int ldb, int bcol0, int bcols, bool transB, int k0, int k1) {
     constexpr int kLd = kLdOps;
     const int tid = threadIdx.x, tr = tid / 16, tc16 = tid % 16;
-    const int kn = min(kNB, k1 - k0);
+    const int kn = min(kKC, k1 - k0);
     // element e = tid + q * kThreads of a 64 x 32 operand is (row, k) with
     // the lane choosing (row mod 8, k mod 4) and the rest (row / 8, k / 4):
     // a warp then stores one whole core matrix (32 consecutive words, no
@@ -331,7 +327,7 @@ __device__ bool tile_gemm_tc(float (&acc)[4][4], TcSmem &tc, TcState &st, const 
         const uint32_t a0 = smem_addr(tc.op[0]), a1 = smem_addr(tc.op[1]);
         const uint32_t b0 = smem_addr(tc.op[2]), b1 = smem_addr(tc.op[3]);
 #pragma unroll
-        for (int ks = 0; ks < kNB / 8; ++ks) {
+        for (int ks = 0; ks < kKC / 8; ++ks) {
             const uint32_t off = ks * 256;  // two core matrices along K per MMA
             tc_mma(st.tmem, tc_desc(a0 + off), tc_desc(b0 + off), idesc, ks > 0);
             tc_mma(st.tmem, tc_desc(a0 + off), tc_desc(b1 + off), idesc, 1);
@@ -388,9 +384,11 @@ __device__ bool tile_gemm_tc(float (&acc)[4][4], TcSmem &tc, TcState &st, const 
 // double-buffered by step parity.
 template <typename T>
 struct __align__(16) FactorSmem {
-    T col[2][kNB][4];
-    T row[2][kNB][4];
-    T lp[kNB][kNB + 1];  // the panel rows of the block's last update
+    T col[2][kDB][4];
+    T row[2][kDB][4];
+    T lp[kNBMax][kKC + 1];  // staged operands (panel rows of the last update; 32 x 32 products)
+    T s1[kDB][kDB + 1];  // L21
+    T s2[kDB][kDB + 1];  // L21 L11^-1
 };
 
 template <typename T>
@@ -410,11 +408,12 @@ __device__ __forceinline__ T pick4(const T (&v)[4], int q) {
 __device__ __forceinline__ float inv_sqrt(float d) { return rsqrtf(d); }
 __device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 
-// The whole block factors the 32x32 diagonal block kb and inverts its factor
-// in the same sweep, four columns per step.  With kp >= 0 the block first
-// applies the last update of the diagonal block itself, S = A_kk - L L^T with
-// L = A[k0:k0+32, kp:kp+32] (the panel of step kp), in the operation order of
-// the trailing-update tiles; with kp < 0 A_kk is already fully updated.  Then:
+// The whole block factors the 32x32 block of A at (k0, k0) (nb <= 32 rows
+// inside the matrix) and inverts its factor in the same sweep, four columns
+// per step.  With kp >= 0 the block first applies the last update of that
+// block itself, S = A_kk - L L^T with L = A[k0:k0+32, kp:kp+32] (the panel
+// of a 32-wide step kp), in the operation order of the trailing-update
+// tiles; with kp < 0 A_kk is already fully updated.  Then:
 // every thread factors the 4x4 pivot block itself, forms the L entries of the
 // rows it needs by forward substitution, and applies the rank-4 update to S
 // and the matching block forward elimination to Y (L Y = I, so Y ends as
@@ -424,10 +423,9 @@ __device__ __forceinline__ double inv_sqrt(double d) { return 1.0 / sqrt(d); }
 // Writes L_kk into A and L_kk^-1 into W (zeros above the diagonal) and flags
 // a non-positive pivot.
 template <typename T>
-__device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int kp) {
+__device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int k0, int nb, int kp) {
     const int tid = threadIdx.x;
-    const int n = s.n, k0 = kb * kNB;
-    const int nb = min(kNB, n - k0);
+    const int n = s.n;
     const int t = tid >> 3, u = tid & 7;
     T sv[4], yv[4];
 #pragma unroll
@@ -441,14 +439,14 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int 
     }
     if (kp >= 0) {
 #pragma unroll
-        for (int q = 0; q < kNB * kNB / kThreads; ++q) {
-            const int e = tid + q * kThreads, r = e / kNB, p = e % kNB;
+        for (int q = 0; q < kDB * kDB / kThreads; ++q) {
+            const int e = tid + q * kThreads, r = e / kDB, p = e % kDB;
             f.lp[r][p] = r < nb ? s.A[(size_t)(k0 + r) * n + kp + p] : (T)0;
         }
         __syncthreads();
         T acc[4] = {};
 #pragma unroll 8
-        for (int p = 0; p < kNB; ++p) {
+        for (int p = 0; p < kDB; ++p) {
             const T a = f.lp[t][p];
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] += a * f.lp[u + 8 * q][p];
@@ -467,7 +465,7 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int 
     // unrolled: buffer indices, register picks and row tests become constants
     // (one system 0.941 -> 0.912 ms at n = 1735)
 #pragma unroll
-    for (int jb = 0; jb < kNB; jb += 4) {
+    for (int jb = 0; jb < kDB; jb += 4) {
         __syncthreads();  // columns jb..jb+3 of S and rows jb..jb+3 of Y are published
         const int b = (jb >> 2) & 1;
         T p0[4], p1[4], p2[4], p3[4], st[4], sc[4][4], yc[4][4];
@@ -529,7 +527,7 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int 
         }
         // publish columns jn..jn+3 of S and rows jn..jn+3 of Y (the other buffer)
         const int jn = jb + 4;
-        if (jn < kNB) {
+        if (jn < kDB) {
             const int u0 = jn & 7;
             if (u >= u0 && u < u0 + 4) f.col[b ^ 1][t][u - u0] = pick4(sv, jn >> 3);
             if (t >= jn && t < jn + 4) {
@@ -552,6 +550,149 @@ __device__ void factor_inv(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int 
         else if ((double)minpiv < s.stats[0]) s.stats[0] = (double)minpiv;
     }
     __syncthreads();
+}
+
+// 32x32 block product in the thread layout of factor_inv (thread (t, u)
+// holds row t, columns u + 8 q): out(t, c) = sum_{p < 32} a(t, p) b(p, c),
+// a at f.lp[0..31][p], b at f.lp[32 + p][c], accumulated over p in order.
+template <typename T>
+__device__ __forceinline__ void mm32(const FactorSmem<T> &f, T (&out)[4]) {
+    const int tid = threadIdx.x, t = tid >> 3, u = tid & 7;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = (T)0;
+#pragma unroll 8
+    for (int p = 0; p < kDB; ++p) {
+        const T a = f.lp[t][p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] += a * f.lp[kDB + p][u + 8 * q];
+    }
+}
+
+// The 64x64 diagonal block kb: with kp >= 0 the block first applies its last
+// update A_kk -= L L^T, L = A[k0:k0+64, kp:kp+64] (the panel of step kp, two
+// chunks of 32 in order, as the trailing-update tiles), to its lower
+// triangle.  Then, with [L11 0; L21 L22] its factor,
+//   L11 (factor_inv), L21 = A21 L11^-T, A22 -= L21 L21^T, L22 (factor_inv),
+//   W21 = -L22^-1 (L21 L11^-1),
+// so that W_kk = [L11^-1 0; W21 L22^-1] = L_kk^-1.  L_kk goes into A, L_kk^-1
+// into W (zeros above the diagonal of both, over the whole 64x64 block).
+template <typename T>
+__device__ void factor64(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int kp) {
+    constexpr int kNB = 64;
+    const int tid = threadIdx.x, n = s.n;
+    const int k0 = kb * kNB, nb = min(kNB, n - k0);
+    if (kp >= 0) {
+        const int tr = tid / 16, tc = tid % 16;  // rows 4 tr + a, columns tc + 16 v
+        T acc[4][4] = {};
+        for (int kc = 0; kc < kNB; kc += kKC) {
+            for (int e = tid; e < kNB * kKC; e += kThreads) {
+                const int r = e / kKC, p = e % kKC;
+                f.lp[r][p] = r < nb ? s.A[(size_t)(k0 + r) * n + kp + kc + p] : (T)0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int p = 0; p < kKC; ++p) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) av[a] = f.lp[tr * 4 + a][p];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) bv[v] = f.lp[tc + 16 * v][p];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[a][v] += av[a] * bv[v];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int r = tr * 4 + a, c = tc + 16 * v;
+                if (r < nb && c <= r) {
+                    T *p = s.A + (size_t)(k0 + r) * n + k0 + c;
+                    *p = *p - acc[a][v];
+                }
+            }
+        __syncthreads();  // the updated block is visible to the whole block
+    }
+    factor_inv(s, f, k0, min(kDB, nb), -1);
+    const int n2 = nb - kDB;
+    if (n2 <= 0) return;
+    const int t = tid >> 3, u = tid & 7;
+    T o[4];
+    // L21 = A21 L11^-T: a(i, p) = A[k0+32+i][k0+p], b(p, c) = L11^-1[c][p]
+    for (int e = tid; e < kDB * kDB; e += kThreads) {
+        const int r = e / kDB, c = e % kDB;
+        f.lp[r][c] = r < n2 ? s.A[(size_t)(k0 + kDB + r) * n + k0 + c] : (T)0;
+        f.lp[kDB + r][c] = s.W[(size_t)(k0 + c) * n + k0 + r];
+    }
+    __syncthreads();
+    mm32(f, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = u + 8 * q;
+        f.s1[t][c] = t < n2 ? o[q] : (T)0;
+        if (t < n2) s.A[(size_t)(k0 + kDB + t) * n + k0 + c] = o[q];
+    }
+    __syncthreads();
+    // A22 -= L21 L21^T (lower triangle)
+    for (int e = tid; e < kDB * kDB; e += kThreads) {
+        const int r = e / kDB, c = e % kDB;
+        f.lp[r][c] = f.s1[r][c];
+        f.lp[kDB + r][c] = f.s1[c][r];
+    }
+    __syncthreads();
+    mm32(f, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = u + 8 * q;
+        if (t < n2 && c <= t) {
+            T *p = s.A + (size_t)(k0 + kDB + t) * n + k0 + kDB + c;
+            *p = *p - o[q];
+        }
+    }
+    __syncthreads();
+    factor_inv(s, f, k0 + kDB, n2, -1);
+    // X = L21 L11^-1, then W21 = -L22^-1 X
+    for (int e = tid; e < kDB * kDB; e += kThreads) {
+        const int r = e / kDB, c = e % kDB;
+        f.lp[r][c] = f.s1[r][c];
+        f.lp[kDB + r][c] = s.W[(size_t)(k0 + r) * n + k0 + c];
+    }
+    __syncthreads();
+    mm32(f, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f.s2[t][u + 8 * q] = o[q];
+    __syncthreads();
+    for (int e = tid; e < kDB * kDB; e += kThreads) {
+        const int r = e / kDB, c = e % kDB;
+        f.lp[r][c] = (r < n2 && c < n2) ? s.W[(size_t)(k0 + kDB + r) * n + k0 + kDB + c] : (T)0;
+        f.lp[kDB + r][c] = f.s2[r][c];
+    }
+    __syncthreads();
+    mm32(f, o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = u + 8 * q;
+        if (t < n2) s.W[(size_t)(k0 + kDB + t) * n + k0 + c] = -o[q];
+        // above the diagonal: the upper-right quadrant of both blocks
+        if (c < n2) {
+            s.A[(size_t)(k0 + t) * n + k0 + kDB + c] = (T)0;
+            s.W[(size_t)(k0 + t) * n + k0 + kDB + c] = (T)0;
+        }
+    }
+    __syncthreads();
+}
+
+// diagonal block kb of an NB-wide factorisation, with the last update from
+// the panel at column kp (kp < 0: none)
+template <int NB, typename T>
+__device__ __forceinline__ void factor_block(const SolveArgs<T> &s, FactorSmem<T> &f, int kb, int kp) {
+    if constexpr (NB == kDB)
+        factor_inv(s, f, kb * kDB, min(kDB, s.n - kb * kDB), kp);
+    else
+        factor64(s, f, kb, kp);
 }
 
 // sum_{j < len} a[j] b[j] by one warp (lane = this thread's lane), with
@@ -627,7 +768,7 @@ __device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int k
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
+            for (int v = 0; v < 4; ++v) {
                 const int i = tr * 4 + u, j = tc + 16 * v;
                 if (i < ni && j < kn) s.A[(size_t)(i0 + i) * n + k0 + j] = acc[u][v];
             }
@@ -635,34 +776,33 @@ __device__ void panel_task(const SolveArgs<T> &s, TileSmem<T> &sm, int k0, int k
         const int j0 = (task - npt) * kTile, nj = min(kTile, k0 - j0);
         // a(r, p) = Linv[r][p], b(p, c) = W[k0 + p][j0 + c]
         tile_gemm(acc, sm, s.W + k0, n, k0, kn, s.W + (size_t)k0 * n, n, j0, nj, false, 0, kn);
-        if (tr < kNB / 4) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int r = tr * 4 + u, c = tc + 16 * v;
-                    if (r < kn && c < nj) s.W[(size_t)(k0 + r) * n + j0 + c] = acc[u][v];
-                }
-        }
+            for (int v = 0; v < 4; ++v) {
+                const int r = tr * 4 + u, c = tc + 16 * v;
+                if (r < kn && c < nj) s.W[(size_t)(k0 + r) * n + j0 + c] = acc[u][v];
+            }
     }
 }
 
-// Phase U task `task` of one system at panel k0: a 64x64 tile of the
-// trailing lower triangle, A_ij -= L_ik L_jk^T (task < ntiles; task 0 holds
-// the next diagonal block, whose update factor_inv applies itself, so that
-// tile stores only its rows below it), or a 64x64 tile of the block rows of W below,
-// W_i[:, 0:k0+32] -= L_ik W_k.  Columns k0..k0+31 of W below the diagonal
+// Phase U task `task` of one system at panel k0 (panel width NB): a 64x64
+// tile of the trailing lower triangle, A_ij -= L_ik L_jk^T (task < ntiles;
+// task 0 holds the next diagonal block, whose last update factor_block
+// applies itself: with NB = 32 that tile stores only its rows below it, with
+// NB = 64 it is not a task), or a 64x64 tile of the block rows of W below,
+// W_i[:, 0:k0+NB] -= L_ik W_k.  Columns k0..k0+NB-1 of W below the diagonal
 // block are first written by this step, so their old values are zero and
-// are not read (W is never cleared).
+// are not read (W is never cleared).  The products run over k in chunks of 32.
 template <typename T>
 struct UpdTile {
     int i0, j0, ni, nj;
     int rmin;       // first row stored
     bool wtile;     // a tile of W (else of A)
-    TileOps<T> op;  // operands of the product, loaded ahead of it
+    TileOps<T> op;  // operands of the first chunk, loaded ahead of the product
 };
 
-template <typename T>
+template <int NB, typename T>
 __device__ __forceinline__ void upd_desc(UpdTile<T> &u, const SolveArgs<T> &s, int k0, int base, int ntiles, int ncw,
                                          int task) {
     const int n = s.n;
@@ -677,10 +817,10 @@ __device__ __forceinline__ void upd_desc(UpdTile<T> &u, const SolveArgs<T> &s, i
         const int q = task - ntiles;
         u.i0 = base + (q / ncw) * kTile;
         u.j0 = (q % ncw) * kTile;
-        u.nj = min(kTile, k0 + kNB - u.j0);
+        u.nj = min(kTile, k0 + NB - u.j0);
     }
     u.ni = min(kTile, n - u.i0);
-    u.rmin = (task == 0) ? base + kNB : u.i0;
+    u.rmin = (task == 0) ? base + NB : u.i0;
 }
 
 // a(i, p) = L[i0 + i][k0 + p]; b(p, j) = L[j0 + j][k0 + p] (A tile) or
@@ -688,16 +828,16 @@ __device__ __forceinline__ void upd_desc(UpdTile<T> &u, const SolveArgs<T> &s, i
 template <bool WT, typename T>
 __device__ __forceinline__ void upd_load(UpdTile<T> &u, const SolveArgs<T> &s, int k0) {
     const int n = s.n;
-    tile_load<!WT>(u.op, s.A + k0, n, u.i0, u.ni, WT ? s.W + (size_t)k0 * n : s.A + k0, n, u.j0, u.nj, 0, kNB);
+    tile_load<!WT>(u.op, s.A + k0, n, u.i0, u.ni, WT ? s.W + (size_t)k0 * n : s.A + k0, n, u.j0, u.nj, 0, kKC);
 }
 
-// element (i, j) of the tile is stored (A: lower triangle; W: columns below k0 + 32)
-template <bool WT>
+// element (i, j) of the tile is stored (A: lower triangle; W: columns below k0 + NB)
+template <bool WT, int NB>
 __device__ __forceinline__ bool upd_in(int n, int k0, int rmin, int i, int j) {
-    return i < n && i >= rmin && (WT ? j < k0 + kNB : (j < n && j <= i));
+    return i < n && i >= rmin && (WT ? j < k0 + NB : (j < n && j <= i));
 }
 
-template <bool WT, typename T>
+template <bool WT, int NB, typename T>
 __device__ __forceinline__ void upd_old(const UpdTile<T> &u, const SolveArgs<T> &s, int k0, T (&old)[4][4]) {
     const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
     const T *C = WT ? s.W : s.A;
@@ -706,11 +846,11 @@ __device__ __forceinline__ void upd_old(const UpdTile<T> &u, const SolveArgs<T> 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
-            old[a][v] = (upd_in<WT>(n, k0, u.rmin, i, j) && !(WT && j >= k0)) ? C[(size_t)i * n + j] : (T)0;
+            old[a][v] = (upd_in<WT, NB>(n, k0, u.rmin, i, j) && !(WT && j >= k0)) ? C[(size_t)i * n + j] : (T)0;
         }
 }
 
-template <bool WT, typename T>
+template <bool WT, int NB, typename T>
 __device__ __forceinline__ void upd_store(const UpdTile<T> &u, const SolveArgs<T> &s, int k0, const T (&old)[4][4],
                                           const T (&acc)[4][4]) {
     const int n = s.n, tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
@@ -720,54 +860,75 @@ __device__ __forceinline__ void upd_store(const UpdTile<T> &u, const SolveArgs<T
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int i = u.i0 + tr * 4 + a, j = u.j0 + tc + 16 * v;
-            if (upd_in<WT>(n, k0, u.rmin, i, j)) C[(size_t)i * n + j] = old[a][v] - acc[a][v];
+            if (upd_in<WT, NB>(n, k0, u.rmin, i, j)) C[(size_t)i * n + j] = old[a][v] - acc[a][v];
         }
 }
 
-// the tile whose operands are in u.op: old values (their loads overlap the
-// product), product on the CUDA cores, store
-template <bool WT, typename T>
+// the tile whose first operand chunk is in u.op: old values (their loads
+// overlap the product), product on the CUDA cores (the loads of a later
+// chunk are in flight during the product of the one before), store
+template <bool WT, int NB, typename T>
 __device__ __forceinline__ void upd_finish(const UpdTile<T> &u, const SolveArgs<T> &s, TileSmem<T> &sm, int k0) {
     T old[4][4], acc[4][4] = {};
-    upd_old<WT>(u, s, k0, old);
-    tile_mul<!WT>(acc, sm, u.op);
-    upd_store<WT>(u, s, k0, old, acc);
+    upd_old<WT, NB>(u, s, k0, old);
+    tile_stage<!WT>(sm, u.op);
+    const int n = s.n;
+#pragma unroll
+    for (int c = 1; c < NB / kKC; ++c) {
+        TileOps<T> o;
+        tile_load<!WT>(o, s.A + k0, n, u.i0, u.ni, WT ? s.W + (size_t)k0 * n : s.A + k0, n, u.j0, u.nj, c * kKC,
+                       kKC);
+        tile_compute(acc, sm);
+        tile_stage<!WT>(sm, o);
+    }
+    tile_compute(acc, sm);
+    upd_store<WT, NB>(u, s, k0, old, acc);
 }
 
 // One task on its own.  The tensor-core variant takes the tile product on
-// the tensor cores in FP32 (3xTF32); a tensor-core wait that timed out flags
-// the system (SFFT_ERR_TIMEOUT) and the tile is computed on the CUDA cores.
-template <typename T, bool TC>
+// the tensor cores in FP32 (3xTF32, per chunk of 32); a tensor-core wait that
+// timed out flags the system (SFFT_ERR_TIMEOUT) and the tile is computed on
+// the CUDA cores.
+template <typename T, bool TC, int NB>
 __device__ void update_task(const SolveArgs<T> &s, SolveSmem<T> &smu, TcState &st, int k0, int base, int ntiles,
                             int ncw, int task) {
     UpdTile<T> u;
-    upd_desc(u, s, k0, base, ntiles, ncw, task);
+    upd_desc<NB>(u, s, k0, base, ntiles, ncw, task);
     if constexpr (TC && sizeof(T) == 4) {
         const int n = s.n;
         T old[4][4], acc[4][4] = {};
         if (u.wtile)
-            upd_old<true>(u, s, k0, old);
+            upd_old<true, NB>(u, s, k0, old);
         else
-            upd_old<false>(u, s, k0, old);
+            upd_old<false, NB>(u, s, k0, old);
         const T *Bg = u.wtile ? s.W + (size_t)k0 * n : s.A + k0;
-        if (!tile_gemm_tc(acc, smu.tc, st, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, 0, kNB)) {
+        bool ok = true;
+        for (int kk = 0; kk < NB && ok; kk += kKC) {
+            T part[4][4];
+            ok = tile_gemm_tc(part, smu.tc, st, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, kk, kk + kKC);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[a][v] += part[a][v];
+        }
+        if (!ok) {
             if (threadIdx.x == 0) s.flag[0] = SFFT_ERR_TIMEOUT;
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[a][v] = (T)0;
-            tile_gemm(acc, smu.tile, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, 0, kNB);
+            tile_gemm(acc, smu.tile, s.A + k0, n, u.i0, u.ni, Bg, n, u.j0, u.nj, !u.wtile, 0, NB);
         }
         if (u.wtile)
-            upd_store<true>(u, s, k0, old, acc);
+            upd_store<true, NB>(u, s, k0, old, acc);
         else
-            upd_store<false>(u, s, k0, old, acc);
+            upd_store<false, NB>(u, s, k0, old, acc);
     } else if (u.wtile) {
         upd_load<true>(u, s, k0);
-        upd_finish<true>(u, s, smu.tile, k0);
+        upd_finish<true, NB>(u, s, smu.tile, k0);
     } else {
         upd_load<false>(u, s, k0);
-        upd_finish<false>(u, s, smu.tile, k0);
+        upd_finish<false, NB>(u, s, smu.tile, k0);
     }
 }
 
@@ -812,7 +973,7 @@ __device__ __forceinline__ int sys_of(const int *offs, int nsys, int task) {
     return b;
 }
 
-template <typename T, bool TC>
+template <typename T, bool TC, int NB>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k_solve_coop(BatchArgs<T> ba) {
     cg::grid_group grid = cg::this_grid();
     __shared__ SolveSmem<T> sm;
@@ -831,7 +992,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     int nblk_max = 0;
     for (int b = 0; b < nsys; ++b) {
         nrow[b + 1] = nrow[b] + ba.sys[b].n;
-        nblk_max = max(nblk_max, ba.sys[b].nblk);
+        nblk_max = max(nblk_max, (ba.sys[b].n + NB - 1) / NB);
     }
     const int nrows_all = nrow[nsys];
 
@@ -877,14 +1038,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
     // be the same in every block, so each step reads the status flags once,
     // right after a barrier and before the update phase in which factor_inv
     // may write them again.
-    if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_inv(ba.sys[bid], sm.fac, 0, -1);
+    if (bid < nsys && ba.sys[bid].flag[0] == 0) factor_block<NB>(ba.sys[bid], sm.fac, 0, -1);
     grid.sync();
     for (int kb = 0; kb < nblk_max; ++kb) {
-        const int k0 = kb * kNB;
-        const int base = k0 + kNB;  // first trailing row
+        const int k0 = kb * NB;
+        const int base = k0 + NB;  // first trailing row
         unsigned live = 0;
         for (int b = 0; b < nsys; ++b)
-            if (kb < ba.sys[b].nblk && ba.sys[b].flag[0] == 0) live |= 1u << b;
+            if (kb < (ba.sys[b].n + NB - 1) / NB && ba.sys[b].flag[0] == 0) live |= 1u << b;
         int offs[kMaxBatch + 1];
         offs[0] = 0;
         for (int b = 0; b < nsys; ++b) {
@@ -901,13 +1062,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             const SolveArgs<T> &s = ba.sys[b];
             const int rows = s.n - base;
             const int npt = rows > 0 ? (rows + kTile - 1) / kTile : 0;
-            panel_task(s, sm.tile, k0, min(kNB, s.n - k0), base, npt, task - offs[b]);
+            panel_task(s, sm.tile, k0, min(NB, s.n - k0), base, npt, task - offs[b]);
         }
         grid.sync();
         // Block b applies the last update to the next diagonal block of
-        // system b and factors that block at once; the other blocks share the
-        // update tiles of all systems (the tile holding that diagonal block
-        // stores only its rows below it).
+        // system b (tile 0) and factors that block at once; the other blocks
+        // share the remaining tiles of all systems.
         bool any = false;
         offs[0] = 0;
         for (int b = 0; b < nsys; ++b) {
@@ -916,7 +1076,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             int per = 0;
             if ((live & (1u << b)) && rows > 0) {
                 const int nt = (rows + kTile - 1) / kTile;
-                per = nt * (nt + 1) / 2 + nt * ((k0 + kNB + kTile - 1) / kTile);
+                // NB = 64: tile 0 is the diagonal block, not a task
+                per = nt * (nt + 1) / 2 + nt * ((k0 + NB + kTile - 1) / kTile) - (NB == kTile ? 1 : 0);
                 any = true;
             }
             offs[b + 1] = offs[b] + per;
@@ -925,14 +1086,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
         if (bid < nsys) {
             const SolveArgs<T> &s = ba.sys[bid];
             const int rows = s.n - base;
-            if ((live & (1u << bid)) && rows > 0) factor_inv(s, sm.fac, kb + 1, k0);
+            if ((live & (1u << bid)) && rows > 0) factor_block<NB>(s, sm.fac, kb + 1, k0);
         } else {
             for (int task = bid - nsys; task < offs[nsys]; task += nbk - nsys) {
                 const int b = sys_of(offs, nsys, task);
                 const SolveArgs<T> &s = ba.sys[b];
                 const int nt = (s.n - base + kTile - 1) / kTile;
-                update_task<T, TC>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + kNB + kTile - 1) / kTile,
-                                   task - offs[b]);
+                update_task<T, TC, NB>(s, sm, st, k0, base, nt * (nt + 1) / 2, (k0 + NB + kTile - 1) / kTile,
+                                       (NB == kTile ? 1 : 0) + task - offs[b]);
             }
         }
         grid.sync();
@@ -1058,7 +1219,6 @@ static SolveArgs<T> system_args(int n, const double *M, const double *rhs, doubl
                                 double *dsc, double *xw, double *r, void *A, void *W, void *zv, int *flag) {
     SolveArgs<T> a;
     a.n = n;
-    a.nblk = (n + kNB - 1) / kNB;
     a.M = M;
     a.rhs = rhs;
     a.dsc = dsc;
@@ -1076,11 +1236,19 @@ static SolveArgs<T> system_args(int n, const double *M, const double *rhs, doubl
     return a;
 }
 
+// the kernel variant: tile products on the tensor cores (FP32 only), panel
+// width 32 or 64 (FP32 only; FP64 solves use 32)
+static const void *solve_kernel(bool fp64, bool tc, int panel) {
+    if (fp64) return (const void *)k_solve_coop<double, false, 32>;
+    if (panel == 64) return tc ? (const void *)k_solve_coop<float, true, 64> : (const void *)k_solve_coop<float, false, 64>;
+    return tc ? (const void *)k_solve_coop<float, true, 32> : (const void *)k_solve_coop<float, false, 32>;
+}
+
 template <typename T>
-static cudaError_t launch_batch(const BatchArgs<T> &ba, int grid, cudaStream_t st, bool tc = false) {
+static cudaError_t launch_batch(const BatchArgs<T> &ba, int grid, cudaStream_t st, bool tc = false, int panel = 32) {
     if (grid <= ba.nsys) return cudaErrorInvalidConfiguration;  // blocks >= nsys take the shared tasks
     void *args[] = {(void *)&ba};
-    void *kern = (sizeof(T) == 4 && tc) ? (void *)k_solve_coop<T, true> : (void *)k_solve_coop<T, false>;
+    const void *kern = solve_kernel(sizeof(T) == 8, tc, panel);
     return cudaLaunchCooperativeKernel(kern, grid, kThreads, args, solve_dyn_smem(sizeof(T) == 8), st);
 }
 
@@ -1109,7 +1277,7 @@ static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *co
         // serving against 515 on 152)
         grid = full / kBlocksPerSM;
     }
-    const cudaError_t err = launch_batch(ba, grid, st, tc);
+    const cudaError_t err = launch_batch(ba, grid, st, tc, plans[0]->solve_panel);
     plans[0]->launches += 1;
     return err;
 }
@@ -1117,8 +1285,9 @@ static cudaError_t solve_batch_t(Plan *const *plans, int count, const double *co
 cudaError_t solve_batch(Plan *const *plans, int count, const double *const *M, const double *const *rhs,
                         double *const *x, sfft_solve_info *const *info, cudaStream_t s) {
     if (count < 1 || count > kMaxBatch) return cudaErrorInvalidValue;
-    for (int b = 1; b < count; ++b)
-        if (plans[b]->fp64 != plans[0]->fp64) return cudaErrorInvalidValue;  // sizes may differ
+    for (int b = 1; b < count; ++b)  // sizes may differ
+        if (plans[b]->fp64 != plans[0]->fp64 || (!plans[0]->fp64 && plans[b]->solve_panel != plans[0]->solve_panel))
+            return cudaErrorInvalidValue;
     return plans[0]->fp64 ? solve_batch_t<double>(plans, count, M, rhs, x, info, s)
                           : solve_batch_t<float>(plans, count, M, rhs, x, info, s);
 }
@@ -1133,13 +1302,18 @@ int solve_grid_size(bool fp64, bool tc) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t dsm = solve_dyn_smem(fp64);
-    const void *kern = fp64 ? (const void *)k_solve_coop<double, false>
-                            : (tc ? (const void *)k_solve_coop<float, true> : (const void *)k_solve_coop<float, false>);
     // all of the unified L1/shared storage as shared memory, so that two FP32
-    // blocks (33 KB of static shared memory each) fit on an SM
-    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, dsm);
+    // blocks (33 KB of static shared memory each) fit on an SM; the grid is
+    // the smaller residency of the two panel widths
+    per = 1 << 30;
+    for (int panel = 32; panel <= (fp64 ? 32 : 64); panel += 32) {
+        const void *kern = solve_kernel(fp64, tc, panel);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+        int pk = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pk, kern, kThreads, dsm);
+        per = pk < per ? pk : per;
+    }
     if (per < 1 || sms < 1) return 0;
     const int g = sms * (per < kBlocksPerSM ? per : kBlocksPerSM);
     return g <= kMaxSolveGrid ? g : 0;

@@ -98,6 +98,17 @@ def test_set_tuning_checks_before_use(lib):
     assert lib.sfft_plan_tuning(None, arr(0, 0, 0, 0, 0)) == binding.SFFT_ERR_INVALID
 
 
+def test_solve_panel_checks_before_use(lib):
+    """Only 32 and 64 are panel widths; the plan is not touched otherwise."""
+    fake = ctypes.c_void_p(4096)  # never dereferenced: every call below is rejected first
+    assert lib.sfft_plan_set_solve_panel(None, 32) == binding.SFFT_ERR_INVALID
+    for bad in (0, 16, 48, 96, 128, -64):
+        assert lib.sfft_plan_set_solve_panel(fake, bad) == binding.SFFT_ERR_INVALID
+    w = ctypes.c_int32()
+    assert lib.sfft_plan_solve_panel(None, ctypes.byref(w)) == binding.SFFT_ERR_INVALID
+    assert lib.sfft_plan_solve_panel(fake, None) == binding.SFFT_ERR_INVALID
+
+
 def test_misaligned_images_rejected(lib):
     """Images and masks must be 16-byte aligned (vector loads); checked before any use."""
     fake = ctypes.c_void_p(4096)  # never dereferenced: every call below is rejected first

@@ -4,7 +4,9 @@ single-pair path.
 Each request runs the kernels of sfft_run_pair on its own slot, and those
 kernels are deterministic, so results must be bitwise equal to sfft_run_pair
 on the same inputs, alone and in a mix of in-flight requests (device and host
-memory, with and without masks).  The single-pair path itself is pinned to
+memory, with and without masks).  A server that batches four or more pairs
+solves with 64-wide Cholesky panels, so the reference plan is set to the
+same width.  The single-pair path itself is pinned to
 the oracle in test_gpu_parity.py.
 """
 import ctypes
@@ -78,6 +80,7 @@ def test_server_matches_run_pair(lib, case, depth, batch):
     tdt = torch.float32 if dtype == "float32" else torch.float64
     pairs = make_pairs(n0, n1, 6, seed=n0 + depth)
     plan = SfftPlan(n0, n1, w, w, dk, db, cpr, dtype=dtype, precision=precision)
+    plan.solve_panel = 64 if batch >= 4 else 32  # the server's slots batch with 64-wide panels
     expected = []
     dev_inputs = []
     for R, S, mask in pairs:
@@ -222,6 +225,7 @@ def test_eager_flush_solves_incomplete_batch_without_wait(lib):
     Rt = torch.from_numpy(R.astype(np.float32)).cuda()
     St = torch.from_numpy(S.astype(np.float32)).cuda()
     plan = SfftPlan(n0, n1, 2, 2, 1, 1, 1, dtype="float32", precision="mixed")
+    plan.solve_panel = 64  # as the batching server's slots
     De, xe, _, _, _ = plan.run_pair(Rt, St)
     torch.cuda.synchronize()
     for eager in (True, False):
