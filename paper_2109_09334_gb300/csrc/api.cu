@@ -207,6 +207,13 @@ int plan_new(const sfft_config *cfg, cudaStream_t s, Plan **out) {
     if (!p) return SFFT_ERR_OOM;
     memset((void *)p, 0, sizeof(Plan));
     p->solve_panel = 32;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            p->sms = 0;
+        cudaGetLastError();
+    }
     p->cfg = *cfg;
     p->n0 = cfg->n0;
     p->n1 = cfg->n1;

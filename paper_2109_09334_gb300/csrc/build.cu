@@ -54,7 +54,7 @@ template <typename T, typename I>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, int n1, int nfy, int TR, const I *__restrict__ R,
                                                const I *__restrict__ S, const uint8_t *__restrict__ mask,
                                                cpx<T> *__restrict__ F, const cpx<T> *__restrict__ tw1g,
-                                               const T *__restrict__ fy) {
+                                               const T *__restrict__ fy, int pf_dist) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = n1 / 16;
     const int np = padded_len(n1) + 4;  // +4: rows start in different banks
@@ -78,6 +78,17 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows(int n0, in
         T rv[16], sv[16];
         load16<T, I>(R + rowoff + y0, rv);
         load16<T, I>(S + rowoff + y0, sv);
+        // the rows of the block pf_dist launches later (about one wave of
+        // resident blocks) into L2, so that its loads need not wait for HBM
+        if (pf_dist > 0) {
+            const int xp = ((blockIdx.x + pf_dist) / nfft) * TR + grp;
+            if (xp < n0) {
+                const size_t po = (size_t)xp * n1 + y0;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(R + po));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(S + po));
+                if (mask != nullptr && (gt & 7) == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(mask + po));
+            }
+        }
         if (mask != nullptr) {
             const uint4 mv = __ldg(reinterpret_cast<const uint4 *>(mask + rowoff + y0));
             const unsigned mw[4] = {mv.x, mv.y, mv.z, mv.w};
@@ -1201,6 +1212,10 @@ __global__ void k_assemble(int n, const int4 *__restrict__ unk, LagView lv, cons
 }
 
 // ---------------------------------------------------------------------------
+// k_rows prefetches into L2 the rows of the block this many waves of one
+// block per multiprocessor later
+constexpr int kRowsPrefetch = 1;
+
 template <typename T, typename I>
 static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const uint8_t *mask,
                                bool moments, cudaStream_t s) {
@@ -1235,7 +1250,8 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     // power), cheaper than the table's per-thread strided reads
     kern<<<((p->n0 + TR - 1) / TR) * nfft, TR * G, smem, s>>>(p->n0, p->n1, p->nfy, TR, (const I *)ref,
                                                               (const I *)sci, mask, (cpx<T> *)p->F,
-                                                              (const cpx<T> *)p->twp1, p->bspline ? ft.fy : nullptr);
+                                                              (const cpx<T> *)p->twp1, p->bspline ? ft.fy : nullptr,
+                                                              kRowsPrefetch * p->sms);
     }
     p->launches++;
     if (moments && !p->bspline) {

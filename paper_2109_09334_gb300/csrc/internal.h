@@ -111,6 +111,7 @@ struct Plan {
     int tune_tr, tune_gi, tune_ng, tune_sgrid, tune_tc;
     // panel width of the FP32 blocked Cholesky: 32 (default) or 64 (solve.cu)
     int solve_panel;
+    int sms;  // multiprocessors of the device the plan was created on
     // basis (see BasisView); the tables are built at plan creation
     int bspline;           // 0 polynomial, 1 B-spline
     int nfx, nfy, nbx, nby;
