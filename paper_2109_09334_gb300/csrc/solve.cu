@@ -46,6 +46,7 @@ constexpr double kTol = 1e-12;  // ||r|| / ||rhs||
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSM = 2;  // resident FP32 solve blocks per SM (more loads in flight); FP64 takes 1
 constexpr int kSeg = 8;         // row segments of the W^T y product
+constexpr int kWDepth32 = 16;   // FP32 loads in flight per lane in the products with W
 constexpr int kMaxBatch = kMaxSolveBatch;  // systems solved together by one launch
 
 template <typename T>
@@ -695,51 +696,66 @@ __device__ __forceinline__ void factor_block(const SolveArgs<T> &s, FactorSmem<T
         factor64(s, f, kb, kp);
 }
 
+// pairwise sum of D partial sums (D a power of two) in a fixed order:
+// neighbours first, ((a0 + a1) + (a2 + a3)) + ... 
+template <typename T, int D>
+__device__ __forceinline__ T tree_sum(T (&acc)[D]) {
+#pragma unroll
+    for (int s = 1; s < D; s *= 2)
+#pragma unroll
+        for (int q = 0; q + s < D; q += 2 * s) acc[q] = acc[q] + acc[q + s];
+    return acc[0];
+}
+
 // sum_{j < len} a[j] b[j] by one warp (lane = this thread's lane), with
-// eight independent loads of each operand in flight; the result is
-// reduced across the warp (every lane returns it).
-template <typename T, typename V>
+// D independent loads of each operand in flight; the result is reduced
+// across the warp (every lane returns it).
+template <typename T, typename V, int D = 8>
 __device__ __forceinline__ T dot_warp(const T *a, const V *b, int lane, int len) {
-    T acc[8];
+    T acc[D];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+    for (int q = 0; q < D; ++q) acc[q] = (T)0;
     int j = lane;
-    for (; j + 7 * 32 < len; j += 8 * 32) {
-        T av[8], bv[8];
+    for (; j + (D - 1) * 32 < len; j += D * 32) {
+        T av[D], bv[D];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < D; ++q) {
             av[q] = a[j + 32 * q];
             bv[q] = (T)b[j + 32 * q];
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] += av[q] * bv[q];
+        for (int q = 0; q < D; ++q) acc[q] += av[q] * bv[q];
     }
     for (; j < len; j += 32) acc[0] += a[j] * (T)b[j];
-    T r = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    T r = tree_sum<T, D>(acc);
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     return r;
 }
 
-// sum_{k0 <= k < k1} W[k][i] y[k] by one thread, eight rows in flight
-template <typename T>
+// sum_{k0 <= k < k1} W[k][i] y[k] by one thread, D rows in flight
+template <typename T, int D = 8>
 __device__ __forceinline__ T col_dot(const T *W, const T *y, int n, int i, int k0, int k1) {
-    T acc[8];
+    T acc[D];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = (T)0;
+    for (int q = 0; q < D; ++q) acc[q] = (T)0;
     int k = k0;
-    for (; k + 7 < k1; k += 8) {
-        T wv[8], yv[8];
+    for (; k + D - 1 < k1; k += D) {
+        T wv[D], yv[D];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < D; ++q) {
             wv[q] = W[(size_t)(k + q) * n + i];
             yv[q] = y[k + q];
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] += wv[q] * yv[q];
+        for (int q = 0; q < D; ++q) acc[q] += wv[q] * yv[q];
     }
     for (; k < k1; ++k) acc[0] += W[(size_t)k * n + i] * y[k];
-    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    return tree_sum<T, D>(acc);
 }
+
+// loads in flight per lane in the refinement's products with W (compute type)
+template <typename T>
+__host__ __device__ constexpr int w_depth() { return sizeof(T) == 4 ? kWDepth32 : 8; }
 
 // trailing-update tile tt -> (ti, tj), ti >= tj
 __device__ __forceinline__ void lower_tile(int tt, int *ti, int *tj) {
@@ -1160,10 +1176,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             if (done & (1u << b)) continue;
             const SolveArgs<T> &s = ba.sys[b];
             const int i2 = s.n - 1 - k;
-            const T a = dot_warp<T>(s.W + (size_t)k * s.n, s.z, lane, k + 1);
+            const T a = dot_warp<T, T, w_depth<T>()>(s.W + (size_t)k * s.n, s.z, lane, k + 1);
             if (lane == 0) s.y[k] = a;
             if (i2 != k) {
-                const T a2 = dot_warp<T>(s.W + (size_t)i2 * s.n, s.z, lane, i2 + 1);
+                const T a2 = dot_warp<T, T, w_depth<T>()>(s.W + (size_t)i2 * s.n, s.z, lane, i2 + 1);
                 if (lane == 0) s.y[i2] = a2;
             }
         }
@@ -1178,7 +1194,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kBlocksPerSM : 1) k
             const int ch = q / kSeg, sg = q % kSeg;
             const int i = ch * 32 + lane;
             const int k0 = max(ch * 32, sg * segrows), k1 = min(n, (sg + 1) * segrows);
-            if (i < n) s.wseg[(size_t)sg * n + i] = col_dot<T>(s.W, s.y, n, i, k0, k1);
+            if (i < n) s.wseg[(size_t)sg * n + i] = col_dot<T, w_depth<T>()>(s.W, s.y, n, i, k0, k1);
         }
         grid.sync();
         for (int e = gtid; e < nrows_all; e += gthreads) {
