@@ -8,16 +8,19 @@
 // until ||r|| / ||rhs|| <= 1e-12.
 //
 // Everything runs in one cooperative (grid-synchronised) kernel with two
-// blocks per SM, so the ~n/32 dependent block steps cost a grid barrier each
-// instead of a kernel launch:
-//   * Cholesky, right-looking with 32-wide panels.  One block applies the
-//     last update to the next diagonal block itself, factors it right away
-//     and inverts the factor in the same sweep (eight steps of four columns,
-//     exchanging through shared memory).  Phase P
-//     then forms the panel L_ik = A_ik L_kk^-T as 64x32 GEMM tiles; phase U
-//     applies A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64
-//     tiles, whose products run on the tensor cores in the FP32 solve
-//     (tcgen05, 3xTF32 split; see tile_gemm_tc).
+// blocks per SM (FP32; one in FP64), so the ~n/NB dependent block steps cost
+// a grid barrier each instead of a kernel launch:
+//   * Cholesky, right-looking with NB-wide panels, NB = 32 (the default) or
+//     64 (per plan; fewer barriers and trailing passes, a longer chain per
+//     step: faster when several systems share a launch).  One block applies
+//     the last update to the next diagonal block itself, factors it right
+//     away and inverts the factor in the same sweep (factor_inv: eight steps
+//     of four columns per 32x32 block, exchanging through shared memory;
+//     factor64 builds the 64x64 block from two of them).  Phase P then forms
+//     the panel L_ik = A_ik L_kk^-T as 64xNB GEMM tiles; phase U applies
+//     A_ij -= L_ik L_jk^T to the trailing lower triangle in 64x64 tiles, on
+//     the CUDA cores or, in the FP32 variant that asks for it, on the tensor
+//     cores (tcgen05, 3xTF32 split; see tile_gemm_tc).
 //   * W = L^-1 is formed in the same sweep (block forward elimination applied
 //     to the identity): W_kk = L_kk^-1 from the diagonal factorisation, phase
 //     P sets W_k[:, 0:k0] = L_kk^-1 W_k[:, 0:k0] and phase U applies
