@@ -196,7 +196,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_rows_blu(int n0
 // plain per-thread partials, then a two-sum reduction across the block.
 //   RR_v = sum_y Rm^2 yt^v (v <= 2dk), R_v = sum_y Rm yt^v (v <= dk+db),
 //   RS_v = sum_y Rm Sm yt^v (v <= dk), S_v = sum_y Sm yt^v (v <= db).
-template <typename T, typename I>
+// NRR, NR, NRS, NS: the powers accumulated of each kind (the largest needed
+// for any degrees: 7, 7, 4, 4; D_K = D_B = 2 needs 5, 5, 3, 3)
+template <typename T, typename I, int NRR = 7, int NR = 7, int NRS = 4, int NS = 4>
 __global__ void __launch_bounds__(256) k_row_moments(int n1, int dk, int db, const I *__restrict__ R,
                                                      const I *__restrict__ S, const uint8_t *__restrict__ mask,
                                                      double *__restrict__ rowmom) {
@@ -216,12 +218,10 @@ __global__ void __launch_bounds__(256) k_row_moments(int n1, int dk, int db, con
         T p = (T)1;
 #pragma unroll
         for (int v = 0; v < 7; ++v) {
-            pRR[v] += rv * rv * p;
-            pR[v] += rv * p;
-            if (v < 4) {
-                pRS[v] += rv * sv * p;
-                pS[v] += sv * p;
-            }
+            if (v < NRR) pRR[v] += rv * rv * p;
+            if (v < NR) pR[v] += rv * p;
+            if (v < NRS) pRS[v] += rv * sv * p;
+            if (v < NS) pS[v] += sv * p;
             p *= yt;
         }
     };
@@ -1166,12 +1166,12 @@ __global__ void k_assemble(int n, const int4 *__restrict__ unk, LagView lv, cons
                            const double *__restrict__ cmat, double *__restrict__ M, double *__restrict__ rhs) {
     const int nk = lv.nk, nb = lv.nbt;
     const int z_la = nk * (nk + 1) / 2, z_th = z_la + nk * nb, z_e = z_th + nk;
-    const size_t total = (size_t)n * n;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total + n;
-         e += (size_t)gridDim.x * blockDim.x) {
-        if (e >= total) {  // rhs
-            const int row = (int)(e - total);
-            const int4 ur = unk[row];
+    // rows blockIdx.y + k gridDim.y of M (row n: rhs), threads along the columns
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= n) return;
+    for (int row = blockIdx.y; row <= n; row += gridDim.y) {
+        if (row == n) {  // rhs
+            const int4 ur = unk[col];
             double v;
             if (ur.x) {
                 if (ur.z == 0 && ur.w == 0) v = z0[z_th + ur.y];  // Theta(0,0)
@@ -1179,10 +1179,9 @@ __global__ void k_assemble(int n, const int4 *__restrict__ unk, LagView lv, cons
             } else {
                 v = z0[z_e + ur.y];  // E (Eq. B15)
             }
-            rhs[row] = v;
+            rhs[col] = v;
             continue;
         }
-        const int row = (int)(e / n), col = (int)(e % n);
         const int4 ur = unk[row], uc = unk[col];
         double v;
         if (ur.x && uc.x) {
@@ -1207,7 +1206,7 @@ __global__ void k_assemble(int n, const int4 *__restrict__ unk, LagView lv, cons
         } else {  // C (Eq. B11)
             v = cmat[(size_t)ur.y * nb + uc.y];
         }
-        M[e] = v;
+        M[(size_t)row * n + col] = v;
     }
 }
 
@@ -1255,8 +1254,8 @@ static cudaError_t launch_rows(Plan *p, const void *ref, const void *sci, const 
     }
     p->launches++;
     if (moments && !p->bspline) {
-        k_row_moments<T, I><<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask,
-                                                  p->rowmom);
+        auto km = (p->cfg.dk == 2 && p->cfg.db == 2) ? k_row_moments<T, I, 5, 5, 3, 3> : k_row_moments<T, I>;
+        km<<<p->n0, 256, 0, s>>>(p->n1, p->cfg.dk, p->cfg.db, (const I *)ref, (const I *)sci, mask, p->rowmom);
         p->launches++;
         if (p->lam_closed) {
             k_boundary<I><<<dim3(2 * p->cfg.w1 + 1, kBndChunks), 256, 0, s>>>(p->n0, p->n1, p->cfg.w0, p->cfg.w1,
@@ -1370,10 +1369,8 @@ static cudaError_t launch_lags(Plan *p, double *M, double *rhs, cudaStream_t s) 
         p->launches++;
         if ((err = cudaGetLastError())) return err;
     }
-    const size_t total = (size_t)p->n * p->n + p->n;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    k_assemble<<<blocks, 256, 0, s>>>(p->n, p->unk, lv, p->z0, p->cmat, M, rhs);
+    const dim3 grid((p->n + 255) / 256, p->n + 1 < 65535 ? p->n + 1 : 65535);
+    k_assemble<<<grid, 256, 0, s>>>(p->n, p->unk, lv, p->z0, p->cmat, M, rhs);
     p->launches++;
     return cudaGetLastError();
 }
