@@ -205,10 +205,10 @@ int flush(Server *v) {
     const uint64_t first = v->flushed, end = v->next_seq;
     const int cnt = (int)(end - first);
     if (cnt == 0) return SFFT_OK;
-    Plan *plans[kMaxDepth];
-    const double *M[kMaxDepth], *rhs[kMaxDepth];
-    double *x[kMaxDepth];
-    sfft_solve_info *info[kMaxDepth];
+    Plan *plans[kMaxDepth] = {};
+    const double *M[kMaxDepth] = {}, *rhs[kMaxDepth] = {};
+    double *x[kMaxDepth] = {};
+    sfft_solve_info *info[kMaxDepth] = {};
     for (int k = 0; k < cnt; ++k) {
         Slot &s = v->slots[(first + k) % v->depth];
         plans[k] = s.plan;
