@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--sector-solve", default="batched", choices=["batched", "single"],
                     help="sectors64: solve the sectors' systems eight per launch, or one per pair")
     ap.add_argument("--no-masked", action="store_true", help="skip the transient-masked pair measurement")
+    ap.add_argument("--no-solve-batch", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--solve-tc", action="store_true",
                     help="pair mode: the solve's tile products on the tensor cores (for profiler captures)")
     ap.add_argument("--no-sectors", action="store_true", help="skip the 64-sector batch measurement")
@@ -598,6 +599,47 @@ def run_ours(args):
                          "clock": "host wall clock, submit of the first to completion of the last; "
                                   "median of three runs",
                          "runs_pairs_per_s": [round(world * ke / r, 1) for r in runs]}
+
+    # the solve of `batch` built systems in one launch (sfft_solve_batch), with
+    # 32- and 64-wide Cholesky panels: the serving path's solve step alone
+    if not args.no_solve_batch and world == 1:
+        from paper_2109_09334_gb300 import SfftPlan as _Plan
+        nb = args.batch
+        bplans = [_Plan(spec.n0, spec.n1, f.w0, f.w1, f.dk, f.db, f.const_phot_ratio, dtype=spec.dtype,
+                        precision=args.precision) for _ in range(nb)]
+        systems = []
+        for k, bp in enumerate(bplans):
+            _, _, _, Mk, rk = bp.run_pair(*dev_pairs[k & 1], keep_system=True)
+            systems.append((Mk, rk))
+        xb = [torch.empty(bp.n, dtype=torch.float64, device=dev) for bp in bplans]
+        ib = [torch.zeros(24, dtype=torch.uint8, device=dev) for _ in bplans]
+        sb_out = {}
+        for panel in (32, 64):
+            for bp in bplans:
+                bp.solve_panel = panel
+
+            def solve_all():
+                binding.sfft_solve_batch([bp.handle for bp in bplans], [s[0] for s in systems],
+                                         [s[1] for s in systems], xb, ib, stream)
+
+            for _ in range(2):
+                solve_all()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                solve_all()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            st = [info_from_bytes(i.cpu().numpy()) for i in ib]
+            if any(s["status"] != 0 for s in st):
+                raise RuntimeError(f"batched solve status {st}")
+            sb_out[str(panel)] = {"ms_per_launch": round(ms, 4), "ms_per_system": round(ms / nb, 4),
+                                  "iters": [s["iters"] for s in st]}
+        result["solve_batch"] = {"api": "sfft_solve_batch", "systems": nb, "n": plan.n, "panels": sb_out}
+        for bp in bplans:
+            bp.close()
 
     # the plain FP64 GPU path (FP64 FFTs, products, sums, Cholesky), one pair
     # at a time on the same inputs, and how far the headline path's difference

@@ -180,6 +180,21 @@ int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double 
                sfft_solve_info *d_info, sfft_stream_t stream);
 
 /*
+ * Several systems of Eq. 18 in one launch: system i is M_i theta_i = rhs_i on
+ * plans[i]'s workspace, solved exactly as sfft_solve would solve it alone
+ * (bit for bit), up to 8 systems of any sizes side by side.
+ *   plans[count] : distinct plans of one precision (and, for FP32, one solve
+ *                  panel width); count 1..8.
+ *   d_M[i], d_rhs[i], d_x[i], d_info[i] : as for sfft_solve (d_info may be
+ *                  NULL, or any of its entries).
+ * SFFT_ERR_INVALID for count outside 1..8, a NULL plan, matrix, right-hand
+ * side or solution, a plan listed twice, or a mismatch, before any CUDA call.
+ */
+int sfft_solve_batch(const sfft_plan_t *plans, int32_t count, const double *const *d_M,
+                     const double *const *d_rhs, double *const *d_x, sfft_solve_info *const *d_info,
+                     sfft_stream_t stream);
+
+/*
  * sfft_solve without a plan and without allocating: the paper has no
  * counterpart; this is an engineering variant of sfft_solve for callers that
  * cannot allocate device memory at call time.  Examples are a pipeline that

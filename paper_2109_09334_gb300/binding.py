@@ -85,6 +85,7 @@ def library():
         lib.sfft_plan_solve_panel.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
         lib.sfft_build_system.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.sfft_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.sfft_solve_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         lib.sfft_solve_static.argtypes = [vp, vp, i32, i32, vp, vp, vp]
         dbl = ctypes.c_double
         lib.sfft_decorrelate.argtypes = [vp, vp, dbl, dbl, dbl, dbl, vp, vp, vp]
@@ -284,6 +285,17 @@ def sfft_run_pairs(plans, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, strea
     _check(library().sfft_run_pairs(hp, n, _ptr_array(d_refs), _ptr_array(d_scis), _ptr_array(d_masks),
                                     _ptr_array(d_xs), _ptr_array(d_infos), _ptr_array(d_diffs), _s(stream)),
            "sfft_run_pairs")
+
+
+def sfft_solve_batch(plans, d_Ms, d_rhss, d_xs, d_infos=None, stream=None):
+    """Several built systems solved in one launch, system i on plans[i]."""
+    n = len(plans)
+    for name, v in (("d_Ms", d_Ms), ("d_rhss", d_rhss), ("d_xs", d_xs), ("d_infos", d_infos)):
+        if v is not None and len(v) != n:
+            raise ValueError(f"sfft_solve_batch: {name} has {len(v)} entries for {n} plans")
+    hp = (ctypes.c_void_p * n)(*plans)
+    _check(library().sfft_solve_batch(hp, n, _ptr_array(d_Ms), _ptr_array(d_rhss), _ptr_array(d_xs),
+                                      _ptr_array(d_infos), _s(stream)), "sfft_solve_batch")
 
 
 def sfft_batch_create(plans, d_refs, d_scis, d_masks, d_xs, d_infos, d_diffs, solve_group=0):

@@ -581,6 +581,27 @@ int sfft_solve(sfft_plan_t plan, const double *d_M, const double *d_rhs, double 
     return status_of(solve_system(p, d_M, d_rhs, d_x, d_info, (cudaStream_t)stream));
 }
 
+int sfft_solve_batch(const sfft_plan_t *plans, int32_t count, const double *const *d_M,
+                     const double *const *d_rhs, double *const *d_x, sfft_solve_info *const *d_info,
+                     sfft_stream_t stream) {
+    if (!plans || count < 1 || count > kMaxSolveBatch || !d_M || !d_rhs || !d_x) return SFFT_ERR_INVALID;
+    Plan *ps[kMaxSolveBatch];
+    sfft_solve_info *inf[kMaxSolveBatch];
+    for (int i = 0; i < count; ++i) {  // pointers only: no plan is read before all pass
+        if (!plans[i] || !d_M[i] || !d_rhs[i] || !d_x[i]) return SFFT_ERR_INVALID;
+        ps[i] = (Plan *)plans[i];
+        inf[i] = d_info ? d_info[i] : nullptr;
+        for (int k = 0; k < i; ++k)
+            if (ps[k] == ps[i]) return SFFT_ERR_INVALID;  // one workspace per system
+    }
+    for (int i = 1; i < count; ++i)
+        if (ps[i]->fp64 != ps[0]->fp64 || (!ps[0]->fp64 && ps[i]->solve_panel != ps[0]->solve_panel))
+            return SFFT_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) ps[i]->last_stream = s;
+    return status_of(solve_batch(ps, count, d_M, d_rhs, d_x, inf, s));
+}
+
 int sfft_subtract(sfft_plan_t plan, const void *d_ref, const void *d_sci, const double *d_x, void *d_diff,
                   sfft_stream_t stream) {
     if (!plan || !d_ref || !d_sci || !d_x || !d_diff) return SFFT_ERR_INVALID;

@@ -209,3 +209,65 @@ def test_batch_graph_matches_run_pair(lib, solve_group):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_solve_batch_rejects_bad_arguments(lib):
+    """sfft_solve_batch checks its arguments before any plan is read or any CUDA call."""
+    from paper_2109_09334_gb300 import binding as B
+    vp = ctypes.c_void_p
+    one = (vp * 1)(1)
+    two = (vp * 2)(1, 1)
+    assert lib.sfft_solve_batch(None, 1, one, one, one, None, None) == B.SFFT_ERR_INVALID
+    for count in (0, -1, 9):
+        assert lib.sfft_solve_batch(one, count, one, one, one, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_batch(one, 1, None, one, one, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_batch(one, 1, one, None, one, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_batch(one, 1, one, one, None, None, None) == B.SFFT_ERR_INVALID
+    nul = (vp * 1)(None)
+    assert lib.sfft_solve_batch(nul, 1, one, one, one, None, None) == B.SFFT_ERR_INVALID
+    assert lib.sfft_solve_batch(one, 1, nul, one, one, None, None) == B.SFFT_ERR_INVALID
+    # a plan listed twice (rejected before the plans are read)
+    assert lib.sfft_solve_batch(two, 2, two, two, two, None, None) == B.SFFT_ERR_INVALID
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("panel", [32, 64])
+def test_solve_batch_matches_solve(lib, panel):
+    """Systems of different sizes built by sfft_build_system, solved together
+    by sfft_solve_batch: every solution and status bitwise equal to
+    sfft_solve's one at a time (same panel width); a width mismatch is
+    rejected."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09334_gb300 import SfftPlan, binding as B, info_from_bytes
+    plans, systems = [], []
+    for k, (n0, n1, w, dk, db, cpr) in enumerate(MIXED[:5]):
+        p = SfftPlan(n0, n1, w, w, dk, db, cpr)
+        p.solve_panel = panel
+        R, S, mask = _pair(n0, n1, k, 700, torch.float32)
+        _, _, _, M, rhs = p.run_pair(R, S, mask, keep_system=True)
+        plans.append(p)
+        systems.append((M, rhs))
+    stream = torch.cuda.current_stream()
+    alone = []
+    for p, (M, rhs) in zip(plans, systems):
+        x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        info = torch.zeros(24, dtype=torch.uint8, device="cuda")
+        B.sfft_solve(p.handle, M, rhs, x, info, stream)
+        alone.append((x, info))
+    xs = [torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda") for p in plans]
+    infos = [torch.zeros(24, dtype=torch.uint8, device="cuda") for _ in plans]
+    B.sfft_solve_batch([p.handle for p in plans], [s[0] for s in systems], [s[1] for s in systems], xs, infos,
+                       stream)
+    torch.cuda.synchronize()
+    for k in range(len(plans)):
+        assert info_from_bytes(infos[k].cpu().numpy())["status"] == 0
+        assert info_from_bytes(infos[k].cpu().numpy()) == info_from_bytes(alone[k][1].cpu().numpy()), k
+        assert np.array_equal(xs[k].cpu().numpy(), alone[k][0].cpu().numpy()), k
+    plans[1].solve_panel = 96 - panel  # the other width
+    with pytest.raises(B.SfftError) as e:
+        B.sfft_solve_batch([p.handle for p in plans[:2]], [s[0] for s in systems[:2]],
+                           [s[1] for s in systems[:2]], xs[:2], None, stream)
+    assert e.value.status == B.SFFT_ERR_INVALID
+    for p in plans:
+        p.close()
